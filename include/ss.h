@@ -1,0 +1,152 @@
+/*
+ * ss.h -- C ABI of the SneakySnake pre-alignment filter for GB300 (sm_103a).
+ *
+ * What it computes (Alser et al., "SneakySnake", Section 2.3-2.4): for each
+ * pair of a reference segment R[1..m] and a query (read) Q[1..m] and an edit
+ * threshold E, the chip maze Z of Eq. 1 -- 2E+1 rows (HRTs) x m columns
+ * (VRTs), Z[i,j] = 0 where R[j] equals the Q base on diagonal i, else 1 --
+ * and the greedy single-net-routing solution of Section 2.4: from checkpoint
+ * column 1, repeatedly take the longest run of zeros over all rows, count the
+ * obstacle that ends it, and move the checkpoint past it; stop at the row end
+ * or once the count exceeds E.  Per pair the library returns
+ *     accept    = (count <= E)                (1 byte: 1 = alignment needed)
+ *     obstacles = min(count, E + 1)           (int32)
+ * Results are bit-identical to a plain CPU reading of the paper.
+ *
+ * Memory: every data pointer is a DEVICE pointer owned by the caller, except
+ * in ss_filter_host(), which takes host pointers.  The library allocates
+ * only its own workspace, inside the context, within the budget given to
+ * ss_create().  Calls are asynchronous on the given CUDA stream (a
+ * cudaStream_t; NULL = the CUDA default stream) and return a launch-time
+ * status; errors found by the
+ * kernels (a non-ACGT byte, a negative per-pair length or threshold) are
+ * latched in the context and returned by ss_sync().
+ *
+ * Threading: a context may be used by one host thread at a time.
+ */
+#ifndef SS_H
+#define SS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SS_OK 0
+#define SS_ERR_INVALID_ARG (-1)  /* bad scalar/pointer, or bad per-pair value */
+#define SS_ERR_INVALID_BASE (-2) /* an input byte is not A/C/G/T (any case)  */
+#define SS_ERR_OOM (-3)          /* workspace would exceed the budget         */
+#define SS_ERR_CUDA (-4)         /* a CUDA runtime call failed                */
+#define SS_ERR_TIMEOUT (-5)      /* a bounded device-side wait gave up        */
+#define SS_ERR_BUSY (-6)         /* no free slot (serving admission)          */
+#define SS_ERR_UNSUPPORTED (-7)  /* shape outside what the build supports     */
+
+/* ---- input formats -------------------------------------------------------
+ * SS_FMT_ASCII   : one byte per base, 'A','C','G','T' in either case.
+ * SS_FMT_PACKED2 : 2 bits per base, 16 bases per little-endian uint32 word.
+ *   Base j of a sequence lives in word j/16: bit (j%16) holds bit 0 of its
+ *   code and bit 16+(j%16) holds bit 1, with codes A=0, C=1, G=2, T=3.  A
+ *   sequence of m bases takes ss_packed_words(m) = ceil(m/16) words; unused
+ *   bits are zero.  ss_pack() writes this format.                          */
+#define SS_FMT_ASCII 0
+#define SS_FMT_PACKED2 1
+
+/* ---- filter modes (flags of ss_filter_batch) -------------------------- */
+#define SS_MODE_AUTO 0     /* plain launch if m and E are uniform, else bucketed */
+#define SS_MODE_PLAIN 1    /* one launch per (m, E) group, no queue            */
+#define SS_MODE_BUCKETED 2 /* length/threshold-bucketed persistent launch      */
+#define SS_FLAG_NO_GRAPH 16 /* do not replay the captured CUDA graph           */
+
+typedef struct ss_ctx ss_ctx;
+
+/* Create a context on CUDA device `device` with a workspace budget of
+ * `workspace_bytes` (0 = 1 GiB).  The context owns one CUDA stream and a
+ * small device status word; the stream orders internal work only (calls run
+ * on the stream the caller passes).  Returns SS_OK, SS_ERR_INVALID_ARG (out NULL or
+ * bad device) or SS_ERR_CUDA. */
+int ss_create(ss_ctx **out, int device, size_t workspace_bytes);
+
+/* Release everything the context owns.  NULL is accepted. */
+int ss_destroy(ss_ctx *ctx);
+
+/* Human-readable text of a status code (static storage). */
+const char *ss_strerror(int code);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int ss_version(void);
+
+/* Words of the packed format needed for m bases: ceil(m / 16). */
+int64_t ss_packed_words(int64_t m);
+
+/* Pack n ASCII sequences into the SS_FMT_PACKED2 format (step Eq. 1 needs
+ * only base equality, so any fixed code works; this one is documented above).
+ *   ascii          device; sequence p starts at byte offsets[p] (or p*m when
+ *                  offsets is NULL) and has lengths[p] (or m) bases.
+ *   packed         device, output; sequence p starts at word
+ *                  packed_offsets[p] (or p*ceil(m/16) when NULL).
+ * A non-ACGT byte latches SS_ERR_INVALID_BASE (returned by ss_sync); the
+ * affected words are written with that byte's code taken as A.
+ * offsets/lengths/packed_offsets must be all NULL (fixed stride) or all
+ * non-NULL.  Returns SS_OK, SS_ERR_INVALID_ARG or SS_ERR_CUDA. */
+int ss_pack(ss_ctx *ctx, const uint8_t *ascii, const int64_t *offsets,
+            const int32_t *lengths, int32_t m, int64_t n, uint32_t *packed,
+            const int64_t *packed_offsets, void *stream);
+
+/* Filter n equal-length read/reference pairs (Section 2.4).
+ *   reads, refs    device; format SS_FMT_ASCII or SS_FMT_PACKED2.  Pair p's
+ *                  query is reads + offsets[p] and its reference is
+ *                  refs + offsets[p] (units: bytes for ASCII, 32-bit words
+ *                  for PACKED2).  offsets == NULL means a fixed stride of m
+ *                  bases per pair (m bytes, or ceil(m/16) words).
+ *   lengths        device int32[n] per-pair m (>= 0), or NULL with scalar m.
+ *   E              device int32[n] per-pair threshold (>= 0), or NULL with
+ *                  scalar e.
+ *   n              number of pairs (>= 0; 0 is a no-op).
+ *   flags          SS_MODE_* | SS_FLAG_*.
+ *   out_accept     device uint8[n]: 1 if count <= E (alignment needed).
+ *   out_obstacles  device int32[n]: min(count, E+1); -1 for a pair with a
+ *                  negative length or threshold (which also latches
+ *                  SS_ERR_INVALID_ARG).
+ * With offsets != NULL, lengths must be non-NULL.  ASCII input is packed
+ * into context workspace first (fails with SS_ERR_OOM beyond the budget).
+ * Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM, SS_ERR_UNSUPPORTED or
+ * SS_ERR_CUDA. */
+int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
+                    int format, const int64_t *offsets,
+                    const int32_t *lengths, int32_t m, const int32_t *E,
+                    int32_t e, int64_t n, int flags, void *stream,
+                    uint8_t *out_accept, int32_t *out_obstacles);
+
+/* Same as ss_filter_batch for fixed-stride pairs of uniform m and E held in
+ * HOST memory: the library streams chunks host -> device, packs (ASCII) and
+ * filters them, and copies the results back into host out_accept /
+ * out_obstacles, overlapping copies with compute on two internal streams.
+ * Synchronous: returns when the host outputs are written.  Pinned host
+ * buffers give the full copy bandwidth.  Returns SS_OK or an error (device
+ * errors included). */
+int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
+                   int format, int32_t m, int32_t e, int64_t n,
+                   uint8_t *out_accept, int32_t *out_obstacles);
+
+/* Wait for all work on `stream` (NULL = default stream) and for the
+ * context's internal streams, and return the first
+ * device-side error latched since the previous ss_sync (then clear it), or
+ * SS_OK. */
+int ss_sync(ss_ctx *ctx, void *stream);
+
+/* Counters of the context since creation (host-side accounting). */
+typedef struct ss_counters {
+    int64_t pairs;        /* pairs submitted to ss_filter_batch/_host */
+    int64_t launches;     /* kernels launched by the library          */
+    int64_t graph_replays;/* CUDA graph launches                      */
+    int64_t workspace_bytes; /* device workspace currently held       */
+} ss_counters;
+int ss_get_counters(const ss_ctx *ctx, ss_counters *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI in ``include/ss.h``.
+
+Argument marshalling only: every step of the filter runs in the CUDA
+library.  The functions below carry the C names (``ss_create``,
+``ss_filter_batch`` ...) and take plain integers for pointers;
+:class:`Filter` adds the marshalling of torch tensors (``data_ptr()``,
+current CUDA stream).  Loading raises if the library cannot be built or
+loaded -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+from . import build as _build
+
+SS_OK = 0
+SS_ERR_INVALID_ARG = -1
+SS_ERR_INVALID_BASE = -2
+SS_ERR_OOM = -3
+SS_ERR_CUDA = -4
+SS_ERR_TIMEOUT = -5
+SS_ERR_BUSY = -6
+SS_ERR_UNSUPPORTED = -7
+
+SS_FMT_ASCII = 0
+SS_FMT_PACKED2 = 1
+
+SS_MODE_AUTO = 0
+SS_MODE_PLAIN = 1
+SS_MODE_BUCKETED = 2
+SS_FLAG_NO_GRAPH = 16
+
+# every symbol include/ss.h declares (checked by the CPU tests)
+EXPORTED = (
+    "ss_create", "ss_destroy", "ss_strerror", "ss_version",
+    "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
+    "ss_sync", "ss_get_counters",
+)
+
+
+class SSError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libss.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I32, I64, SZ = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                       ctypes.c_size_t)
+    lib.ss_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, SZ]
+    lib.ss_destroy.argtypes = [P]
+    lib.ss_strerror.argtypes = [ctypes.c_int]
+    lib.ss_strerror.restype = ctypes.c_char_p
+    lib.ss_version.restype = ctypes.c_int
+    lib.ss_packed_words.argtypes = [I64]
+    lib.ss_packed_words.restype = I64
+    lib.ss_pack.argtypes = [P, P, P, P, I32, I64, P, P, P]
+    lib.ss_filter_batch.argtypes = [P, P, P, ctypes.c_int, P, P, I32, P, I32,
+                                    I64, ctypes.c_int, P, P, P]
+    lib.ss_filter_host.argtypes = [P, P, P, ctypes.c_int, I32, I32, I64, P, P]
+    lib.ss_sync.argtypes = [P, P]
+    lib.ss_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    for name in EXPORTED:
+        getattr(lib, name)  # raises AttributeError if a symbol is missing
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().ss_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != SS_OK:
+        raise SSError(rc, what)
+
+
+# ---- same-name functions (pointers as ints; 0 = NULL) --------------------
+
+def ss_create(device: int = 0, workspace_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().ss_create(ctypes.byref(h), device, workspace_bytes),
+           "ss_create")
+    return h.value
+
+
+def ss_destroy(ctx: int) -> None:
+    _check(load().ss_destroy(ctx), "ss_destroy")
+
+
+def ss_version() -> int:
+    return load().ss_version()
+
+
+def ss_packed_words(m: int) -> int:
+    return int(load().ss_packed_words(m))
+
+
+def ss_pack(ctx, ascii, offsets, lengths, m, n, packed, packed_offsets,
+            stream) -> int:
+    return load().ss_pack(ctx, ascii or None, offsets or None,
+                          lengths or None, m, n, packed or None,
+                          packed_offsets or None, stream or None)
+
+
+def ss_filter_batch(ctx, reads, refs, fmt, offsets, lengths, m, E, e, n,
+                    flags, stream, out_accept, out_obstacles) -> int:
+    return load().ss_filter_batch(ctx, reads or None, refs or None, fmt,
+                                  offsets or None, lengths or None, m,
+                                  E or None, e, n, flags, stream or None,
+                                  out_accept or None, out_obstacles or None)
+
+
+def ss_filter_host(ctx, reads, refs, fmt, m, e, n, out_accept,
+                   out_obstacles) -> int:
+    return load().ss_filter_host(ctx, reads or None, refs or None, fmt, m, e,
+                                 n, out_accept or None, out_obstacles or None)
+
+
+def ss_sync(ctx, stream=0) -> int:
+    return load().ss_sync(ctx, stream or None)
+
+
+def ss_get_counters(ctx) -> Counters:
+    c = Counters()
+    _check(load().ss_get_counters(ctx, ctypes.byref(c)), "ss_get_counters")
+    return c
+
+
+# ---- torch marshalling ------------------------------------------------------
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Filter:
+    """A context bound to one CUDA device; methods take torch tensors."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.device = device
+        self.ctx = ss_create(device, workspace_bytes)
+
+    def close(self):
+        if self.ctx:
+            ss_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, ascii, m: int = 0, n: Optional[int] = None, offsets=None,
+             lengths=None, out=None, out_offsets=None, stream=None):
+        """ASCII (uint8, device) -> packed int32 words (device)."""
+        import torch
+        if offsets is None:
+            n = ascii.shape[0] if n is None else n
+            if out is None:
+                out = torch.empty(n * ss_packed_words(m), dtype=torch.int32,
+                                  device=ascii.device)
+        else:
+            n = lengths.shape[0]
+        rc = ss_pack(self.ctx, _ptr(ascii), _ptr(offsets), _ptr(lengths), m,
+                     n, _ptr(out), _ptr(out_offsets), _stream_handle(stream))
+        _check(rc, "ss_pack")
+        return out
+
+    def filter(self, reads, refs, *, m: int = 0, e: int = 0, n=None,
+               fmt: int = SS_FMT_PACKED2, offsets=None, lengths=None, E=None,
+               flags: int = SS_MODE_AUTO, out_accept=None,
+               out_obstacles=None, stream=None, sync: bool = False):
+        """Filter device pairs; returns (accept uint8, obstacles int32)."""
+        import torch
+        if n is None:
+            n = lengths.shape[0] if lengths is not None else reads.shape[0]
+        dev = reads.device
+        if out_accept is None:
+            out_accept = torch.empty(n, dtype=torch.uint8, device=dev)
+        if out_obstacles is None:
+            out_obstacles = torch.empty(n, dtype=torch.int32, device=dev)
+        rc = ss_filter_batch(self.ctx, _ptr(reads), _ptr(refs), fmt,
+                             _ptr(offsets), _ptr(lengths), m, _ptr(E), e, n,
+                             flags, _stream_handle(stream), _ptr(out_accept),
+                             _ptr(out_obstacles))
+        _check(rc, "ss_filter_batch")
+        if sync:
+            self.sync(stream)
+        return out_accept, out_obstacles
+
+    def filter_host(self, reads, refs, *, m: int, e: int,
+                    fmt: int = SS_FMT_ASCII, out_accept=None,
+                    out_obstacles=None):
+        """Host (CPU, ideally pinned) tensors in and out."""
+        import torch
+        n = reads.shape[0]
+        if out_accept is None:
+            out_accept = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+        if out_obstacles is None:
+            out_obstacles = torch.empty(n, dtype=torch.int32,
+                                        pin_memory=True)
+        rc = ss_filter_host(self.ctx, _ptr(reads), _ptr(refs), fmt, m, e, n,
+                            _ptr(out_accept), _ptr(out_obstacles))
+        _check(rc, "ss_filter_host")
+        return out_accept, out_obstacles
+
+    def sync(self, stream=None):
+        """Wait for the stream (default: torch's current stream) and raise
+        any error the kernels latched."""
+        _check(ss_sync(self.ctx, _stream_handle(stream)), "ss_sync")
+
+    def counters(self) -> Counters:
+        return ss_get_counters(self.ctx)

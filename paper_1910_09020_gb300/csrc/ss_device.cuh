@@ -1,0 +1,51 @@
+// ss_device.cuh -- device-side helpers shared by the filter kernels.
+//
+// Packed format (SS_FMT_PACKED2, include/ss.h): 16 bases per uint32; bit t
+// holds code bit 0 of base t and bit 16+t holds code bit 1.  The kernels work
+// on "bit planes" of 32 columns: lo32/hi32 hold code bits 0/1 of 32
+// consecutive bases, so one XOR per plane compares 32 bases at once.
+#pragma once
+#include <cstdint>
+
+namespace ssk {
+
+// Device status bits latched in the context (returned by ss_sync).
+constexpr int kStatusInvalidBase = 1;
+constexpr int kStatusInvalidArg = 2;
+constexpr int kStatusTimeout = 4;
+
+// Two packed words (bases 32k..32k+15 and 32k+16..32k+31) -> the two
+// 32-column planes of word k.
+__device__ __forceinline__ void planes_of(uint32_t p0, uint32_t p1,
+                                          uint32_t &lo, uint32_t &hi)
+{
+    lo = __byte_perm(p0, p1, 0x5410);  // low halves: code bit 0
+    hi = __byte_perm(p0, p1, 0x7632);  // high halves: code bit 1
+}
+
+// Bits t >= lim of a 32-column word set (lim <= 0: all, lim >= 32: none).
+__device__ __forceinline__ uint32_t mask_from(int lim)
+{
+    return lim <= 0 ? 0xffffffffu : (lim >= 32 ? 0u : (0xffffffffu << lim));
+}
+
+// Bits t < lim set (lim <= 0: none, lim >= 32: all).
+__device__ __forceinline__ uint32_t mask_below(int lim)
+{
+    return lim <= 0 ? 0u : (lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u));
+}
+
+// ceil(2^32 / d) for d >= 2 (0 for d <= 1, where fast_div returns x):
+// __umulhi(x, magic) equals x / d whenever x * d < 2^32.
+__host__ __device__ inline uint32_t div_magic(uint32_t d)
+{
+    return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d);
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t x, uint32_t d,
+                                             uint32_t magic)
+{
+    return d <= 1 ? x : __umulhi(x, magic);
+}
+
+}  // namespace ssk

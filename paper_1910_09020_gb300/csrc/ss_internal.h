@@ -1,0 +1,37 @@
+// ss_internal.h -- host-side launch entry points of the kernels (not ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ssk {
+
+struct RwUniformArgs;
+
+// Largest E and m served by the thread-per-pair row-wise kernel (K3a).
+constexpr int kRwMaxE = 31;
+constexpr int kRwMaxM = 1024;
+constexpr int kRwThreads = 128;
+
+cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,
+                              uint32_t *out, int *status, cudaStream_t st);
+cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
+                               const int32_t *lengths, int64_t n,
+                               uint32_t *out, const int64_t *out_offsets,
+                               int *status, int sm_count, cudaStream_t st);
+
+// K3a plain launch for 0 <= E <= kRwMaxE, m <= kRwMaxM.
+cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
+                              const uint32_t *refs, int64_t n, int32_t m,
+                              uint8_t *acc, int32_t *obs, cudaStream_t st);
+
+// Per-translation-unit dispatchers (E ranges).
+cudaError_t launch_rw_uniform_e0(int E, const RwUniformArgs &a, size_t smem,
+                                 unsigned grid, cudaStream_t st);
+cudaError_t launch_rw_uniform_e1(int E, const RwUniformArgs &a, size_t smem,
+                                 unsigned grid, cudaStream_t st);
+cudaError_t launch_rw_uniform_e2(int E, const RwUniformArgs &a, size_t smem,
+                                 unsigned grid, cudaStream_t st);
+cudaError_t launch_rw_uniform_e3(int E, const RwUniformArgs &a, size_t smem,
+                                 unsigned grid, cudaStream_t st);
+
+}  // namespace ssk

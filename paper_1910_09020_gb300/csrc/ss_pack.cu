@@ -1,0 +1,164 @@
+// ss_pack.cu -- K1: ASCII bases -> SS_FMT_PACKED2 (2 bits per base).
+//
+// Eq. 1 only ever asks whether two bases are equal, so the filter works on a
+// 2-bit code of each base.  The code is computed arithmetically from the
+// ASCII byte: with v = byte | 0x20 (lower case), bit 0 = bit1(v) ^ bit2(v)
+// and bit 1 = bit2(v) ^ bit3(v), which maps a/c/g/t to 0/1/2/3.  A byte is
+// valid iff v equals the canonical letter of its code; anything else latches
+// kStatusInvalidBase.  Four bytes are handled per 32-bit lane operation.
+//
+// One thread writes one output word (16 bases); the kernel is bound by HBM
+// bandwidth (16 bytes read, 4 written per word).
+#include <cstdint>
+
+#include "ss_device.cuh"
+#include "ss_internal.h"
+
+namespace ssk {
+
+// Four ASCII bytes -> 4 code-bit-0 bits, 4 code-bit-1 bits; false if any
+// byte is not a base.  Missing bytes must be passed as 'A'.
+__device__ __forceinline__ bool codes4(uint32_t x, uint32_t &lo4,
+                                       uint32_t &hi4)
+{
+    const uint32_t v = x | 0x20202020u;
+    const uint32_t k0 = ((v >> 1) ^ (v >> 2)) & 0x01010101u;
+    const uint32_t k1 = ((v >> 2) ^ (v >> 3)) & 0x01010101u;
+    // canonical lower-case letter per code: 'a' + {0, 2, 6, 19}[code]
+    const uint32_t canon =
+        0x61616161u + (k0 << 1) + k1 * 6u + (k0 & k1) * 11u;
+    // gather bits at 0, 8, 16, 24 into bits 0..3 (no carries can occur)
+    lo4 = (k0 * 0x10204080u) >> 28;
+    hi4 = (k1 * 0x10204080u) >> 28;
+    return v == canon;
+}
+
+// Pack up to 16 bases starting at src (len in 1..16).
+__device__ __forceinline__ uint32_t pack16(const uint8_t *__restrict__ src,
+                                           int len, bool aligned4,
+                                           bool &valid)
+{
+    uint32_t w[4];
+    if (len == 16 && aligned4) {
+        const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            w[q] = __ldg(s4 + q);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = q * 4 + b;
+                const uint32_t c = j < len ? (uint32_t)__ldg(src + j) : 0x41u;
+                x |= c << (8 * b);
+            }
+            w[q] = x;
+        }
+    }
+    uint32_t lo = 0, hi = 0;
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t l4, h4;
+        ok &= codes4(w[q], l4, h4);
+        lo |= l4 << (4 * q);
+        hi |= h4 << (4 * q);
+    }
+    valid = ok;
+    return lo | (hi << 16);
+}
+
+// Fixed stride: pair p at byte p*m, output at word p*w16.
+__global__ void k_pack_fixed(const uint8_t *__restrict__ ascii, int64_t n,
+                             int32_t m, int32_t w16, uint32_t w16_magic,
+                             uint32_t *__restrict__ out, int *status)
+{
+    const int64_t total = n * (int64_t)w16;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    if (g0 >= total)
+        return;
+    // pair/word of the block's first word; the rest by 32-bit magic division
+    const int64_t p0 = g0 / w16;
+    const uint32_t w0 = (uint32_t)(g0 - p0 * w16);
+    const int64_t g = g0 + threadIdx.x;
+    bool bad = false;
+    if (g < total) {
+        const uint32_t off = w0 + threadIdx.x;
+        const uint32_t dp = fast_div(off, (uint32_t)w16, w16_magic);
+        const int64_t p = p0 + dp;
+        const int w = (int)(off - dp * (uint32_t)w16);
+        const uint8_t *src = ascii + p * (int64_t)m + (int64_t)w * 16;
+        const int len = min(16, m - w * 16);
+        bool valid;
+        out[g] = pack16(src, len, ((uintptr_t)src & 3) == 0, valid);
+        bad = !valid;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+        atomicOr(status, kStatusInvalidBase);
+}
+
+// Per-pair offsets and lengths: one warp per pair, lanes over its words.
+__global__ void k_pack_varlen(const uint8_t *__restrict__ ascii,
+                              const int64_t *__restrict__ offsets,
+                              const int32_t *__restrict__ lengths, int64_t n,
+                              uint32_t *__restrict__ out,
+                              const int64_t *__restrict__ out_offsets,
+                              int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool bad = false;
+    for (int64_t p = warp; p < n; p += nwarps) {
+        const int32_t m = lengths[p];
+        if (m <= 0)
+            continue;
+        const uint8_t *src = ascii + offsets[p];
+        uint32_t *dst = out + out_offsets[p];
+        const int w16 = (m + 15) >> 4;
+        for (int w = lane; w < w16; w += 32) {
+            const uint8_t *s = src + (int64_t)w * 16;
+            const int len = min(16, m - w * 16);
+            bool valid;
+            dst[w] = pack16(s, len, ((uintptr_t)s & 3) == 0, valid);
+            bad |= !valid;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0)
+        atomicOr(status, kStatusInvalidBase);
+}
+
+cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,
+                              uint32_t *out, int *status, cudaStream_t st)
+{
+    if (n <= 0 || m <= 0)
+        return cudaSuccess;
+    const int32_t w16 = (m + 15) / 16;
+    const int64_t total = n * (int64_t)w16;
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    k_pack_fixed<<<(unsigned)blocks, threads, 0, st>>>(
+        ascii, n, m, w16, div_magic((uint32_t)w16), out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
+                               const int32_t *lengths, int64_t n,
+                               uint32_t *out, const int64_t *out_offsets,
+                               int *status, int sm_count, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int threads = 256;
+    int64_t blocks = (n * 32 + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count * 8;
+    if (blocks > cap)
+        blocks = cap;
+    k_pack_varlen<<<(unsigned)blocks, threads, 0, st>>>(
+        ascii, offsets, lengths, n, out, out_offsets, status);
+    return cudaGetLastError();
+}
+
+}  // namespace ssk

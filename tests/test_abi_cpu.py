@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/ss.h
+declares; host-only argument checks (no kernel launches, no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1910_09020_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(ss_\w+)\s*\(", text,
+                            flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_builds_and_loads():
+    path = build.build()
+    assert os.path.exists(path)
+    lib = binding.load()
+    assert isinstance(lib, ctypes.CDLL)
+
+
+def test_every_declared_symbol_is_exported():
+    lib = binding.load()
+    decl = declared_functions()
+    assert len(decl) >= 10
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(binding.EXPORTED) == sorted(
+        n for n in decl if n in binding.EXPORTED)
+    assert set(decl) <= set(binding.EXPORTED), set(decl) - set(binding.EXPORTED)
+
+
+def test_host_only_functions():
+    assert binding.ss_version() >= 100
+    assert binding.ss_packed_words(0) == 0
+    assert binding.ss_packed_words(1) == 1
+    assert binding.ss_packed_words(16) == 1
+    assert binding.ss_packed_words(17) == 2
+    assert binding.ss_packed_words(100000) == 6250
+    assert "A/C/G/T" in binding.strerror(binding.SS_ERR_INVALID_BASE)
+    assert binding.strerror(12345) == "unknown status"
+
+
+def test_null_context_rejected():
+    lib = binding.load()
+    assert binding.ss_filter_batch(0, 1, 1, 0, 0, 0, 10, 0, 1, 5, 0, 0, 1,
+                                   1) == binding.SS_ERR_INVALID_ARG
+    assert binding.ss_sync(0) == binding.SS_ERR_INVALID_ARG
+    assert lib.ss_destroy(None) == binding.SS_OK
+
+
+def test_create_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = binding.load().ss_create(ctypes.byref(h), 0, 0)
+    assert rc in (binding.SS_ERR_CUDA, binding.SS_ERR_INVALID_ARG)
+    assert not h.value

@@ -1,0 +1,158 @@
+"""GPU parity of the pack kernel and the plain (uniform m, E) filter against
+the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import (FMT_ASCII, FMT_PACKED2, assert_same, gpu_filter_fixed,
+                      oracle_fixed, recipes, to_dev, torch_cuda)
+from paper_1910_09020_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    torch_cuda()
+    f = binding.Filter(0)
+    yield f
+    f.close()
+
+
+# ---- K1 pack ------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [1, 15, 16, 17, 31, 33, 100, 150, 250, 1000])
+def test_pack_matches_reference_packer(F, m):
+    reads, _ = synth.pairs_fixed(101, 0, 300, m, synth.SHORT_UNIFORM_K)
+    rng = np.random.default_rng(m)
+    lower = rng.random(reads.shape) < 0.3
+    reads = np.where(lower, reads | 0x20, reads).astype(np.uint8)
+    packed = F.pack(to_dev(reads.reshape(-1)), m=m, n=300)
+    F.sync()
+    got = packed.cpu().numpy().view(np.uint32).reshape(300, -1)
+    for p in range(300):
+        want = oracle.pack_reference(reads[p].tobytes())
+        assert (got[p] == want).all(), p
+
+
+def test_pack_varlen_matches_reference_packer(F):
+    torch = torch_cuda()
+    L = synth.log_uniform(5, 0, 200, 1, 3000)
+    reads, _, off = synth.pairs_varlen(5, 0, L, synth.rate_recipe(0.1))
+    words = (L.astype(np.int64) + 15) // 16
+    poff = np.zeros(len(L) + 1, np.int64)
+    np.cumsum(words, out=poff[1:])
+    out = torch.zeros(int(poff[-1]) + 1, dtype=torch.int32, device="cuda")
+    F.pack(to_dev(reads), offsets=to_dev(off), lengths=to_dev(L), out=out,
+           out_offsets=to_dev(poff))
+    F.sync()
+    got = out.cpu().numpy().view(np.uint32)
+    for p in range(len(L)):
+        seq = reads[off[p]:off[p] + L[p]].tobytes()
+        want = oracle.pack_reference(seq)
+        assert (got[poff[p]:poff[p + 1]] == want).all(), p
+
+
+def test_pack_invalid_base_latches(F):
+    reads, _ = synth.pairs_fixed(3, 0, 64, 100, synth.SHORT_UNIFORM_K)
+    reads[17, 55] = ord("N")
+    F.pack(to_dev(reads.reshape(-1)), m=100, n=64)
+    with pytest.raises(binding.SSError) as ei:
+        F.sync()
+    assert ei.value.code == binding.SS_ERR_INVALID_BASE
+    F.sync()  # cleared
+
+
+# ---- plain filter -----------------------------------------------------------------
+
+def test_worked_example(F):
+    """Fig. 2: R = GGTGCAGAGCTC, Q = GGTGAGAGTTGT, E = 3 -> 3 obstacles,
+    accept."""
+    Q = np.frombuffer(b"GGTGAGAGTTGT", np.uint8).reshape(1, 12)
+    R = np.frombuffer(b"GGTGCAGAGCTC", np.uint8).reshape(1, 12)
+    for fmt in (FMT_ASCII, FMT_PACKED2):
+        acc, obs = gpu_filter_fixed(F, Q, R, 3, fmt)
+        assert (acc[0], obs[0]) == (1, 3)
+
+
+def test_config1_all_pairs(F):
+    """10,000 pairs of 100 bp, k ~ U{0..10} edits, ASCII input, E = 5."""
+    reads, refs = synth.pairs_fixed(1910_09020 + 1, 0, 10000, 100,
+                                    synth.SHORT_UNIFORM_K)
+    acc, obs = gpu_filter_fixed(F, reads, refs, 5, FMT_ASCII)
+    oacc, oobs = oracle_fixed(reads, refs, 5)
+    assert_same(acc, obs, oacc, oobs, "config 1")
+    assert 0 < oacc.mean() < 1
+
+
+SIZES = [1, 2, 5, 31, 32, 33, 63, 64, 65, 100, 127, 150, 250, 511, 1000, 1024]
+
+
+@pytest.mark.parametrize("m", SIZES)
+def test_uniform_parity_all_E(F, m):
+    """Every E the plain kernel serves (0..31), several tiles (n = 777, a
+    ragged last CTA), three edit recipes."""
+    n = 777 if m <= 256 else 260
+    for name, rec in recipes().items():
+        reads, refs = synth.pairs_fixed(7 + m, 0, n, m, rec)
+        for E in list(range(0, 12)) + [15, 16, 20, 25, 31]:
+            acc, obs = gpu_filter_fixed(F, reads, refs, E)
+            oacc, oobs = oracle_fixed(reads, refs, E)
+            assert_same(acc, obs, oacc, oobs, f"m={m} E={E} {name}")
+
+
+def test_edge_cases(F):
+    rng = np.random.default_rng(0)
+    m = 100
+    base = synth.pairs_fixed(9, 0, 4, m, synth.SHORT_UNIFORM_K)[0]
+    allA = np.full((1, m), ord("A"), np.uint8)
+    allC = np.full((1, m), ord("C"), np.uint8)
+    first = base[:1].copy()
+    first[0, 0] = ord("A") if first[0, 0] != ord("A") else ord("C")
+    last = base[:1].copy()
+    last[0, -1] = ord("A") if last[0, -1] != ord("A") else ord("C")
+    reads = np.concatenate([base[:1], allA, base[:1], base[:1]])
+    refs = np.concatenate([base[:1], allC, first, last])
+    for E in (0, 1, 2, 5, 31):
+        acc, obs = gpu_filter_fixed(F, reads, refs, E)
+        oacc, oobs = oracle_fixed(reads, refs, E)
+        assert_same(acc, obs, oacc, oobs, f"edges E={E}")
+    # E >= m: always accepted
+    for m2 in (1, 3, 7, 20):
+        r, f = synth.pairs_fixed(11, 0, 200, m2, synth.SHORT_POISSON)
+        for E in (m2, m2 + 1, 31):
+            acc, obs = gpu_filter_fixed(F, r, f, E)
+            oacc, oobs = oracle_fixed(r, f, E)
+            assert_same(acc, obs, oacc, oobs, f"E>=m m={m2} E={E}")
+            assert acc.all()
+
+
+def test_empty_and_zero_length(F):
+    torch = torch_cuda()
+    z = torch.empty(0, dtype=torch.uint8, device="cuda")
+    acc, obs = F.filter(z, z, m=100, e=3, n=0)
+    assert acc.numel() == 0
+    one = torch.zeros(8, dtype=torch.uint8, device="cuda")
+    acc, obs = F.filter(one, one, m=0, e=2, n=8, fmt=FMT_ASCII, sync=True)
+    assert acc.cpu().tolist() == [1] * 8 and obs.cpu().tolist() == [0] * 8
+
+
+def test_invalid_base_through_filter(F):
+    reads, refs = synth.pairs_fixed(4, 0, 300, 100, synth.SHORT_POISSON)
+    refs[299, 99] = ord("x")
+    with pytest.raises(binding.SSError) as ei:
+        gpu_filter_fixed(F, reads, refs, 4, FMT_ASCII)
+    assert ei.value.code == binding.SS_ERR_INVALID_BASE
+
+
+def test_filter_host_matches_device(F):
+    """ss_filter_host (host buffers, chunked copy/compute pipeline)."""
+    torch = torch_cuda()
+    reads, refs = synth.pairs_fixed(21, 0, 5000, 150, synth.rate_recipe(0.12))
+    hq = torch.from_numpy(reads.reshape(-1).copy()).pin_memory()
+    hr = torch.from_numpy(refs.reshape(-1).copy()).pin_memory()
+    hq2 = hq.view(5000, 150)
+    hr2 = hr.view(5000, 150)
+    acc, obs = F.filter_host(hq2, hr2, m=150, e=7, fmt=FMT_ASCII)
+    oacc, oobs = oracle_fixed(reads, refs, 7)
+    assert_same(acc.numpy(), obs.numpy(), oacc, oobs, "filter_host")
