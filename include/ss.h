@@ -120,16 +120,18 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
                     int32_t e, int64_t n, int flags, void *stream,
                     uint8_t *out_accept, int32_t *out_obstacles);
 
-/* Same as ss_filter_batch for fixed-stride pairs of uniform m and E held in
- * HOST memory: the library streams chunks host -> device, packs (ASCII) and
- * filters them, and copies the results back into host out_accept /
- * out_obstacles, overlapping copies with compute on two internal streams.
- * Synchronous: returns when the host outputs are written.  Pinned host
- * buffers give the full copy bandwidth.  Returns SS_OK or an error (device
- * errors included). */
+/* Fixed-stride pairs of uniform length m held in HOST memory, filtered at
+ * each of the n_e thresholds of the host array e_list (a threshold sweep as
+ * in Section 3.2 needs the pairs copied once).  The library streams chunks
+ * host -> device, packs them (ASCII), runs one plain filter launch per
+ * threshold and copies the results back, overlapping copies and compute on
+ * two internal streams.  Outputs are HOST arrays laid out [n_e][n]:
+ * out_accept[t * n + p], out_obstacles[t * n + p].  Synchronous: returns
+ * when the host outputs are written (device errors included).  Pinned host
+ * buffers give the full copy bandwidth. */
 int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
-                   int format, int32_t m, int32_t e, int64_t n,
-                   uint8_t *out_accept, int32_t *out_obstacles);
+                   int format, int32_t m, const int32_t *e_list, int n_e,
+                   int64_t n, uint8_t *out_accept, int32_t *out_obstacles);
 
 /* Wait for all work on `stream` (NULL = default stream) and for the
  * context's internal streams, and return the first

@@ -81,7 +81,8 @@ def load(build_if_needed: bool = True):
     lib.ss_pack.argtypes = [P, P, P, P, I32, I64, P, P, P]
     lib.ss_filter_batch.argtypes = [P, P, P, ctypes.c_int, P, P, I32, P, I32,
                                     I64, ctypes.c_int, P, P, P]
-    lib.ss_filter_host.argtypes = [P, P, P, ctypes.c_int, I32, I32, I64, P, P]
+    lib.ss_filter_host.argtypes = [P, P, P, ctypes.c_int, I32, P,
+                                   ctypes.c_int, I64, P, P]
     lib.ss_sync.argtypes = [P, P]
     lib.ss_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
     for name in EXPORTED:
@@ -135,10 +136,11 @@ def ss_filter_batch(ctx, reads, refs, fmt, offsets, lengths, m, E, e, n,
                                   out_accept or None, out_obstacles or None)
 
 
-def ss_filter_host(ctx, reads, refs, fmt, m, e, n, out_accept,
+def ss_filter_host(ctx, reads, refs, fmt, m, e_list, n_e, n, out_accept,
                    out_obstacles) -> int:
-    return load().ss_filter_host(ctx, reads or None, refs or None, fmt, m, e,
-                                 n, out_accept or None, out_obstacles or None)
+    return load().ss_filter_host(ctx, reads or None, refs or None, fmt, m,
+                                 e_list or None, n_e, n, out_accept or None,
+                                 out_obstacles or None)
 
 
 def ss_sync(ctx, stream=0) -> int:
@@ -226,20 +228,27 @@ class Filter:
             self.sync(stream)
         return out_accept, out_obstacles
 
-    def filter_host(self, reads, refs, *, m: int, e: int,
+    def filter_host(self, reads, refs, *, m: int, e, n=None,
                     fmt: int = SS_FMT_ASCII, out_accept=None,
                     out_obstacles=None):
-        """Host (CPU, ideally pinned) tensors in and out."""
+        """Host (CPU, ideally pinned) tensors in and out.  ``e`` is one
+        threshold or a list; outputs have shape (len(e), n) for a list."""
         import torch
-        n = reads.shape[0]
+        n = reads.shape[0] if n is None else n
+        es = [int(e)] if isinstance(e, int) else [int(x) for x in e]
+        e_arr = (ctypes.c_int32 * len(es))(*es)
         if out_accept is None:
-            out_accept = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+            out_accept = torch.empty((len(es), n), dtype=torch.uint8,
+                                     pin_memory=True)
         if out_obstacles is None:
-            out_obstacles = torch.empty(n, dtype=torch.int32,
+            out_obstacles = torch.empty((len(es), n), dtype=torch.int32,
                                         pin_memory=True)
-        rc = ss_filter_host(self.ctx, _ptr(reads), _ptr(refs), fmt, m, e, n,
+        rc = ss_filter_host(self.ctx, _ptr(reads), _ptr(refs), fmt, m,
+                            ctypes.addressof(e_arr), len(es), n,
                             _ptr(out_accept), _ptr(out_obstacles))
         _check(rc, "ss_filter_host")
+        if isinstance(e, int):
+            return out_accept[0], out_obstacles[0]
         return out_accept, out_obstacles
 
     def sync(self, stream=None):

@@ -83,6 +83,25 @@ def build(force: bool = False, verbose_ptxas: bool = False,
     return LIB
 
 
+PEAKS_SRC = os.path.join(HERE, "peaks", "ss_peaks.cu")
+PEAKS_LIB = os.path.join(BUILD, "libss_peaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """Build the integer-pipe microbenchmark library."""
+    if (not force and os.path.exists(PEAKS_LIB)
+            and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC)):
+        return PEAKS_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc()] + NVCC_FLAGS + ["-shared", PEAKS_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv,
                 verbose_ptxas="--ptxas-v" in sys.argv))

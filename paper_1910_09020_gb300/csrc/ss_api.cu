@@ -312,14 +312,17 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
 }
 
 int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
-                   int format, int32_t m, int32_t e, int64_t n,
-                   uint8_t *out_accept, int32_t *out_obstacles)
+                   int format, int32_t m, const int32_t *e_list, int n_e,
+                   int64_t n, uint8_t *out_accept, int32_t *out_obstacles)
 {
-    if (!ctx || n < 0 || m < 0 || e < 0)
+    if (!ctx || n < 0 || m < 0 || n_e < 0 || (n_e > 0 && !e_list))
         return SS_ERR_INVALID_ARG;
     if (format != SS_FMT_ASCII && format != SS_FMT_PACKED2)
         return SS_ERR_INVALID_ARG;
-    if (n == 0)
+    for (int t = 0; t < n_e; ++t)
+        if (e_list[t] < 0)
+            return SS_ERR_INVALID_ARG;
+    if (n == 0 || n_e == 0)
         return SS_OK;
     if (!reads || !refs || !out_accept || !out_obstacles)
         return SS_ERR_INVALID_ARG;
@@ -331,7 +334,8 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     const size_t seq_in = format == SS_FMT_ASCII ? (size_t)m : (size_t)w16 * 4;
     const size_t packed = (size_t)w16 * 4;
     const size_t per_pair = 2 * seq_in +
-                            (format == SS_FMT_ASCII ? 2 * packed : 0) + 1 + 4;
+                            (format == SS_FMT_ASCII ? 2 * packed : 0) +
+                            (size_t)n_e * 5;
     // two pipeline slots, each holding one chunk
     int64_t chunk = (int64_t)(ctx->budget / (2 * per_pair + 1024));
     chunk = std::min<int64_t>(chunk, (int64_t)1 << 22);
@@ -341,8 +345,8 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     const size_t a_in = align_up((size_t)chunk * seq_in, 256);
     const size_t a_pk =
         format == SS_FMT_ASCII ? align_up((size_t)chunk * packed, 256) : 0;
-    const size_t a_acc = align_up((size_t)chunk, 256);
-    const size_t a_obs = align_up((size_t)chunk * 4, 256);
+    const size_t a_acc = align_up((size_t)chunk * n_e, 256);
+    const size_t a_obs = align_up((size_t)chunk * 4 * n_e, 256);
     const size_t slot = 2 * a_in + 2 * a_pk + a_acc + a_obs;
     int rc = ensure_workspace(ctx, 2 * slot);
     if (rc != SS_OK)
@@ -372,20 +376,26 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
             fq = pq;
             fr = pr;
         }
-        if (m == 0) {
-            SS_CUDA(cudaMemsetAsync(dacc, 1, (size_t)cn, st));
-            SS_CUDA(cudaMemsetAsync(dobs, 0, (size_t)cn * 4, st));
-        } else {
-            rc = filter_packed_uniform(ctx, fq, fr, m, e, cn, dacc, dobs, st);
-            if (rc != SS_OK)
-                return rc;
+        for (int t = 0; t < n_e; ++t) {
+            uint8_t *ta = dacc + (size_t)t * cn;
+            int32_t *to = dobs + (size_t)t * cn;
+            if (m == 0) {
+                SS_CUDA(cudaMemsetAsync(ta, 1, (size_t)cn, st));
+                SS_CUDA(cudaMemsetAsync(to, 0, (size_t)cn * 4, st));
+            } else {
+                rc = filter_packed_uniform(ctx, fq, fr, m, e_list[t], cn, ta,
+                                           to, st);
+                if (rc != SS_OK)
+                    return rc;
+            }
+            SS_CUDA(cudaMemcpyAsync(out_accept + (size_t)t * n + p0, ta,
+                                    (size_t)cn, cudaMemcpyDeviceToHost, st));
+            SS_CUDA(cudaMemcpyAsync(out_obstacles + (size_t)t * n + p0, to,
+                                    (size_t)cn * 4, cudaMemcpyDeviceToHost,
+                                    st));
         }
-        SS_CUDA(cudaMemcpyAsync(out_accept + p0, dacc, (size_t)cn,
-                                cudaMemcpyDeviceToHost, st));
-        SS_CUDA(cudaMemcpyAsync(out_obstacles + p0, dobs, (size_t)cn * 4,
-                                cudaMemcpyDeviceToHost, st));
     }
-    ctx->counters.pairs += n;
+    ctx->counters.pairs += n * n_e;
     SS_CUDA(cudaStreamSynchronize(ctx->hstream[0]));
     SS_CUDA(cudaStreamSynchronize(ctx->hstream[1]));
     return ss_sync(ctx, nullptr);

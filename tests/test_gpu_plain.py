@@ -156,3 +156,20 @@ def test_filter_host_matches_device(F):
     acc, obs = F.filter_host(hq2, hr2, m=150, e=7, fmt=FMT_ASCII)
     oacc, oobs = oracle_fixed(reads, refs, 7)
     assert_same(acc.numpy(), obs.numpy(), oacc, oobs, "filter_host")
+    # a threshold sweep from packed host input, several pipeline chunks
+    F2 = binding.Filter(0, workspace_bytes=1 << 20)
+    try:
+        dq = F2.pack(to_dev(reads.reshape(-1)), m=150, n=5000)
+        drf = F2.pack(to_dev(refs.reshape(-1)), m=150, n=5000)
+        F2.sync()
+        pq = dq.cpu().pin_memory()
+        pr = drf.cpu().pin_memory()
+        sweep = [0, 3, 7, 15]
+        acc, obs = F2.filter_host(pq, pr, m=150, e=sweep, n=5000,
+                                  fmt=FMT_PACKED2)
+        for t, E in enumerate(sweep):
+            oacc, oobs = oracle_fixed(reads, refs, E)
+            assert_same(acc[t].numpy(), obs[t].numpy(), oacc, oobs,
+                        f"filter_host sweep E={E}")
+    finally:
+        F2.close()
