@@ -110,10 +110,15 @@ int ss_pack(ss_ctx *ctx, const uint8_t *ascii, const int64_t *offsets,
  *   out_obstacles  device int32[n]: min(count, E+1); -1 for a pair with a
  *                  negative length or threshold (which also latches
  *                  SS_ERR_INVALID_ARG).
- * With offsets != NULL, lengths must be non-NULL.  ASCII input is packed
- * into context workspace first (fails with SS_ERR_OOM beyond the budget).
- * Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM, SS_ERR_UNSUPPORTED or
- * SS_ERR_CUDA. */
+ * With offsets != NULL, lengths must be non-NULL.  ASCII input must have a
+ * fixed stride (per-pair offsets need PACKED2: pack first with ss_pack); it
+ * is packed into context workspace chunk by chunk (SS_ERR_OOM if one pair
+ * does not fit the budget).  Per-pair lengths up to 131072 are supported
+ * for any E (longer pairs with E' > 31 latch SS_ERR_UNSUPPORTED and get
+ * obstacles = -1).  Calls that use the workspace (ASCII input, the bucketed
+ * form) must not overlap on the GPU for one context.
+ * Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM, SS_ERR_UNSUPPORTED (MODE_PLAIN
+ * on a shape the plain kernel does not cover) or SS_ERR_CUDA. */
 int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
                     int format, const int64_t *offsets,
                     const int32_t *lengths, int32_t m, const int32_t *E,
@@ -138,6 +143,32 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
  * device-side error latched since the previous ss_sync (then clear it), or
  * SS_OK. */
 int ss_sync(ss_ctx *ctx, void *stream);
+
+/* ---- batch scheduling of mixed batches (not in the paper: its GPU
+ * version runs one thread per pair, Section 2.6) --------------------------
+ * A batch with per-pair lengths or thresholds (or E > 31, or m > 1024) is
+ * filtered in the bucketed form: every pair is classified by (m, E') with
+ * E' = min(E, m-1), pairs are grouped by class and length (longest first),
+ * and one persistent kernel per class routes its pairs from an atomic work
+ * queue; the whole sequence is captured once in a CUDA graph and replayed
+ * for identical arguments.  Two knobs change speed, never results:
+ *   rw_max_e   15 or 31: largest E' routed with one thread per pair (above
+ *              it, one warp or one CTA per pair, rows across the lanes);
+ *   cw_subgrid 4, 8 or 16: columns evaluated across all rows per step by
+ *              the warp/CTA kernels before surviving runs are extended
+ *              32 columns at a time.
+ * ss_autotune() times every combination on the given batch (device
+ * pointers as in ss_filter_batch, outputs written) and keeps the fastest in
+ * the context; ss_set_tuning()/ss_get_tuning() set or read them directly.
+ * Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM or SS_ERR_CUDA; best_ms
+ * (may be NULL) receives the best time per pass. */
+int ss_set_tuning(ss_ctx *ctx, int rw_max_e, int cw_subgrid);
+int ss_get_tuning(const ss_ctx *ctx, int *rw_max_e, int *cw_subgrid);
+int ss_autotune(ss_ctx *ctx, const void *reads, const void *refs,
+                const int64_t *offsets, const int32_t *lengths, int32_t m,
+                const int32_t *E, int32_t e, int64_t n, void *stream,
+                uint8_t *out_accept, int32_t *out_obstacles, int reps,
+                float *best_ms);
 
 /* Counters of the context since creation (host-side accounting). */
 typedef struct ss_counters {

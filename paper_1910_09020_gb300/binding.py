@@ -36,7 +36,8 @@ SS_FLAG_NO_GRAPH = 16
 EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
-    "ss_sync", "ss_get_counters",
+    "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
+    "ss_autotune",
 )
 
 
@@ -85,6 +86,11 @@ def load(build_if_needed: bool = True):
                                    ctypes.c_int, I64, P, P]
     lib.ss_sync.argtypes = [P, P]
     lib.ss_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    lib.ss_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.ss_get_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    lib.ss_autotune.argtypes = [P, P, P, P, P, I32, P, I32, I64, P, P, P,
+                                ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     for name in EXPORTED:
         getattr(lib, name)  # raises AttributeError if a symbol is missing
     _lib = lib
@@ -151,6 +157,28 @@ def ss_get_counters(ctx) -> Counters:
     c = Counters()
     _check(load().ss_get_counters(ctx, ctypes.byref(c)), "ss_get_counters")
     return c
+
+
+def ss_set_tuning(ctx, rw_max_e: int, cw_subgrid: int) -> int:
+    return load().ss_set_tuning(ctx, rw_max_e, cw_subgrid)
+
+
+def ss_get_tuning(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().ss_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b)),
+           "ss_get_tuning")
+    return a.value, b.value
+
+
+def ss_autotune(ctx, reads, refs, offsets, lengths, m, E, e, n, stream,
+                out_accept, out_obstacles, reps=3):
+    best = ctypes.c_float()
+    rc = load().ss_autotune(ctx, reads or None, refs or None, offsets or None,
+                            lengths or None, m, E or None, e, n,
+                            stream or None, out_accept or None,
+                            out_obstacles or None, reps, ctypes.byref(best))
+    _check(rc, "ss_autotune")
+    return best.value
 
 
 # ---- torch marshalling ------------------------------------------------------
@@ -250,6 +278,29 @@ class Filter:
         if isinstance(e, int):
             return out_accept[0], out_obstacles[0]
         return out_accept, out_obstacles
+
+    def autotune(self, reads, refs, *, m: int = 0, e: int = 0, n=None,
+                 offsets=None, lengths=None, E=None, reps: int = 3,
+                 out_accept=None, out_obstacles=None, stream=None):
+        """Time every tuning of the bucketed form on this (packed) batch and
+        keep the fastest; returns (rw_max_e, cw_subgrid, best ms)."""
+        import torch
+        if n is None:
+            n = lengths.shape[0] if lengths is not None else reads.shape[0]
+        if out_accept is None:
+            out_accept = torch.empty(n, dtype=torch.uint8, device=reads.device)
+        if out_obstacles is None:
+            out_obstacles = torch.empty(n, dtype=torch.int32,
+                                        device=reads.device)
+        ms = ss_autotune(self.ctx, _ptr(reads), _ptr(refs), _ptr(offsets),
+                         _ptr(lengths), m, _ptr(E), e, n,
+                         _stream_handle(stream), _ptr(out_accept),
+                         _ptr(out_obstacles), reps)
+        rmax, k = ss_get_tuning(self.ctx)
+        return rmax, k, ms
+
+    def set_tuning(self, rw_max_e: int, cw_subgrid: int):
+        _check(ss_set_tuning(self.ctx, rw_max_e, cw_subgrid), "ss_set_tuning")
 
     def sync(self, stream=None):
         """Wait for the stream (default: torch's current stream) and raise

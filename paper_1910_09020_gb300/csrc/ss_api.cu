@@ -1,33 +1,63 @@
-// ss_api.cu -- the C ABI of include/ss.h: context, argument checks, workspace
-// and kernel dispatch.  Every step of the filter runs in the CUDA kernels;
-// this file only validates, allocates workspace and launches.
+// ss_api.cu -- the C ABI of include/ss.h: context, argument checks, workspace,
+// kernel dispatch, CUDA-graph cache and autotuner.  Every step of the filter
+// runs in the CUDA kernels; this file only validates, allocates workspace and
+// launches.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
+#include <vector>
 
 #include "../../include/ss.h"
+#include "ss_bucket.cuh"
 #include "ss_device.cuh"
 #include "ss_internal.h"
 #include "ss_rw.cuh"
 
+namespace {
+
+// Everything a captured graph of the bucketed path depends on.
+struct GraphKey {
+    const void *reads, *refs, *offsets, *lengths, *E, *acc, *obs, *ws;
+    int32_t m, e;
+    int64_t n;
+    int rw_max_e, cw_subgrid;
+    bool operator==(const GraphKey &o) const
+    {
+        return std::memcmp(this, &o, sizeof(GraphKey)) == 0;
+    }
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+};
+
+}  // namespace
+
 struct ss_ctx {
     int device = 0;
     int sm_count = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // graph capture and internal work
+    cudaStream_t side = nullptr;     // column-wise classes (forked)
     cudaStream_t hstream[2] = {nullptr, nullptr};  // ss_filter_host pipeline
-    int *d_status = nullptr;                        // latched device errors
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int *d_status = nullptr;         // latched device errors
     size_t budget = 0;
-    // workspace: one growable device block
-    void *ws = nullptr;
+    void *ws = nullptr;              // workspace: one growable device block
     size_t ws_bytes = 0;
+    ssk::TuneParams tune;
+    std::vector<GraphEntry> graphs;
+    uint64_t tick = 0;
     ss_counters counters{};
 };
 
 namespace {
+
+constexpr size_t kMaxGraphs = 16;
 
 int cuda_fail(cudaError_t e)
 {
@@ -40,6 +70,13 @@ int cuda_fail(cudaError_t e)
         cudaError_t e_ = (call);                                             \
         if (e_ != cudaSuccess)                                               \
             return cuda_fail(e_);                                            \
+    } while (0)
+
+#define SS_TRY(call)                                                         \
+    do {                                                                     \
+        int rc_ = (call);                                                    \
+        if (rc_ != SS_OK)                                                    \
+            return rc_;                                                      \
     } while (0)
 
 // Make the context's device current for the duration of a call.
@@ -60,8 +97,14 @@ struct DeviceGuard {
     }
 };
 
-// Grow the workspace to at least `bytes` (within the budget).  Only called
-// outside of stream capture; the caller synchronises before a regrow.
+void drop_graphs(ss_ctx *ctx)
+{
+    for (GraphEntry &g : ctx->graphs)
+        cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+// Grow the workspace to at least `bytes` (within the budget).
 int ensure_workspace(ss_ctx *ctx, size_t bytes)
 {
     if (bytes <= ctx->ws_bytes)
@@ -71,6 +114,7 @@ int ensure_workspace(ss_ctx *ctx, size_t bytes)
     if (ctx->ws) {
         // the old block may still be read by work on any caller stream
         SS_CUDA(cudaDeviceSynchronize());
+        drop_graphs(ctx);
         SS_CUDA(cudaFree(ctx->ws));
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
@@ -85,23 +129,124 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // NULL selects the CUDA default stream, as in other CUDA libraries (and as
 // torch's default stream handle is 0).
-cudaStream_t pick_stream(ss_ctx *, void *stream)
+cudaStream_t pick_stream(void *stream) { return (cudaStream_t)stream; }
+
+bool plain_ok(int32_t m, int32_t e)
 {
-    return (cudaStream_t)stream;
+    return e <= ssk::kRwMaxE && m <= ssk::kRwMaxM;
 }
 
-// Packed pairs, uniform m and E: the plain launch.
-int filter_packed_uniform(ss_ctx *ctx, const uint32_t *reads,
-                          const uint32_t *refs, int32_t m, int32_t e,
-                          int64_t n, uint8_t *acc, int32_t *obs,
-                          cudaStream_t st)
+// The bucketed persistent form over packed pairs, as a replayed CUDA graph
+// (or direct launches).  The workspace must already hold the bucket area at
+// its start.
+int run_bucketed(ss_ctx *ctx, const ssk::PairSet &ps, cudaStream_t st,
+                 bool use_graph)
 {
-    if (e <= ssk::kRwMaxE && m <= ssk::kRwMaxM) {
-        SS_CUDA(ssk::launch_rw_uniform(e, reads, refs, n, m, acc, obs, st));
+    ssk::BucketWs ws = ssk::bucket_ws_at(ctx->ws, ps.n);
+    int launches = 0;
+    if (!use_graph) {
+        SS_CUDA(ssk::launch_bucketed(ps, ws, ctx->tune, ctx->d_status,
+                                     ctx->sm_count, st, ctx->side, ctx->fork,
+                                     ctx->join, &launches));
+        ctx->counters.launches += launches;
+        return SS_OK;
+    }
+    GraphKey key;
+    std::memset(&key, 0, sizeof key);
+    key.reads = ps.reads;
+    key.refs = ps.refs;
+    key.offsets = ps.offsets;
+    key.lengths = ps.lengths;
+    key.E = ps.Es;
+    key.acc = ps.acc;
+    key.obs = ps.obs;
+    key.ws = ctx->ws;
+    key.m = ps.m;
+    key.e = ps.e;
+    key.n = ps.n;
+    key.rw_max_e = ctx->tune.rw_max_e;
+    key.cw_subgrid = ctx->tune.cw_subgrid;
+    for (GraphEntry &g : ctx->graphs)
+        if (g.key == key) {
+            g.last_use = ++ctx->tick;
+            SS_CUDA(cudaGraphLaunch(g.exec, st));
+            ctx->counters.graph_replays += 1;
+            return SS_OK;
+        }
+    // capture on the context's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured), replay on the caller's
+    cudaGraph_t graph = nullptr;
+    SS_CUDA(cudaStreamBeginCapture(ctx->stream,
+                                   cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = ssk::launch_bucketed(ps, ws, ctx->tune, ctx->d_status,
+                                          ctx->sm_count, ctx->stream,
+                                          ctx->side, ctx->fork, ctx->join,
+                                          &launches);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return cuda_fail(le != cudaSuccess ? le : ce);
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess)
+        return cuda_fail(ie);
+    if (ctx->graphs.size() >= kMaxGraphs) {
+        auto lru = std::min_element(
+            ctx->graphs.begin(), ctx->graphs.end(),
+            [](const GraphEntry &a, const GraphEntry &b) {
+                return a.last_use < b.last_use;
+            });
+        cudaGraphExecDestroy(lru->exec);
+        ctx->graphs.erase(lru);
+    }
+    ctx->graphs.push_back(GraphEntry{key, exec, ++ctx->tick});
+    ctx->counters.launches += launches;  // kernels per replay
+    SS_CUDA(cudaGraphLaunch(exec, st));
+    ctx->counters.graph_replays += 1;
+    return SS_OK;
+}
+
+// Packed pairs: plain launch when m and E are uniform and the plain kernel
+// covers them (unless the caller forces the bucketed form), else bucketed.
+int filter_packed(ss_ctx *ctx, const ssk::PairSet &ps, int flags,
+                  cudaStream_t st)
+{
+    const int mode = flags & 3;
+    const bool uniform = !ps.offsets && !ps.lengths && !ps.Es;
+    if (uniform && mode != SS_MODE_BUCKETED && plain_ok(ps.m, ps.e)) {
+        SS_CUDA(ssk::launch_rw_uniform(ps.e, ps.reads, ps.refs, ps.n, ps.m,
+                                       ps.acc, ps.obs, st));
         ctx->counters.launches += 1;
         return SS_OK;
     }
-    return SS_ERR_UNSUPPORTED;
+    if (mode == SS_MODE_PLAIN)
+        return uniform ? SS_ERR_UNSUPPORTED : SS_ERR_INVALID_ARG;
+    if (ps.n > INT32_MAX)
+        return SS_ERR_UNSUPPORTED;
+    return run_bucketed(ctx, ps, st, !(flags & SS_FLAG_NO_GRAPH));
+}
+
+ssk::PairSet make_pairs(const void *reads, const void *refs,
+                        const int64_t *offsets, const int32_t *lengths,
+                        int32_t m, const int32_t *E, int32_t e, int64_t n,
+                        uint8_t *acc, int32_t *obs)
+{
+    ssk::PairSet ps;
+    ps.reads = (const uint32_t *)reads;
+    ps.refs = (const uint32_t *)refs;
+    ps.offsets = offsets;
+    ps.lengths = lengths;
+    ps.Es = E;
+    ps.m = m;
+    ps.e = e;
+    ps.stride = (m + 15) / 16;
+    ps.n = n;
+    ps.acc = acc;
+    ps.obs = obs;
+    return ps;
 }
 
 }  // namespace
@@ -139,7 +284,7 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
 
 extern "C" {
 
-int ss_version(void) { return 100; }
+int ss_version(void) { return 200; }
 
 const char *ss_strerror(int code)
 {
@@ -180,9 +325,15 @@ int ss_create(ss_ctx **out, int device, size_t workspace_bytes)
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) !=
             cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) !=
+            cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->hstream[0], cudaStreamNonBlocking) !=
             cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->hstream[1], cudaStreamNonBlocking) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) !=
             cudaSuccess ||
         cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
@@ -191,6 +342,11 @@ int ss_create(ss_ctx **out, int device, size_t workspace_bytes)
         return SS_ERR_CUDA;
     }
     ctx->sm_count = prop.multiProcessorCount;
+    if (ssk::bucket_init(ctx->sm_count) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ss_destroy(ctx);
+        return SS_ERR_CUDA;
+    }
     *out = ctx;
     return SS_OK;
 }
@@ -200,19 +356,20 @@ int ss_destroy(ss_ctx *ctx)
     if (!ctx)
         return SS_OK;
     DeviceGuard g(ctx->device);
-    if (ctx->stream)
-        cudaStreamSynchronize(ctx->stream);
-    for (cudaStream_t s : ctx->hstream)
-        if (s) {
-            cudaStreamSynchronize(s);
+    cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    for (cudaStream_t s : {ctx->stream, ctx->side, ctx->hstream[0],
+                           ctx->hstream[1]})
+        if (s)
             cudaStreamDestroy(s);
-        }
+    if (ctx->fork)
+        cudaEventDestroy(ctx->fork);
+    if (ctx->join)
+        cudaEventDestroy(ctx->join);
     if (ctx->ws)
         cudaFree(ctx->ws);
     if (ctx->d_status)
         cudaFree(ctx->d_status);
-    if (ctx->stream)
-        cudaStreamDestroy(ctx->stream);
     delete ctx;
     return SS_OK;
 }
@@ -233,7 +390,7 @@ int ss_pack(ss_ctx *ctx, const uint8_t *ascii, const int64_t *offsets,
     if (!var && m < 0)
         return SS_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    cudaStream_t st = pick_stream(ctx, stream);
+    cudaStream_t st = pick_stream(stream);
     if (var)
         SS_CUDA(ssk::launch_pack_varlen(ascii, offsets, lengths, n, packed,
                                         packed_offsets, ctx->d_status,
@@ -251,10 +408,11 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
                     int32_t e, int64_t n, int flags, void *stream,
                     uint8_t *out_accept, int32_t *out_obstacles)
 {
-    (void)flags;
     if (!ctx || n < 0)
         return SS_ERR_INVALID_ARG;
     if (format != SS_FMT_ASCII && format != SS_FMT_PACKED2)
+        return SS_ERR_INVALID_ARG;
+    if ((flags & 3) == 3)
         return SS_ERR_INVALID_ARG;
     if (n == 0)
         return SS_OK;
@@ -267,35 +425,46 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
     DeviceGuard g(ctx->device);
     if (!g.ok)
         return SS_ERR_CUDA;
-    cudaStream_t st = pick_stream(ctx, stream);
+    cudaStream_t st = pick_stream(stream);
     ctx->counters.pairs += n;
 
-    const bool uniform = !offsets && !lengths && !E;
-    if (!uniform)
-        return SS_ERR_UNSUPPORTED;  // bucketed path: added with K2/K4
-    if (m == 0) {
+    const bool uniform_len = !offsets && !lengths;
+    if (uniform_len && m == 0) {
         // nothing to route: every pair accepted with 0 obstacles
         SS_CUDA(cudaMemsetAsync(out_accept, 1, (size_t)n, st));
         SS_CUDA(cudaMemsetAsync(out_obstacles, 0, (size_t)n * 4, st));
         return SS_OK;
     }
-    if (format == SS_FMT_PACKED2)
-        return filter_packed_uniform(ctx, (const uint32_t *)reads,
-                                     (const uint32_t *)refs, m, e, n,
-                                     out_accept, out_obstacles, st);
-    // ASCII: pack chunks into the workspace, then filter them.
+    const bool needs_bucket = !(uniform_len && !E && plain_ok(m, e)) ||
+                              (flags & 3) == SS_MODE_BUCKETED;
+    if (format == SS_FMT_PACKED2) {
+        if (needs_bucket)
+            SS_TRY(ensure_workspace(ctx, ssk::bucket_ws_bytes(n)));
+        return filter_packed(ctx,
+                             make_pairs(reads, refs, offsets, lengths, m, E, e,
+                                        n, out_accept, out_obstacles),
+                             flags, st);
+    }
+    // ASCII input: fixed stride only; packed chunk by chunk into workspace.
+    if (!uniform_len)
+        return SS_ERR_UNSUPPORTED;  // pack first with ss_pack
     const int64_t w16 = (m + 15) / 16;
-    const size_t per_pair = (size_t)2 * (size_t)w16 * 4;
-    int64_t chunk = (int64_t)((ctx->budget - std::min<size_t>(ctx->budget, 1024)) / per_pair);
+    const size_t per_pair =
+        (size_t)2 * (size_t)w16 * 4 + (needs_bucket ? 4 : 0);
+    const size_t fixed =
+        needs_bucket ? ssk::bucket_ws_bytes(0) + 2048 : 1024;
+    if (ctx->budget <= fixed)
+        return SS_ERR_OOM;
+    int64_t chunk = (int64_t)((ctx->budget - fixed) / per_pair);
     if (chunk < 1)
         return SS_ERR_OOM;
     chunk = std::min(chunk, n);
+    const size_t bws =
+        needs_bucket ? align_up(ssk::bucket_ws_bytes(chunk), 256) : 0;
     const size_t seq_bytes = align_up((size_t)chunk * w16 * 4, 256);
-    int rc = ensure_workspace(ctx, 2 * seq_bytes);
-    if (rc != SS_OK)
-        return rc;
-    uint32_t *pq = (uint32_t *)ctx->ws;
-    uint32_t *pr = (uint32_t *)((char *)ctx->ws + seq_bytes);
+    SS_TRY(ensure_workspace(ctx, bws + 2 * seq_bytes));
+    uint32_t *pq = (uint32_t *)((char *)ctx->ws + bws);
+    uint32_t *pr = (uint32_t *)((char *)ctx->ws + bws + seq_bytes);
     for (int64_t p0 = 0; p0 < n; p0 += chunk) {
         const int64_t cn = std::min(chunk, n - p0);
         const uint8_t *rq = (const uint8_t *)reads + p0 * (int64_t)m;
@@ -303,10 +472,11 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
         SS_CUDA(ssk::launch_pack_fixed(rq, cn, m, pq, ctx->d_status, st));
         SS_CUDA(ssk::launch_pack_fixed(rr, cn, m, pr, ctx->d_status, st));
         ctx->counters.launches += 2;
-        rc = filter_packed_uniform(ctx, pq, pr, m, e, cn, out_accept + p0,
-                                   out_obstacles + p0, st);
-        if (rc != SS_OK)
-            return rc;
+        const int32_t *Ec = E ? E + p0 : nullptr;
+        SS_TRY(filter_packed(ctx,
+                             make_pairs(pq, pr, nullptr, nullptr, m, Ec, e, cn,
+                                        out_accept + p0, out_obstacles + p0),
+                             flags | SS_FLAG_NO_GRAPH, st));
     }
     return SS_OK;
 }
@@ -319,9 +489,12 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
         return SS_ERR_INVALID_ARG;
     if (format != SS_FMT_ASCII && format != SS_FMT_PACKED2)
         return SS_ERR_INVALID_ARG;
-    for (int t = 0; t < n_e; ++t)
+    bool all_plain = true;
+    for (int t = 0; t < n_e; ++t) {
         if (e_list[t] < 0)
             return SS_ERR_INVALID_ARG;
+        all_plain &= plain_ok(m, e_list[t]);
+    }
     if (n == 0 || n_e == 0)
         return SS_OK;
     if (!reads || !refs || !out_accept || !out_obstacles)
@@ -335,9 +508,9 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     const size_t packed = (size_t)w16 * 4;
     const size_t per_pair = 2 * seq_in +
                             (format == SS_FMT_ASCII ? 2 * packed : 0) +
-                            (size_t)n_e * 5;
+                            (size_t)n_e * 5 + (all_plain ? 0 : 2);
     // two pipeline slots, each holding one chunk
-    int64_t chunk = (int64_t)(ctx->budget / (2 * per_pair + 1024));
+    int64_t chunk = (int64_t)(ctx->budget / (2 * per_pair + 2048));
     chunk = std::min<int64_t>(chunk, (int64_t)1 << 22);
     chunk = std::min(chunk, n);
     if (chunk < 1)
@@ -348,14 +521,17 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     const size_t a_acc = align_up((size_t)chunk * n_e, 256);
     const size_t a_obs = align_up((size_t)chunk * 4 * n_e, 256);
     const size_t slot = 2 * a_in + 2 * a_pk + a_acc + a_obs;
-    int rc = ensure_workspace(ctx, 2 * slot);
-    if (rc != SS_OK)
-        return rc;
+    // the bucket area (thresholds beyond the plain kernel) sits first
+    const size_t bws =
+        all_plain ? 0 : align_up(ssk::bucket_ws_bytes(chunk), 256);
+    if (bws + 2 * slot > ctx->budget)
+        return SS_ERR_OOM;
+    SS_TRY(ensure_workspace(ctx, bws + 2 * slot));
     for (int64_t p0 = 0, it = 0; p0 < n; p0 += chunk, ++it) {
         const int64_t cn = std::min(chunk, n - p0);
         const int sidx = (int)(it & 1);
         cudaStream_t st = ctx->hstream[sidx];
-        char *base = (char *)ctx->ws + sidx * slot;
+        char *base = (char *)ctx->ws + bws + sidx * slot;
         char *dq = base, *dr = base + a_in;
         uint32_t *pq = (uint32_t *)(base + 2 * a_in);
         uint32_t *pr = (uint32_t *)(base + 2 * a_in + a_pk);
@@ -383,10 +559,15 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
                 SS_CUDA(cudaMemsetAsync(ta, 1, (size_t)cn, st));
                 SS_CUDA(cudaMemsetAsync(to, 0, (size_t)cn * 4, st));
             } else {
-                rc = filter_packed_uniform(ctx, fq, fr, m, e_list[t], cn, ta,
-                                           to, st);
-                if (rc != SS_OK)
-                    return rc;
+                // the bucket area is shared: bucketed thresholds run on one
+                // stream at a time, so wait for the other slot first
+                if (!plain_ok(m, e_list[t]))
+                    SS_CUDA(cudaStreamSynchronize(ctx->hstream[sidx ^ 1]));
+                SS_TRY(filter_packed(ctx,
+                                     make_pairs(fq, fr, nullptr, nullptr, m,
+                                                nullptr, e_list[t], cn, ta,
+                                                to),
+                                     SS_FLAG_NO_GRAPH, st));
             }
             SS_CUDA(cudaMemcpyAsync(out_accept + (size_t)t * n + p0, ta,
                                     (size_t)cn, cudaMemcpyDeviceToHost, st));
@@ -406,9 +587,10 @@ int ss_sync(ss_ctx *ctx, void *stream)
     if (!ctx)
         return SS_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    cudaStream_t st = pick_stream(ctx, stream);
+    cudaStream_t st = pick_stream(stream);
     SS_CUDA(cudaStreamSynchronize(st));
     SS_CUDA(cudaStreamSynchronize(ctx->stream));
+    SS_CUDA(cudaStreamSynchronize(ctx->side));
     int flags = 0;
     SS_CUDA(cudaMemcpy(&flags, ctx->d_status, sizeof(int),
                        cudaMemcpyDeviceToHost));
@@ -418,6 +600,8 @@ int ss_sync(ss_ctx *ctx, void *stream)
             return SS_ERR_INVALID_BASE;
         if (flags & ssk::kStatusInvalidArg)
             return SS_ERR_INVALID_ARG;
+        if (flags & ssk::kStatusUnsupported)
+            return SS_ERR_UNSUPPORTED;
         if (flags & ssk::kStatusTimeout)
             return SS_ERR_TIMEOUT;
     }
@@ -430,6 +614,82 @@ int ss_get_counters(const ss_ctx *ctx, ss_counters *out)
         return SS_ERR_INVALID_ARG;
     *out = ctx->counters;
     return SS_OK;
+}
+
+int ss_set_tuning(ss_ctx *ctx, int rw_max_e, int cw_subgrid)
+{
+    if (!ctx || (rw_max_e != 15 && rw_max_e != 31) ||
+        (cw_subgrid != 4 && cw_subgrid != 8 && cw_subgrid != 16))
+        return SS_ERR_INVALID_ARG;
+    ctx->tune.rw_max_e = rw_max_e;
+    ctx->tune.cw_subgrid = cw_subgrid;
+    return SS_OK;
+}
+
+int ss_get_tuning(const ss_ctx *ctx, int *rw_max_e, int *cw_subgrid)
+{
+    if (!ctx || !rw_max_e || !cw_subgrid)
+        return SS_ERR_INVALID_ARG;
+    *rw_max_e = ctx->tune.rw_max_e;
+    *cw_subgrid = ctx->tune.cw_subgrid;
+    return SS_OK;
+}
+
+int ss_autotune(ss_ctx *ctx, const void *reads, const void *refs,
+                const int64_t *offsets, const int32_t *lengths, int32_t m,
+                const int32_t *E, int32_t e, int64_t n, void *stream,
+                uint8_t *out_accept, int32_t *out_obstacles, int reps,
+                float *best_ms)
+{
+    if (!ctx || n <= 0 || reps < 1 || !reads || !refs || !out_accept ||
+        !out_obstacles || (offsets && !lengths) || (!lengths && m < 0) ||
+        (!E && e < 0) || n > INT32_MAX)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick_stream(stream);
+    SS_TRY(ensure_workspace(ctx, ssk::bucket_ws_bytes(n)));
+    const ssk::PairSet ps = make_pairs(reads, refs, offsets, lengths, m, E, e,
+                                       n, out_accept, out_obstacles);
+    const ssk::TuneParams saved = ctx->tune;
+    ssk::TuneParams best = saved;
+    float best_t = 1e30f;
+    cudaEvent_t a, z;
+    SS_CUDA(cudaEventCreate(&a));
+    SS_CUDA(cudaEventCreate(&z));
+    int rc = SS_OK;
+    for (int rmax : {15, 31}) {
+        for (int k : {4, 8, 16}) {
+            ctx->tune.rw_max_e = rmax;
+            ctx->tune.cw_subgrid = k;
+            rc = run_bucketed(ctx, ps, st, false);  // warm-up
+            if (rc != SS_OK)
+                break;
+            cudaEventRecord(a, st);
+            for (int r = 0; r < reps && rc == SS_OK; ++r)
+                rc = run_bucketed(ctx, ps, st, false);
+            cudaEventRecord(z, st);
+            if (rc != SS_OK || cudaEventSynchronize(z) != cudaSuccess) {
+                if (rc == SS_OK)
+                    rc = SS_ERR_CUDA;
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, z);
+            ms /= reps;
+            if (ms < best_t) {
+                best_t = ms;
+                best = ctx->tune;
+            }
+        }
+        if (rc != SS_OK)
+            break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    ctx->tune = rc == SS_OK ? best : saved;
+    if (best_ms)
+        *best_ms = best_t;
+    return rc;
 }
 
 }  // extern "C"

@@ -7,30 +7,80 @@
 #pragma once
 #include <cstdint>
 
+// The routing functions are __host__ __device__ so that the test suite can
+// also compile them for the host and check their logic on the CPU; the
+// wrappers below are the device intrinsics on the GPU.
+#define SS_HD __host__ __device__ __forceinline__
+
 namespace ssk {
+
+SS_HD uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s)
+{
+#ifdef __CUDA_ARCH__
+    return __funnelshift_r(lo, hi, s);
+#else
+    return (uint32_t)(((((uint64_t)hi) << 32) | lo) >> (s & 31u));
+#endif
+}
+
+SS_HD uint32_t funnel_l(uint32_t lo, uint32_t hi, uint32_t s)
+{
+#ifdef __CUDA_ARCH__
+    return __funnelshift_l(lo, hi, s);
+#else
+    return (uint32_t)((((((uint64_t)hi) << 32) | lo) << (s & 31u)) >> 32);
+#endif
+}
+
+SS_HD int ffs32(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __ffs((int)x);
+#else
+    return __builtin_ffs((int)x);
+#endif
+}
+
+SS_HD int imax(int a, int b) { return a > b ? a : b; }
+SS_HD int imin(int a, int b) { return a < b ? a : b; }
+
+template <class T>
+SS_HD T ldg(const T *p)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
 
 // Device status bits latched in the context (returned by ss_sync).
 constexpr int kStatusInvalidBase = 1;
 constexpr int kStatusInvalidArg = 2;
 constexpr int kStatusTimeout = 4;
+constexpr int kStatusUnsupported = 8;
 
 // Two packed words (bases 32k..32k+15 and 32k+16..32k+31) -> the two
 // 32-column planes of word k.
-__device__ __forceinline__ void planes_of(uint32_t p0, uint32_t p1,
-                                          uint32_t &lo, uint32_t &hi)
+SS_HD void planes_of(uint32_t p0, uint32_t p1, uint32_t &lo, uint32_t &hi)
 {
+#ifdef __CUDA_ARCH__
     lo = __byte_perm(p0, p1, 0x5410);  // low halves: code bit 0
     hi = __byte_perm(p0, p1, 0x7632);  // high halves: code bit 1
+#else
+    lo = (p0 & 0xffffu) | (p1 << 16);
+    hi = (p0 >> 16) | (p1 & 0xffff0000u);
+#endif
 }
 
 // Bits t >= lim of a 32-column word set (lim <= 0: all, lim >= 32: none).
-__device__ __forceinline__ uint32_t mask_from(int lim)
+SS_HD uint32_t mask_from(int lim)
 {
     return lim <= 0 ? 0xffffffffu : (lim >= 32 ? 0u : (0xffffffffu << lim));
 }
 
 // Bits t < lim set (lim <= 0: none, lim >= 32: all).
-__device__ __forceinline__ uint32_t mask_below(int lim)
+SS_HD uint32_t mask_below(int lim)
 {
     return lim <= 0 ? 0u : (lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u));
 }

@@ -6,6 +6,9 @@
 namespace ssk {
 
 struct RwUniformArgs;
+struct PairSet;
+struct BucketWs;
+struct TuneParams;
 
 // Largest E and m served by the thread-per-pair row-wise kernel (K3a).
 constexpr int kRwMaxE = 31;
@@ -23,6 +26,19 @@ cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
 cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
                               const uint32_t *refs, int64_t n, int32_t m,
                               uint8_t *acc, int32_t *obs, cudaStream_t st);
+
+// K2 + K4: bucketed persistent form of a mixed batch.
+size_t bucket_ws_bytes(int64_t n);
+BucketWs bucket_ws_at(void *base, int64_t n);
+int cw_class_slice_words(int cls);
+// Kernel attributes and persistent grid sizes (once per process, called by
+// ss_create before any capture).
+cudaError_t bucket_init(int sm_count);
+cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
+                            const TuneParams &tp, int *status, int sm_count,
+                            cudaStream_t st, cudaStream_t side,
+                            cudaEvent_t fork, cudaEvent_t join,
+                            int *launches);
 
 // Per-translation-unit dispatchers (E ranges).
 cudaError_t launch_rw_uniform_e0(int E, const RwUniformArgs &a, size_t smem,

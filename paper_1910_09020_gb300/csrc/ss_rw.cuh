@@ -9,19 +9,26 @@
 // past it, until the row end is reached or the count exceeds E.
 //
 // GB300 mapping: each thread holds, for the 32-column word k it is routing
-// through, the 2E+1 maze row words Z_s (one register each, built with one
-// funnel shift per bit plane and two logic ops: the maze is built lazily word
-// by word, as in the implicit maze of Section 2.4).  The longest run from
+// through, the maze row words Z_s (one register each, built with one funnel
+// shift per bit plane and two logic ops: the maze is built lazily word by
+// word, as in the implicit maze of Section 2.4).  The longest run from
 // checkpoint c needs no per-row bit scan: with x_s = Z_s masked to columns
 // >= c, x_s | -x_s sets every bit at or above row s's first obstacle, so the
 // AND over rows has its lowest set bit at max_s(first obstacle) -- the end of
-// the longest escape segment -- found with one __ffs per iteration.  Rows
-// whose run crosses into the next word carry a "dead" mask (rows that already
-// met an obstacle since c) so that runs spanning words are exact.
+// the longest escape segment -- found with one find-first per iteration.
+// When a run crosses into the next word, the rows that already met an
+// obstacle since c are kept in a bitmask and count as all-obstacle rows
+// until the next obstacle is found, so runs spanning words are exact.
 //
-// Data: a CTA stages its pairs' packed words in shared memory, transposed
-// (word i of the CTA's pair t at [i * ld + t], ld = T + 1) so that the
-// per-thread reads are conflict-free.  Results are written coalesced.
+// Two launch forms share rw_route():
+//  * k_rw_uniform<E>: the plain launch (uniform m and E).  A CTA stages its
+//    pairs' packed words in shared memory, transposed (word i of the CTA's
+//    pair t at [i * ld + t], ld = T + 1) so per-thread reads are
+//    conflict-free; results are written coalesced.
+//  * k_rw_bucket<EMAX>: persistent launch over one bucket of a mixed batch
+//    (runtime E <= EMAX, any m); each thread reads its pair straight from
+//    global memory (contiguous words, L1-cached).  Rows with |s| > E are
+//    all-obstacle rows, which never bound the longest run.
 #pragma once
 #include <cstdint>
 
@@ -29,54 +36,66 @@
 
 namespace ssk {
 
-// 32-column planes of word k of a sequence stored transposed in shared
-// memory (packed word i at s[i * ld]).
-__device__ __forceinline__ void smem_planes(const uint32_t *s, int ld,
-                                            int w16, int k, uint32_t &lo,
-                                            uint32_t &hi)
-{
-    const int i = 2 * k;
-    const uint32_t p0 = i < w16 ? s[i * ld] : 0u;
-    const uint32_t p1 = i + 1 < w16 ? s[(i + 1) * ld] : 0u;
-    planes_of(p0, p1, lo, hi);
-}
+// Packed words of one sequence, transposed in shared memory (word i at
+// s[i * ld]).
+struct SmemSeq {
+    const uint32_t *s;
+    int ld;
+    int w16;
+    SS_HD void planes(int k, uint32_t &lo, uint32_t &hi) const
+    {
+        const int i = 2 * k;
+        const uint32_t p0 = i < w16 ? s[i * ld] : 0u;
+        const uint32_t p1 = i + 1 < w16 ? s[(i + 1) * ld] : 0u;
+        planes_of(p0, p1, lo, hi);
+    }
+};
 
-// Route one pair of length m; returns min(count, E+1).
-template <int E>
-__device__ __forceinline__ int rw_route(const uint32_t *sq,
-                                        const uint32_t *sr, int ld, int m,
-                                        int w16)
+// Packed words of one sequence in global memory.
+struct GlobalSeq {
+    const uint32_t *g;
+    int w16;
+    SS_HD void planes(int k, uint32_t &lo, uint32_t &hi) const
+    {
+        const int i = 2 * k;
+        const uint32_t p0 = i < w16 ? ldg(g + i) : 0u;
+        const uint32_t p1 = i + 1 < w16 ? ldg(g + i + 1) : 0u;
+        planes_of(p0, p1, lo, hi);
+    }
+};
+
+// Route one pair of length m with threshold E (E == EMAX when EXACT);
+// returns min(count, E+1).  Rows |s| > min(E, EMAX) are never built.
+template <int EMAX, bool EXACT, class Seq>
+SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E)
 {
-    constexpr int NR = 2 * E + 1;
+    constexpr int NR = 2 * EMAX + 1;
     const int W32 = (m + 31) >> 5;
-    uint32_t Z[NR], dead[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-        dead[r] = 0u;
+    uint32_t Z[NR];
+    uint64_t deadbits = 0;  // rows that met an obstacle since c (crossing)
 
     uint32_t qlo_p = 0u, qhi_p = 0u, qlo_c, qhi_c, qlo_n, qhi_n;
-    smem_planes(sq, ld, w16, 0, qlo_c, qhi_c);
-    smem_planes(sq, ld, w16, 1, qlo_n, qhi_n);
+    Qs.planes(0, qlo_c, qhi_c);
+    Qs.planes(1, qlo_n, qhi_n);
 
-    int c = 0;  // checkpoint column (0-based)
     int count = 0;
     bool finished = false;
     for (int k = 0; k < W32 && !finished; ++k) {
         const int base = k << 5;
         uint32_t rlo, rhi;
-        smem_planes(sr, ld, w16, k, rlo, rhi);
-        const bool edge = (k == 0) || (base + 32 + E > m);
+        Rs.planes(k, rlo, rhi);
+        const bool edge = (k == 0) || (base + 32 + EMAX > m);
         // Eq. 1 for the 32 columns of word k, every row.
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
-            const int s = r - E;
+            const int s = r - EMAX;
             uint32_t ql, qh;
             if (s >= 0) {
-                ql = __funnelshift_r(qlo_c, qlo_n, s);
-                qh = __funnelshift_r(qhi_c, qhi_n, s);
+                ql = funnel_r(qlo_c, qlo_n, s);
+                qh = funnel_r(qhi_c, qhi_n, s);
             } else {
-                ql = __funnelshift_l(qlo_p, qlo_c, -s);
-                qh = __funnelshift_l(qhi_p, qhi_c, -s);
+                ql = funnel_l(qlo_p, qlo_c, -s);
+                qh = funnel_l(qhi_p, qhi_c, -s);
             }
             uint32_t z = (ql ^ rlo) | (qh ^ rhi);
             if (edge) {
@@ -86,27 +105,41 @@ __device__ __forceinline__ int rw_route(const uint32_t *sq,
                     z |= mask_below(-s - base);
                 z |= mask_from((s > 0 ? m - s : m) - base);
             }
+            if (!EXACT && (s > E || -s > E))
+                z = 0xffffffffu;  // row outside this pair's 2E+1
             Z[r] = z;
         }
-        // Greedy routing inside word k.
-        uint32_t M = 0xffffffffu;  // columns >= checkpoint (c <= base here)
+        // Greedy routing inside word k (checkpoint c <= base on entry).
+        uint32_t M = 0xffffffffu;  // columns >= checkpoint
         for (;;) {
             uint32_t A = 0xffffffffu;
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t x = (Z[r] & M) | dead[r];
-                A &= x | (0u - x);
-            }
-            if (A == 0u) {
-                // a live row runs past the word end: keep only those rows
+            if (deadbits) {
+                // runs continued from the previous word: rows that already
+                // met an obstacle since the checkpoint do not count
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    const uint32_t x = (Z[r] & M) | dead[r];
-                    dead[r] = x ? 0xffffffffu : 0u;
+                    const uint32_t x = (Z[r] & M) |
+                                       (0u - (uint32_t)((deadbits >> r) & 1u));
+                    A &= x | (0u - x);
                 }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t x = Z[r] & M;
+                    A &= x | (0u - x);
+                }
+            }
+            if (A == 0u) {
+                // a live row runs past the word end: remember the others
+                uint64_t d = deadbits;
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    d |= (uint64_t)((Z[r] & M) != 0u) << r;
+                deadbits = d;
                 break;
             }
-            const int e = base + __ffs(A) - 1;  // end of the escape segment
+            deadbits = 0;  // an obstacle ends every run: fresh checkpoint
+            const int e = base + ffs32(A) - 1;  // end of the escape segment
             if (e >= m) {                       // reached the destination
                 finished = true;
                 break;
@@ -116,10 +149,7 @@ __device__ __forceinline__ int rw_route(const uint32_t *sq,
                 finished = true;
                 break;
             }
-            c = e + 1;                          // new checkpoint
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-                dead[r] = 0u;
+            const int c = e + 1;                // new checkpoint
             if (c >= base + 32)
                 break;
             M = 0xffffffffu << (c - base);
@@ -129,7 +159,7 @@ __device__ __forceinline__ int rw_route(const uint32_t *sq,
         qhi_p = qhi_c;
         qlo_c = qlo_n;
         qhi_c = qhi_n;
-        smem_planes(sq, ld, w16, k + 2, qlo_n, qhi_n);
+        Qs.planes(k + 2, qlo_n, qhi_n);
     }
     return count;
 }
@@ -170,8 +200,9 @@ __global__ void __launch_bounds__(128)
     }
     __syncthreads();
     if (threadIdx.x < np) {
-        const int cnt = rw_route<E>(sQ + threadIdx.x, sR + threadIdx.x, ld,
-                                    a.m, a.w16);
+        const SmemSeq q{sQ + threadIdx.x, ld, a.w16};
+        const SmemSeq r{sR + threadIdx.x, ld, a.w16};
+        const int cnt = rw_route<E, true>(q, r, a.m, E);
         a.acc[p0 + threadIdx.x] = (uint8_t)(cnt <= E);
         a.obs[p0 + threadIdx.x] = cnt;
     }

@@ -1,0 +1,44 @@
+"""Host build of the library's routing functions (test harness only)."""
+import ctypes
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+CSRC = os.path.join(ROOT, "paper_1910_09020_gb300", "csrc")
+SRC = os.path.join(HERE, "emu.cu")
+OUT = os.path.join(HERE, "_build", "libemu.so")
+_lib = None
+
+
+def _deps():
+    return [SRC] + [os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                    if f.endswith((".cuh", ".h"))]
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    stale = (not os.path.exists(OUT) or
+             any(os.path.getmtime(d) > os.path.getmtime(OUT) for d in _deps()))
+    if stale:
+        os.makedirs(os.path.dirname(OUT), exist_ok=True)
+        tmp = OUT + f".tmp{os.getpid()}"
+        nvcc = os.environ.get("NVCC", "nvcc")
+        if not os.path.exists(nvcc) and os.path.exists("/usr/local/cuda/bin/nvcc"):
+            nvcc = "/usr/local/cuda/bin/nvcc"
+        subprocess.check_call([
+            nvcc, "-std=c++17", "-O2", "-gencode",
+            "arch=compute_103a,code=sm_103a", "-Xcompiler", "-fPIC",
+            "-shared", "-I", CSRC, SRC, "-o", tmp])
+        os.replace(tmp, OUT)
+    lib = ctypes.CDLL(OUT)
+    P = ctypes.c_void_p
+    lib.emu_rw_exact.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
+    lib.emu_rw_runtime.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int]
+    lib.emu_cw.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.emu_class_of.argtypes = [ctypes.c_int, ctypes.c_int]
+    _lib = lib
+    return lib

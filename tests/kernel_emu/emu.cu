@@ -1,0 +1,99 @@
+// emu.cu -- TEST HARNESS: the library's routing functions compiled for the
+// host, so the CPU suite can check their logic against the oracle without a
+// GPU.  Not part of the library and never loaded by it; the GPU tests remain
+// the parity tests proper.
+#include <cstdint>
+#include <vector>
+
+#include "ss_cw.cuh"
+#include "ss_rw.cuh"
+
+using namespace ssk;
+
+namespace {
+
+template <int E>
+int exact_one(const uint32_t *q, const uint32_t *r, int m)
+{
+    const int w16 = (m + 15) / 16;
+    return rw_route<E, true>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E);
+}
+
+template <int... Es>
+int exact_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
+                   std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    ((E == Es ? (out = exact_one<Es>(q, r, m), 0) : 0), ...);
+    return out;
+}
+
+template <int EMAX>
+int runtime_one(const uint32_t *q, const uint32_t *r, int m, int E)
+{
+    const int w16 = (m + 15) / 16;
+    return rw_route<EMAX, false>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E);
+}
+
+template <int K>
+int cw_one(const uint32_t *q, const uint32_t *r, int m, int E)
+{
+    const int Ee = eff_threshold(m, E);
+    const CwLayout L = CwLayout::of(m, Ee);
+    std::vector<uint32_t> sm(L.words());
+    cw_stage(sm.data(), L, q, r, m, 0, 1);
+    const int nwords = (2 * Ee + 1 + 31) >> 5;
+    int c = 0, count = 0;
+    for (;;) {
+        int pstar = -1;
+        for (int w = 0; w < nwords; ++w)
+            pstar = imax(pstar, cw_word<K>(sm.data(), L, m, Ee, c, w));
+        if (pstar >= m)
+            break;
+        ++count;
+        if (count > E)
+            break;
+        c = pstar + 1;
+    }
+    return count;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Plain-kernel routine with compile-time E (0..31).
+int emu_rw_exact(const uint32_t *q, const uint32_t *r, int m, int E)
+{
+    return exact_dispatch(E, q, r, m, std::make_integer_sequence<int, 32>{});
+}
+
+// Bucketed row-wise routine: runtime E <= EMAX (1, 3, 7, 15, 31).
+int emu_rw_runtime(const uint32_t *q, const uint32_t *r, int m, int E,
+                   int emax)
+{
+    switch (emax) {
+    case 1: return runtime_one<1>(q, r, m, E);
+    case 3: return runtime_one<3>(q, r, m, E);
+    case 7: return runtime_one<7>(q, r, m, E);
+    case 15: return runtime_one<15>(q, r, m, E);
+    case 31: return runtime_one<31>(q, r, m, E);
+    default: return -100;
+    }
+}
+
+// Column-wise routine with subgrid width K (4, 8, 16), serial group max.
+int emu_cw(const uint32_t *q, const uint32_t *r, int m, int E, int K)
+{
+    switch (K) {
+    case 4: return cw_one<4>(q, r, m, E);
+    case 8: return cw_one<8>(q, r, m, E);
+    case 16: return cw_one<16>(q, r, m, E);
+    default: return -100;
+    }
+}
+
+// Class of a pair under the default tuning (for coverage checks).
+int emu_class_of(int m, int E) { return class_of(m, E); }
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+"""The library's routing functions, compiled for the host by the test
+harness in tests/kernel_emu, against the CPU oracle (no GPU needed).
+
+This checks the kernels' logic (word crossings, edge masks, runtime
+thresholds, the column-wise phases) quickly on the CPU; the GPU parity
+tests remain the proof that the kernels themselves agree with the oracle.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_09020_gb300 import synth
+
+kernel_emu = pytest.importorskip("kernel_emu")
+
+
+@pytest.fixture(scope="module")
+def emu():
+    return kernel_emu.load()
+
+
+def packed(seq: bytes) -> np.ndarray:
+    w = oracle.pack_reference(seq)
+    return np.concatenate([w, np.zeros(2, np.uint32)])  # slack for reads
+
+
+def P(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def pairs(seed, n, m, recipe):
+    r, f = synth.pairs_fixed(seed, 0, n, m, recipe)
+    return [(r[i].tobytes(), f[i].tobytes()) for i in range(n)]
+
+
+@pytest.mark.parametrize("m", [1, 2, 17, 31, 32, 33, 64, 65, 100, 150, 257])
+def test_rw_exact_matches_oracle(emu, m):
+    for Q, R in pairs(60 + m, 60, m, synth.rate_recipe(0.15)):
+        q, r = packed(Q), packed(R)
+        for E in (0, 1, 2, 5, 10, 17, 31):
+            got = emu.emu_rw_exact(P(q), P(r), m, E)
+            want = oracle.filter_pair(Q, R, E).obstacles
+            assert got == want, (m, E, Q, R)
+
+
+@pytest.mark.parametrize("emax", [1, 3, 7, 15, 31])
+def test_rw_runtime_threshold_matches_oracle(emu, emax):
+    rng = np.random.default_rng(emax)
+    for i in range(150):
+        m = int(rng.integers(1, 400))
+        Q, R = pairs(900 + i, 1, m, synth.rate_recipe(0.12))[0]
+        q, r = packed(Q), packed(R)
+        E = int(rng.integers(0, emax + 1))
+        if rng.random() < 0.2:
+            E = m + int(rng.integers(0, 5))  # E >= m (rows clamped)
+            if min(E, m - 1) > emax:
+                continue
+        got = emu.emu_rw_runtime(P(q), P(r), m, E, emax)
+        want = oracle.filter_pair(Q, R, E).obstacles
+        assert got == want, (m, E, emax)
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_cw_matches_oracle(emu, K):
+    rng = np.random.default_rng(K)
+    for i in range(60):
+        m = int(np.exp(rng.uniform(np.log(2), np.log(2500))))
+        E = int(rng.choice([0, 3, 31, 32, 70, m // 10, m // 2, m + 3]))
+        rec = synth.rate_recipe(float(rng.choice([0.01, 0.05, 0.2])))
+        Q, R = pairs(500 + i, 1, m, rec)[0]
+        q, r = packed(Q), packed(R)
+        got = emu.emu_cw(P(q), P(r), m, E, K)
+        want = oracle.filter_pair(Q, R, E).obstacles
+        assert got == want, (m, E, K)
+
+
+def test_worked_example_every_routine(emu):
+    Q, R = b"GGTGAGAGTTGT", b"GGTGCAGAGCTC"
+    q, r = packed(Q), packed(R)
+    assert emu.emu_rw_exact(P(q), P(r), 12, 3) == 3
+    assert emu.emu_rw_runtime(P(q), P(r), 12, 3, 7) == 3
+    for K in (4, 8, 16):
+        assert emu.emu_cw(P(q), P(r), 12, 3, K) == 3
+
+
+def test_class_table_covers_the_shapes(emu):
+    seen = set()
+    for m, E in [(100, 0), (100, 3), (100, 7), (100, 15), (100, 31),
+                 (1000, 50), (5000, 250), (12000, 500), (20000, 40),
+                 (3000, 600), (50000, 5000), (100000, 10000), (131072, 100)]:
+        c = emu.emu_class_of(m, E)
+        assert c >= 0, (m, E)
+        seen.add(c)
+    assert len(seen) >= 10
+    assert emu.emu_class_of(0, 5) == -1
+    assert emu.emu_class_of(5, -1) == -2
+    assert emu.emu_class_of(200000, 500) == -3
+    assert emu.emu_class_of(200000, 20) == 4  # small E: any length
