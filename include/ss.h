@@ -170,6 +170,33 @@ int ss_autotune(ss_ctx *ctx, const void *reads, const void *refs,
                 uint8_t *out_accept, int32_t *out_obstacles, int reps,
                 float *best_ms);
 
+/* ---- allocation-free entry point (the paper has no counterpart) -------
+ * For callers that cannot allocate device memory: a service that reserves
+ * all of a GPU's memory up front through its own allocator (an extra
+ * cudaMalloc would fail, or would synchronise the device at an unpredictable
+ * moment), or a plug-in inside another program that must stay within that
+ * program's memory.  Same arguments and results as ss_filter_batch for
+ * SS_FMT_PACKED2 input in the bucketed form (default tuning), but with no
+ * context and no allocation: the scratch (class tables and the pair
+ * permutation) is one fixed __device__ array of about 4 MiB in the library,
+ * held by every GPU that loads it until the process exits.
+ *   - Runs on the CURRENT device, on `stream` (NULL = default stream).  The
+ *     first call on a device looks up the array's device address and sizes
+ *     the kernels' grids; make that first call before any stream capture.
+ *   - n must be <= SS_NOALLOC_MAX_PAIRS, else SS_ERR_OOM (nothing launched).
+ *   - All calls share the one array and it keeps the last call's contents:
+ *     calls that overlap on the GPU (other streams or host threads) race.
+ *     Order them on one stream or synchronise between them.
+ *   - There is no ss_sync for it: a pair with a negative length or
+ *     threshold, or one too long to stage, gets obstacles = -1 (accept 0).
+ * Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM or SS_ERR_CUDA. */
+#define SS_NOALLOC_MAX_PAIRS 1048576
+int ss_filter_batch_noalloc(const void *reads, const void *refs,
+                            const int64_t *offsets, const int32_t *lengths,
+                            int32_t m, const int32_t *E, int32_t e, int64_t n,
+                            void *stream, uint8_t *out_accept,
+                            int32_t *out_obstacles);
+
 /* Counters of the context since creation (host-side accounting). */
 typedef struct ss_counters {
     int64_t pairs;        /* pairs submitted to ss_filter_batch/_host */

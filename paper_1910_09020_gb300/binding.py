@@ -37,8 +37,9 @@ EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
-    "ss_autotune",
+    "ss_autotune", "ss_filter_batch_noalloc",
 )
+SS_NOALLOC_MAX_PAIRS = 1048576
 
 
 class SSError(RuntimeError):
@@ -86,6 +87,8 @@ def load(build_if_needed: bool = True):
                                    ctypes.c_int, I64, P, P]
     lib.ss_sync.argtypes = [P, P]
     lib.ss_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    lib.ss_filter_batch_noalloc.argtypes = [P, P, P, P, I32, P, I32, I64, P,
+                                            P, P]
     lib.ss_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
     lib.ss_get_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
@@ -157,6 +160,15 @@ def ss_get_counters(ctx) -> Counters:
     c = Counters()
     _check(load().ss_get_counters(ctx, ctypes.byref(c)), "ss_get_counters")
     return c
+
+
+def ss_filter_batch_noalloc(reads, refs, offsets, lengths, m, E, e, n,
+                            stream, out_accept, out_obstacles) -> int:
+    """Allocation-free bucketed filter (packed input, current device)."""
+    return load().ss_filter_batch_noalloc(
+        reads or None, refs or None, offsets or None, lengths or None, m,
+        E or None, e, n, stream or None, out_accept or None,
+        out_obstacles or None)
 
 
 def ss_set_tuning(ctx, rw_max_e: int, cw_subgrid: int) -> int:

@@ -345,4 +345,45 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
     return cudaSuccess;
 }
 
+// The same kernel sequence on a single stream, for callers that hold no
+// context (no side stream, no events): used by the allocation-free entry
+// point.
+cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
+                                       int *status, cudaStream_t st)
+{
+    if (ps.n <= 0)
+        return cudaSuccess;
+    if (!g_cfg.ready)
+        return cudaErrorNotReady;
+    cudaError_t e;
+    const TuneParams tp;
+    int sm_count = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount,
+                                    dev)) != cudaSuccess)
+        return e;
+    const int64_t want = (ps.n + kBucketThreads - 1) / kBucketThreads;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)sm_count * 4);
+    if ((e = cudaMemsetAsync(ws.hist, 0, (size_t)kKeys * 4, st)) !=
+        cudaSuccess)
+        return e;
+    k_classify<<<grid, kBucketThreads, 0, st>>>(ps, ws, tp, status);
+    k_scan<<<1, 1024, 0, st>>>(ws);
+    k_scatter<<<grid, kBucketThreads, 0, st>>>(ps, ws, tp);
+    CwArgs a{ps, ws, 0, 0};
+    a.cls = 0;
+    k_rw_bucket<1><<<g_cfg.rw[0], 128, 0, st>>>(a);
+    a.cls = 1;
+    k_rw_bucket<3><<<g_cfg.rw[1], 128, 0, st>>>(a);
+    a.cls = 2;
+    k_rw_bucket<7><<<g_cfg.rw[2], 128, 0, st>>>(a);
+    a.cls = 3;
+    k_rw_bucket<15><<<g_cfg.rw[3], 128, 0, st>>>(a);
+    a.cls = 4;
+    k_rw_bucket<31><<<g_cfg.rw[4], 128, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    return launch_cw_classes<8>(a, st);
+}
+
 }  // namespace ssk

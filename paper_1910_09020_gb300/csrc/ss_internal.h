@@ -31,6 +31,8 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
 size_t bucket_ws_bytes(int64_t n);
 BucketWs bucket_ws_at(void *base, int64_t n);
 int cw_class_slice_words(int cls);
+cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
+                                       int *status, cudaStream_t st);
 // Kernel attributes and persistent grid sizes (once per process, called by
 // ss_create before any capture).
 cudaError_t bucket_init(int sm_count);
