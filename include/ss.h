@@ -197,6 +197,54 @@ int ss_filter_batch_noalloc(const void *reads, const void *refs,
                             void *stream, uint8_t *out_accept,
                             int32_t *out_obstacles);
 
+/* ---- serving: continuous batching of filter requests (not in the paper;
+ * its GPU version filters one prepared batch) -------------------------------
+ * A server owns a scheduler thread and `slots` in-flight batch slots.  A
+ * request is n pairs in HOST memory: ASCII reads and refs concatenated
+ * (pair k at byte sum(lengths[0..k-1])), per-pair lengths and thresholds.
+ * Whenever a slot is free the scheduler admits pending requests first-in
+ * first-out while their device footprint fits `hbm_budget_bytes`, copies
+ * them to the device, packs them and runs the bucketed filter with its
+ * persistent grids sized to 1/slots of the SMs, so batches admitted while
+ * others run execute beside them.  Results stay in device memory until
+ * fetched.  A request whose bases are not all A/C/G/T fails alone
+ * (SS_ERR_INVALID_BASE; its bad pairs get obstacles = -1).
+ *   ss_server_create   device, budget (0 = 8 GiB), slots 1..16.
+ *   ss_server_submit   1 <= n <= 2^20; the host buffers must stay valid and
+ *                      unchanged until the request is done (pinned memory
+ *                      copies fastest).  Returns SS_ERR_OOM if the request
+ *                      alone exceeds the budget.  *ticket identifies it.
+ *   ss_server_poll     SS_ERR_BUSY while pending/running, else its status.
+ *   ss_server_wait     blocks up to timeout_us; SS_ERR_TIMEOUT if not done.
+ *   ss_server_fetch    copies the results to host arrays of n entries,
+ *                      frees the request; latency_s (may be NULL) receives
+ *                      completion minus submission time.
+ *   ss_server_get_stats / ss_server_reset_stats  latency percentiles of the
+ *                      completed requests and counters.
+ * A server is driven from any number of client threads. */
+typedef struct ss_server ss_server;
+typedef struct ss_server_stats {
+    int64_t requests_done, pairs_done, bases_done;
+    int64_t batches;        /* batches launched                         */
+    int64_t max_inflight;   /* most batches seen in flight at once       */
+    int64_t pending;        /* requests waiting for admission            */
+    int64_t device_bytes_in_use;
+    double latency_p50_s, latency_p99_s, latency_max_s;
+    double span_s;          /* first submission to last completion       */
+} ss_server_stats;
+int ss_server_create(ss_server **out, int device, size_t hbm_budget_bytes,
+                     int slots);
+int ss_server_submit(ss_server *srv, const uint8_t *reads,
+                     const uint8_t *refs, const int32_t *lengths,
+                     const int32_t *E, int64_t n, uint64_t *ticket);
+int ss_server_poll(ss_server *srv, uint64_t ticket);
+int ss_server_wait(ss_server *srv, uint64_t ticket, int64_t timeout_us);
+int ss_server_fetch(ss_server *srv, uint64_t ticket, uint8_t *out_accept,
+                    int32_t *out_obstacles, double *latency_s);
+int ss_server_get_stats(ss_server *srv, ss_server_stats *out);
+int ss_server_reset_stats(ss_server *srv);
+int ss_server_destroy(ss_server *srv);
+
 /* Counters of the context since creation (host-side accounting). */
 typedef struct ss_counters {
     int64_t pairs;        /* pairs submitted to ss_filter_batch/_host */

@@ -37,7 +37,9 @@ EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
-    "ss_autotune", "ss_filter_batch_noalloc",
+    "ss_autotune", "ss_filter_batch_noalloc", "ss_server_create",
+    "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
+    "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
 )
 SS_NOALLOC_MAX_PAIRS = 1048576
 
@@ -46,6 +48,23 @@ class SSError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
         super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_int64),
+                ("pairs_done", ctypes.c_int64),
+                ("bases_done", ctypes.c_int64),
+                ("batches", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int64),
+                ("pending", ctypes.c_int64),
+                ("device_bytes_in_use", ctypes.c_int64),
+                ("latency_p50_s", ctypes.c_double),
+                ("latency_p99_s", ctypes.c_double),
+                ("latency_max_s", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Counters(ctypes.Structure):
@@ -89,6 +108,17 @@ def load(build_if_needed: bool = True):
     lib.ss_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
     lib.ss_filter_batch_noalloc.argtypes = [P, P, P, P, I32, P, I32, I64, P,
                                             P, P]
+    lib.ss_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, SZ,
+                                     ctypes.c_int]
+    lib.ss_server_submit.argtypes = [P, P, P, P, P, I64,
+                                     ctypes.POINTER(ctypes.c_uint64)]
+    lib.ss_server_poll.argtypes = [P, ctypes.c_uint64]
+    lib.ss_server_wait.argtypes = [P, ctypes.c_uint64, I64]
+    lib.ss_server_fetch.argtypes = [P, ctypes.c_uint64, P, P,
+                                    ctypes.POINTER(ctypes.c_double)]
+    lib.ss_server_get_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.ss_server_reset_stats.argtypes = [P]
+    lib.ss_server_destroy.argtypes = [P]
     lib.ss_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
     lib.ss_get_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
@@ -321,3 +351,82 @@ class Filter:
 
     def counters(self) -> Counters:
         return ss_get_counters(self.ctx)
+
+
+class Server:
+    """Continuous-batching request server (ss_server_* of include/ss.h).
+
+    Requests are numpy arrays in host memory: concatenated ASCII reads and
+    refs, per-pair int32 lengths and thresholds.  The arrays are kept alive
+    here until the request is fetched, as the C API requires."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0,
+                 slots: int = 3):
+        h = ctypes.c_void_p()
+        _check(load().ss_server_create(ctypes.byref(h), device,
+                                       hbm_budget_bytes, slots),
+               "ss_server_create")
+        self.h = h.value
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            load().ss_server_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, reads, refs, lengths, E) -> int:
+        import numpy as np
+        reads = np.ascontiguousarray(reads, dtype=np.uint8)
+        refs = np.ascontiguousarray(refs, dtype=np.uint8)
+        lengths = np.ascontiguousarray(lengths, dtype=np.int32)
+        E = np.ascontiguousarray(E, dtype=np.int32)
+        t = ctypes.c_uint64()
+        rc = load().ss_server_submit(
+            self.h, reads.ctypes.data if reads.size else None,
+            refs.ctypes.data if refs.size else None, lengths.ctypes.data,
+            E.ctypes.data, len(lengths), ctypes.byref(t))
+        _check(rc, "ss_server_submit")
+        self._keep[t.value] = (reads, refs, lengths, E)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return load().ss_server_poll(self.h, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> int:
+        return load().ss_server_wait(self.h, ticket, int(timeout_s * 1e6))
+
+    def fetch(self, ticket: int):
+        """(status, accept uint8[n], obstacles int32[n], latency seconds)."""
+        import numpy as np
+        n = len(self._keep[ticket][2])
+        acc = np.empty(max(n, 1), np.uint8)
+        obs = np.empty(max(n, 1), np.int32)
+        lat = ctypes.c_double()
+        rc = load().ss_server_fetch(self.h, ticket, acc.ctypes.data,
+                                    obs.ctypes.data, ctypes.byref(lat))
+        if rc != SS_ERR_BUSY:
+            self._keep.pop(ticket, None)
+        return rc, acc[:n], obs[:n], lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        rc = load().ss_server_get_stats(self.h, ctypes.byref(st))
+        d = st.as_dict()
+        d["status"] = rc
+        return d
+
+    def reset_stats(self):
+        load().ss_server_reset_stats(self.h)

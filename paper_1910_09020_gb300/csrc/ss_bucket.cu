@@ -201,8 +201,9 @@ int cw_class_slice_words(int cls)
 
 namespace {
 
+// Resident CTAs per SM of a kernel configuration (at least 1).
 template <class KernelT>
-int occupancy_grid(KernelT kernel, int threads, size_t smem, int sm_count)
+int occupancy_per_sm(KernelT kernel, int threads, size_t smem)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads,
@@ -211,10 +212,12 @@ int occupancy_grid(KernelT kernel, int threads, size_t smem, int sm_count)
         (void)cudaGetLastError();
         per_sm = 1;
     }
-    return per_sm * sm_count;
+    return per_sm;
 }
 
-// Persistent grid sizes, computed once (outside any stream capture).
+// Resident CTAs per SM of every persistent kernel, computed once (outside
+// any stream capture); a launch over `sm_share` SMs uses per_sm * sm_share
+// CTAs, so several bucketed passes can share the GPU side by side.
 struct LaunchCfg {
     int rw[kRwClasses];
     int cw[3][kClasses];  // [subgrid 4/8/16][class]
@@ -238,35 +241,35 @@ cudaError_t init_cw(int sm_count)
     for (int c = 0; c < kCwwClasses; ++c) {
         const int cls = kRwClasses + c;
         const size_t smem = (size_t)4 * cw_class_slice_words(cls) * 4;
-        g_cfg.cw[kidx(K)][cls] =
-            occupancy_grid(k_cw_warp<K>, 128, smem, sm_count);
+        g_cfg.cw[kidx(K)][cls] = occupancy_per_sm(k_cw_warp<K>, 128, smem);
     }
     for (int w = 0; w < kCwcWidths; ++w)
         for (int b = 0; b < kCwcMbounds; ++b) {
             const int cls = cwc_class(w, b);
             const size_t smem = (size_t)cw_class_slice_words(cls) * 4;
             g_cfg.cw[kidx(K)][cls] =
-                occupancy_grid(k_cw_cta<K>, cwc_width(w), smem, sm_count);
+                occupancy_per_sm(k_cw_cta<K>, cwc_width(w), smem);
         }
     return cudaSuccess;
 }
 
 template <int K>
-cudaError_t launch_cw_classes(CwArgs a, cudaStream_t st)
+cudaError_t launch_cw_classes(CwArgs a, int sm_share, cudaStream_t st)
 {
     for (int c = 0; c < kCwwClasses; ++c) {
         a.cls = kRwClasses + c;
         a.slice_words = cw_class_slice_words(a.cls);
         const size_t smem = (size_t)4 * a.slice_words * 4;
-        k_cw_warp<K><<<g_cfg.cw[kidx(K)][a.cls], 128, smem, st>>>(a);
+        k_cw_warp<K><<<g_cfg.cw[kidx(K)][a.cls] * sm_share, 128, smem, st>>>(
+            a);
     }
     for (int w = 0; w < kCwcWidths; ++w)
         for (int b = 0; b < kCwcMbounds; ++b) {
             a.cls = cwc_class(w, b);
             a.slice_words = cw_class_slice_words(a.cls);
             const size_t smem = (size_t)a.slice_words * 4;
-            k_cw_cta<K><<<g_cfg.cw[kidx(K)][a.cls], cwc_width(w), smem,
-                          st>>>(a);
+            k_cw_cta<K><<<g_cfg.cw[kidx(K)][a.cls] * sm_share, cwc_width(w),
+                          smem, st>>>(a);
         }
     return cudaGetLastError();
 }
@@ -278,11 +281,11 @@ cudaError_t bucket_init(int sm_count)
     if (g_cfg.ready)
         return cudaSuccess;
     cudaError_t e;
-    g_cfg.rw[0] = occupancy_grid(k_rw_bucket<1>, 128, 0, sm_count);
-    g_cfg.rw[1] = occupancy_grid(k_rw_bucket<3>, 128, 0, sm_count);
-    g_cfg.rw[2] = occupancy_grid(k_rw_bucket<7>, 128, 0, sm_count);
-    g_cfg.rw[3] = occupancy_grid(k_rw_bucket<15>, 128, 0, sm_count);
-    g_cfg.rw[4] = occupancy_grid(k_rw_bucket<31>, 128, 0, sm_count);
+    g_cfg.rw[0] = occupancy_per_sm(k_rw_bucket<1>, 128, 0);
+    g_cfg.rw[1] = occupancy_per_sm(k_rw_bucket<3>, 128, 0);
+    g_cfg.rw[2] = occupancy_per_sm(k_rw_bucket<7>, 128, 0);
+    g_cfg.rw[3] = occupancy_per_sm(k_rw_bucket<15>, 128, 0);
+    g_cfg.rw[4] = occupancy_per_sm(k_rw_bucket<31>, 128, 0);
     if ((e = init_cw<4>(sm_count)) != cudaSuccess ||
         (e = init_cw<8>(sm_count)) != cudaSuccess ||
         (e = init_cw<16>(sm_count)) != cudaSuccess)
@@ -317,24 +320,24 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
         return e;
     if (!g_cfg.ready)
         return cudaErrorNotReady;
-    (void)sm_count;
+    const int sh = sm_count;  // persistent grids span this many SMs
     CwArgs a{ps, ws, 0, 0};
     a.cls = 0;
-    k_rw_bucket<1><<<g_cfg.rw[0], 128, 0, st>>>(a);
+    k_rw_bucket<1><<<g_cfg.rw[0] * sh, 128, 0, st>>>(a);
     a.cls = 1;
-    k_rw_bucket<3><<<g_cfg.rw[1], 128, 0, st>>>(a);
+    k_rw_bucket<3><<<g_cfg.rw[1] * sh, 128, 0, st>>>(a);
     a.cls = 2;
-    k_rw_bucket<7><<<g_cfg.rw[2], 128, 0, st>>>(a);
+    k_rw_bucket<7><<<g_cfg.rw[2] * sh, 128, 0, st>>>(a);
     a.cls = 3;
-    k_rw_bucket<15><<<g_cfg.rw[3], 128, 0, st>>>(a);
+    k_rw_bucket<15><<<g_cfg.rw[3] * sh, 128, 0, st>>>(a);
     a.cls = 4;
-    k_rw_bucket<31><<<g_cfg.rw[4], 128, 0, st>>>(a);
+    k_rw_bucket<31><<<g_cfg.rw[4] * sh, 128, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     switch (tp.cw_subgrid) {
-    case 4: e = launch_cw_classes<4>(a, side); break;
-    case 16: e = launch_cw_classes<16>(a, side); break;
-    default: e = launch_cw_classes<8>(a, side); break;
+    case 4: e = launch_cw_classes<4>(a, sh, side); break;
+    case 16: e = launch_cw_classes<16>(a, sh, side); break;
+    default: e = launch_cw_classes<8>(a, sh, side); break;
     }
     if (e != cudaSuccess)
         return e;
@@ -370,20 +373,21 @@ cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
     k_classify<<<grid, kBucketThreads, 0, st>>>(ps, ws, tp, status);
     k_scan<<<1, 1024, 0, st>>>(ws);
     k_scatter<<<grid, kBucketThreads, 0, st>>>(ps, ws, tp);
+    const int sh = sm_count;
     CwArgs a{ps, ws, 0, 0};
     a.cls = 0;
-    k_rw_bucket<1><<<g_cfg.rw[0], 128, 0, st>>>(a);
+    k_rw_bucket<1><<<g_cfg.rw[0] * sh, 128, 0, st>>>(a);
     a.cls = 1;
-    k_rw_bucket<3><<<g_cfg.rw[1], 128, 0, st>>>(a);
+    k_rw_bucket<3><<<g_cfg.rw[1] * sh, 128, 0, st>>>(a);
     a.cls = 2;
-    k_rw_bucket<7><<<g_cfg.rw[2], 128, 0, st>>>(a);
+    k_rw_bucket<7><<<g_cfg.rw[2] * sh, 128, 0, st>>>(a);
     a.cls = 3;
-    k_rw_bucket<15><<<g_cfg.rw[3], 128, 0, st>>>(a);
+    k_rw_bucket<15><<<g_cfg.rw[3] * sh, 128, 0, st>>>(a);
     a.cls = 4;
-    k_rw_bucket<31><<<g_cfg.rw[4], 128, 0, st>>>(a);
+    k_rw_bucket<31><<<g_cfg.rw[4] * sh, 128, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    return launch_cw_classes<8>(a, st);
+    return launch_cw_classes<8>(a, sh, st);
 }
 
 }  // namespace ssk

@@ -20,7 +20,8 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,
 cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
                                const int32_t *lengths, int64_t n,
                                uint32_t *out, const int64_t *out_offsets,
-                               int *status, int sm_count, cudaStream_t st);
+                               int *status, int sm_count, cudaStream_t st,
+                               uint8_t *bad_flags = nullptr);
 
 // K3a plain launch for 0 <= E <= kRwMaxE, m <= kRwMaxM.
 cudaError_t launch_rw_uniform(int E, const uint32_t *reads,

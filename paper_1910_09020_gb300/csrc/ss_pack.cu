@@ -100,17 +100,18 @@ __global__ void k_pack_fixed(const uint8_t *__restrict__ ascii, int64_t n,
 }
 
 // Per-pair offsets and lengths: one warp per pair, lanes over its words.
+// bad (optional): per-pair flag set to 1 when the pair holds a non-base.
 __global__ void k_pack_varlen(const uint8_t *__restrict__ ascii,
                               const int64_t *__restrict__ offsets,
                               const int32_t *__restrict__ lengths, int64_t n,
                               uint32_t *__restrict__ out,
                               const int64_t *__restrict__ out_offsets,
-                              int *status)
+                              int *status, uint8_t *bad_flags)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    bool bad = false;
+    bool any_bad = false;
     for (int64_t p = warp; p < n; p += nwarps) {
         const int32_t m = lengths[p];
         if (m <= 0)
@@ -118,15 +119,20 @@ __global__ void k_pack_varlen(const uint8_t *__restrict__ ascii,
         const uint8_t *src = ascii + offsets[p];
         uint32_t *dst = out + out_offsets[p];
         const int w16 = (m + 15) >> 4;
+        bool pair_bad = false;
         for (int w = lane; w < w16; w += 32) {
             const uint8_t *s = src + (int64_t)w * 16;
             const int len = min(16, m - w * 16);
             bool valid;
             dst[w] = pack16(s, len, ((uintptr_t)s & 3) == 0, valid);
-            bad |= !valid;
+            pair_bad |= !valid;
         }
+        pair_bad = __any_sync(0xffffffffu, pair_bad);
+        if (pair_bad && bad_flags && lane == 0)
+            bad_flags[p] = 1;
+        any_bad |= pair_bad;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0)
+    if (any_bad && lane == 0)
         atomicOr(status, kStatusInvalidBase);
 }
 
@@ -147,7 +153,8 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,
 cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
                                const int32_t *lengths, int64_t n,
                                uint32_t *out, const int64_t *out_offsets,
-                               int *status, int sm_count, cudaStream_t st)
+                               int *status, int sm_count, cudaStream_t st,
+                               uint8_t *bad_flags)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -157,7 +164,7 @@ cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
     if (blocks > cap)
         blocks = cap;
     k_pack_varlen<<<(unsigned)blocks, threads, 0, st>>>(
-        ascii, offsets, lengths, n, out, out_offsets, status);
+        ascii, offsets, lengths, n, out, out_offsets, status, bad_flags);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,646 @@
+// ss_server.cu -- continuous-batching request server over the bucketed
+// filter (not in the paper, whose GPU version filters one prepared batch).
+//
+// Clients submit requests (host ASCII pairs with per-pair lengths and
+// thresholds).  A scheduler thread keeps up to `slots` batches in flight:
+// whenever a slot is free it admits pending requests first-in first-out
+// while their device footprint fits the HBM budget, copies them to the
+// device, packs them, and runs the bucketed pass with persistent grids
+// sized to 1/slots of the SMs, so that a batch admitted while others run
+// executes beside them instead of queueing behind them.  A host-function
+// callback on the batch's stream timestamps completion; results stay in
+// device memory until the client fetches them.  No device-side wait exists
+// on this path: the scheduler only polls host state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ss.h"
+#include "ss_bucket.cuh"
+#include "ss_device.cuh"
+#include "ss_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s()
+{
+    return std::chrono::duration<double>(Clock::now().time_since_epoch())
+        .count();
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+enum ReqState { kPending = 0, kRunning = 1, kDone = 2 };
+
+struct Batch;
+
+struct Request {
+    uint64_t id = 0;
+    const uint8_t *reads = nullptr, *refs = nullptr;  // caller-owned, host
+    std::vector<int32_t> lengths, E;
+    std::vector<int64_t> offsets;  // byte offset of each pair in reads/refs
+    int64_t n = 0;
+    int64_t bases = 0;
+    size_t footprint = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int state = kPending;
+    int status = SS_OK;
+    std::shared_ptr<Batch> batch;  // holds the device results
+    int64_t first = 0;             // first pair of this request in the batch
+};
+
+struct Batch {
+    int slot = -1;
+    std::vector<Request *> reqs;
+    int64_t n = 0;
+    void *dev = nullptr;   // inputs + workspace + results of the batch
+    size_t bytes = 0;
+    uint8_t *acc = nullptr;
+    int32_t *obs = nullptr;
+    int *status = nullptr;
+    uint8_t *bad = nullptr;         // per-pair invalid-input flags (device)
+    std::vector<uint8_t> host_bad;  // copied back at completion
+    cudaStream_t st = nullptr;
+    int pinned_refs = 0;   // requests whose results are still unfetched
+    std::atomic<bool> done{false};
+    double t_done = 0;
+    std::vector<char> host_meta;  // staging of offsets/lengths/E
+};
+
+struct Slot {
+    cudaStream_t st = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    std::shared_ptr<Batch> running;
+};
+
+}  // namespace
+
+struct ss_server {
+    int device = 0;
+    int sm_count = 0;
+    int nslots = 2;
+    size_t budget = 0;
+    size_t in_use = 0;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> pending;
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread thread;
+    int64_t max_batch_pairs = 1 << 20;
+    // statistics
+    std::vector<double> latencies;
+    int64_t done_requests = 0, done_pairs = 0, done_bases = 0;
+    int64_t batches = 0, max_inflight_seen = 0;
+    double t_first_submit = 0, t_last_done = 0;
+    int sticky_error = SS_OK;
+};
+
+namespace {
+
+// Device bytes a request needs while it runs (inputs, packed words,
+// per-pair metadata, bucket permutation, results).
+size_t footprint_of(const Request &r)
+{
+    size_t words = 0;
+    for (int32_t m : r.lengths)
+        words += (size_t)(m + 15) / 16;
+    return 2 * (size_t)r.bases + 2 * 4 * words + (size_t)r.n * (8 + 8 + 4 + 4 + 4 + 1 + 4) + 4096;
+}
+
+// Pairs whose input held a non-base are answered (accept 0, obstacles -1)
+// after routing, so a bad request fails alone.
+__global__ void k_mark_bad(const uint8_t *__restrict__ bad, int64_t n,
+                           uint8_t *acc, int32_t *obs)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (bad[p]) {
+            acc[p] = 0;
+            obs[p] = -1;
+        }
+}
+
+void CUDART_CB on_batch_done(void *arg)
+{
+    Batch *b = (Batch *)arg;
+    b->t_done = now_s();
+    b->done.store(true, std::memory_order_release);
+}
+
+// Launch one batch on a free slot.  Called with the server lock held.
+int launch_batch(ss_server *s, int slot_idx, std::vector<Request *> &take)
+{
+    Slot &sl = s->slots[slot_idx];
+    auto b = std::make_shared<Batch>();
+    b->slot = slot_idx;
+    b->reqs = take;
+    int64_t n = 0, bases = 0;
+    size_t words = 0;
+    for (Request *r : take) {
+        r->first = n;
+        n += r->n;
+        bases += r->bases;
+        for (int32_t m : r->lengths)
+            words += (size_t)(m + 15) / 16;
+    }
+    b->n = n;
+    // device layout: [bucket ws][ascii Q][ascii R][packed Q][packed R]
+    //                [byte off][word off][lengths][E][acc][obs][status]
+    const size_t a_ws = align_up(ssk::bucket_ws_bytes(n), 256);
+    const size_t a_ascii = align_up((size_t)std::max<int64_t>(bases, 1), 256);
+    const size_t a_pk = align_up(std::max<size_t>(words, 1) * 4, 256);
+    const size_t a_i64 = align_up((size_t)n * 8, 256);
+    const size_t a_i32 = align_up((size_t)n * 4, 256);
+    const size_t a_u8 = align_up((size_t)n, 256);
+    b->bytes = a_ws + 2 * a_ascii + 2 * a_pk + 2 * a_i64 + 2 * a_i32 +
+               2 * a_u8 + a_i32 + 256;
+    if (cudaMallocAsync(&b->dev, b->bytes, sl.st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SS_ERR_OOM;
+    }
+    char *p = (char *)b->dev;
+    void *ws = p;
+    p += a_ws;
+    uint8_t *dq = (uint8_t *)p;
+    p += a_ascii;
+    uint8_t *dr = (uint8_t *)p;
+    p += a_ascii;
+    uint32_t *pq = (uint32_t *)p;
+    p += a_pk;
+    uint32_t *pr = (uint32_t *)p;
+    p += a_pk;
+    int64_t *boff = (int64_t *)p;
+    p += a_i64;
+    int64_t *woff = (int64_t *)p;
+    p += a_i64;
+    int32_t *dlen = (int32_t *)p;
+    p += a_i32;
+    int32_t *dE = (int32_t *)p;
+    p += a_i32;
+    b->acc = (uint8_t *)p;
+    p += a_u8;
+    b->obs = (int32_t *)p;
+    p += a_i32;
+    b->bad = (uint8_t *)p;
+    p += a_u8;
+    b->status = (int *)p;
+    b->st = sl.st;
+
+    // host metadata of the batch (staged once, copied in one transfer each)
+    b->host_meta.resize((size_t)n * (8 + 8 + 4 + 4));
+    int64_t *h_boff = (int64_t *)b->host_meta.data();
+    int64_t *h_woff = h_boff + n;
+    int32_t *h_len = (int32_t *)(h_woff + n);
+    int32_t *h_E = h_len + n;
+    int64_t bo = 0, wo = 0, i = 0;
+    for (Request *r : take) {
+        for (int64_t k = 0; k < r->n; ++k, ++i) {
+            h_boff[i] = bo + r->offsets[k];
+            h_woff[i] = wo;
+            h_len[i] = r->lengths[k];
+            h_E[i] = r->E[k];
+            wo += (r->lengths[k] + 15) / 16;
+        }
+        bo += r->bases;
+    }
+    cudaStream_t st = sl.st;
+    cudaError_t e = cudaSuccess;
+    // inputs: one copy per request and sequence set
+    int64_t at = 0;
+    for (Request *r : take) {
+        if (r->bases > 0) {
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dq + at, r->reads, (size_t)r->bases,
+                                    cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dr + at, r->refs, (size_t)r->bases,
+                                    cudaMemcpyHostToDevice, st);
+        }
+        at += r->bases;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(boff, h_boff, (size_t)n * 8,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(woff, h_woff, (size_t)n * 8,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dlen, h_len, (size_t)n * 4,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dE, h_E, (size_t)n * 4, cudaMemcpyHostToDevice,
+                            st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->status, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->bad, 0, (size_t)n, st);
+    if (e == cudaSuccess)
+        e = ssk::launch_pack_varlen(dq, boff, dlen, n, pq, woff, b->status,
+                                    s->sm_count, st, b->bad);
+    if (e == cudaSuccess)
+        e = ssk::launch_pack_varlen(dr, boff, dlen, n, pr, woff, b->status,
+                                    s->sm_count, st, b->bad);
+    ssk::PairSet ps;
+    ps.reads = pq;
+    ps.refs = pr;
+    ps.offsets = woff;
+    ps.lengths = dlen;
+    ps.Es = dE;
+    ps.m = 0;
+    ps.e = 0;
+    ps.stride = 0;
+    ps.n = n;
+    ps.acc = b->acc;
+    ps.obs = b->obs;
+    int launches = 0;
+    const int share = std::max(1, s->sm_count / s->nslots);
+    if (e == cudaSuccess)
+        e = ssk::launch_bucketed(ps, ssk::bucket_ws_at(ws, n), ssk::TuneParams(),
+                                 b->status, share, st, sl.side, sl.fork,
+                                 sl.join, &launches);
+    if (e == cudaSuccess) {
+        const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * s->sm_count);
+        k_mark_bad<<<g, 256, 0, st>>>(b->bad, n, b->acc, b->obs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaLaunchHostFunc(st, on_batch_done, b.get());
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaStreamSynchronize(st);
+        cudaFreeAsync(b->dev, st);
+        return SS_ERR_CUDA;
+    }
+    const double t = now_s();
+    for (Request *r : take) {
+        r->state = kRunning;
+        r->t_start = t;
+        r->batch = b;
+    }
+    b->pinned_refs = (int)take.size();
+    sl.running = b;
+    s->batches += 1;
+    return SS_OK;
+}
+
+// Release the device memory of a batch whose results are all fetched.
+void maybe_free_batch(ss_server *s, const std::shared_ptr<Batch> &b)
+{
+    if (b->pinned_refs == 0 && b->dev) {
+        cudaFreeAsync(b->dev, b->st);  // back to the stream-ordered pool
+        b->dev = nullptr;
+        s->in_use -= std::min(s->in_use, b->bytes);
+    }
+}
+
+void scheduler(ss_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    while (!s->stop) {
+        // completions
+        bool any_done = false;
+        for (Slot &sl : s->slots) {
+            std::shared_ptr<Batch> b = sl.running;
+            if (!b || !b->done.load(std::memory_order_acquire))
+                continue;
+            int dev_status = 0;
+            cudaMemcpy(&dev_status, b->status, sizeof(int),
+                       cudaMemcpyDeviceToHost);
+            // a bad base fails its own request only
+            if (dev_status & ssk::kStatusInvalidBase) {
+                b->host_bad.resize((size_t)b->n);
+                cudaMemcpy(b->host_bad.data(), b->bad, (size_t)b->n,
+                           cudaMemcpyDeviceToHost);
+            }
+            int st = SS_OK;
+            if (dev_status & ssk::kStatusUnsupported)
+                st = SS_ERR_UNSUPPORTED;
+            for (Request *r : b->reqs) {
+                r->state = kDone;
+                r->status = st;
+                if (!b->host_bad.empty())
+                    for (int64_t k = 0; k < r->n; ++k)
+                        if (b->host_bad[(size_t)(r->first + k)]) {
+                            r->status = SS_ERR_INVALID_BASE;
+                            break;
+                        }
+                r->t_done = b->t_done;
+                s->latencies.push_back(r->t_done - r->t_submit);
+                s->done_requests += 1;
+                s->done_pairs += r->n;
+                s->done_bases += r->bases;
+            }
+            s->t_last_done = std::max(s->t_last_done, b->t_done);
+            sl.running.reset();
+            any_done = true;
+        }
+        if (any_done)
+            s->cv_done.notify_all();
+        // admission: fill free slots first-in first-out within the budget
+        for (int k = 0; k < s->nslots && !s->pending.empty(); ++k) {
+            if (s->slots[k].running)
+                continue;
+            std::vector<Request *> take;
+            size_t need = 0;
+            int64_t pairs = 0;
+            while (!s->pending.empty()) {
+                Request *r = s->pending.front();
+                const bool first = take.empty();
+                if (!first && (s->in_use + need + r->footprint > s->budget ||
+                               pairs + r->n > s->max_batch_pairs))
+                    break;
+                if (first && s->in_use + r->footprint > s->budget)
+                    break;  // wait for memory to free up
+                take.push_back(r);
+                need += r->footprint;
+                pairs += r->n;
+                s->pending.pop_front();
+            }
+            if (take.empty())
+                break;
+            const int rc = launch_batch(s, k, take);
+            if (rc != SS_OK) {
+                for (Request *r : take) {
+                    r->state = kDone;
+                    r->status = rc;
+                    r->t_done = now_s();
+                }
+                s->sticky_error = rc;
+                s->cv_done.notify_all();
+                continue;
+            }
+            s->in_use += s->slots[k].running->bytes;
+            int64_t inflight = 0;
+            for (Slot &sl : s->slots)
+                inflight += sl.running ? 1 : 0;
+            s->max_inflight_seen = std::max(s->max_inflight_seen, inflight);
+        }
+        s->cv_work.wait_for(lock, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ss_server_create(ss_server **out, int device, size_t hbm_budget_bytes,
+                     int slots)
+{
+    if (!out || slots < 1 || slots > 16)
+        return SS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SS_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev)
+        return SS_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return SS_ERR_CUDA;
+    auto s = new ss_server();
+    s->device = device;
+    s->nslots = slots;
+    s->budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)8 << 30);
+    cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount,
+                           device);
+    // keep freed batch memory in the device's pool instead of returning it
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    (void)cudaGetLastError();
+    if (ssk::bucket_init(s->sm_count) != cudaSuccess) {
+        delete s;
+        return SS_ERR_CUDA;
+    }
+    s->slots.resize(slots);
+    for (Slot &sl : s->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) !=
+                cudaSuccess ||
+            cudaStreamCreateWithFlags(&sl.side, cudaStreamNonBlocking) !=
+                cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) !=
+                cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.join, cudaEventDisableTiming) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            ss_server_destroy(s);
+            return SS_ERR_CUDA;
+        }
+    }
+    s->thread = std::thread(scheduler, s);
+    *out = s;
+    return SS_OK;
+}
+
+int ss_server_destroy(ss_server *s)
+{
+    if (!s)
+        return SS_OK;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->thread.joinable())
+        s->thread.join();
+    cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : s->reqs) {
+        Request *r = kv.second.get();
+        if (r->batch) {
+            r->batch->pinned_refs = std::max(0, r->batch->pinned_refs - 1);
+            maybe_free_batch(s, r->batch);
+            r->batch.reset();
+        }
+    }
+    for (Slot &sl : s->slots) {
+        if (sl.running) {
+            sl.running->pinned_refs = 0;
+            maybe_free_batch(s, sl.running);
+        }
+        if (sl.st)
+            cudaStreamDestroy(sl.st);
+        if (sl.side)
+            cudaStreamDestroy(sl.side);
+        if (sl.fork)
+            cudaEventDestroy(sl.fork);
+        if (sl.join)
+            cudaEventDestroy(sl.join);
+    }
+    delete s;
+    return SS_OK;
+}
+
+int ss_server_submit(ss_server *s, const uint8_t *reads, const uint8_t *refs,
+                     const int32_t *lengths, const int32_t *E, int64_t n,
+                     uint64_t *ticket)
+{
+    if (!s || !ticket || n < 1 || n > (1 << 20) || !lengths || !E)
+        return SS_ERR_INVALID_ARG;
+    auto r = std::make_unique<Request>();
+    r->reads = reads;
+    r->refs = refs;
+    r->n = n;
+    r->lengths.assign(lengths, lengths + n);
+    r->E.assign(E, E + n);
+    r->offsets.resize((size_t)n);
+    int64_t bases = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (lengths[k] < 0 || E[k] < 0)
+            return SS_ERR_INVALID_ARG;
+        r->offsets[(size_t)k] = bases;
+        bases += lengths[k];
+    }
+    if (bases > 0 && (!reads || !refs))
+        return SS_ERR_INVALID_ARG;
+    r->bases = bases;
+    r->footprint = footprint_of(*r);
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (r->footprint > s->budget)
+        return SS_ERR_OOM;
+    r->id = s->next_id++;
+    r->t_submit = now_s();
+    if (s->t_first_submit == 0)
+        s->t_first_submit = r->t_submit;
+    *ticket = r->id;
+    s->pending.push_back(r.get());
+    s->reqs.emplace(r->id, std::move(r));
+    s->cv_work.notify_one();
+    return SS_OK;
+}
+
+int ss_server_poll(ss_server *s, uint64_t ticket)
+{
+    if (!s)
+        return SS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return SS_ERR_INVALID_ARG;
+    const Request *r = it->second.get();
+    if (r->state != kDone)
+        return SS_ERR_BUSY;
+    return r->status;
+}
+
+int ss_server_wait(ss_server *s, uint64_t ticket, int64_t timeout_us)
+{
+    if (!s)
+        return SS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return SS_ERR_INVALID_ARG;
+    const Request *r = it->second.get();
+    const auto deadline =
+        Clock::now() + std::chrono::microseconds(std::max<int64_t>(0, timeout_us));
+    while (r->state != kDone) {
+        if (s->cv_done.wait_until(lock, deadline) == std::cv_status::timeout &&
+            r->state != kDone)
+            return SS_ERR_TIMEOUT;
+    }
+    return r->status;
+}
+
+int ss_server_fetch(ss_server *s, uint64_t ticket, uint8_t *out_accept,
+                    int32_t *out_obstacles, double *latency_s)
+{
+    if (!s || !out_accept || !out_obstacles)
+        return SS_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return SS_ERR_INVALID_ARG;
+    Request *r = it->second.get();
+    if (r->state != kDone)
+        return SS_ERR_BUSY;
+    int rc = r->status;
+    if (r->batch && r->batch->dev) {
+        cudaSetDevice(s->device);
+        if (cudaMemcpy(out_accept, r->batch->acc + r->first, (size_t)r->n,
+                       cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(out_obstacles, r->batch->obs + r->first,
+                       (size_t)r->n * 4, cudaMemcpyDeviceToHost) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = SS_ERR_CUDA;
+        }
+    } else if (rc == SS_OK) {
+        rc = SS_ERR_CUDA;
+    }
+    if (latency_s)
+        *latency_s = r->t_done - r->t_submit;
+    if (r->batch) {
+        r->batch->pinned_refs -= 1;
+        maybe_free_batch(s, r->batch);
+        r->batch.reset();
+    }
+    s->reqs.erase(it);
+    s->cv_work.notify_one();
+    return rc;
+}
+
+int ss_server_get_stats(ss_server *s, ss_server_stats *out)
+{
+    if (!s || !out)
+        return SS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    std::memset(out, 0, sizeof *out);
+    out->requests_done = s->done_requests;
+    out->pairs_done = s->done_pairs;
+    out->bases_done = s->done_bases;
+    out->batches = s->batches;
+    out->max_inflight = s->max_inflight_seen;
+    out->pending = (int64_t)s->pending.size();
+    out->device_bytes_in_use = (int64_t)s->in_use;
+    std::vector<double> v = s->latencies;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const size_t i = (size_t)std::min<double>(
+                (double)(v.size() - 1), q * (double)(v.size() - 1) + 0.5);
+            return v[i];
+        };
+        out->latency_p50_s = pct(0.50);
+        out->latency_p99_s = pct(0.99);
+        out->latency_max_s = v.back();
+    }
+    if (s->t_last_done > s->t_first_submit && s->t_first_submit > 0)
+        out->span_s = s->t_last_done - s->t_first_submit;
+    return s->sticky_error;
+}
+
+int ss_server_reset_stats(ss_server *s)
+{
+    if (!s)
+        return SS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->latencies.clear();
+    s->done_requests = s->done_pairs = s->done_bases = 0;
+    s->batches = s->max_inflight_seen = 0;
+    s->t_first_submit = s->t_last_done = 0;
+    s->sticky_error = SS_OK;
+    return SS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+"""GPU tests of the continuous-batching server: every request's result is
+the same alone and in the mix (and equals the oracle's), a poisoned request
+fails alone, batches admitted while others run overlap, and admission
+respects the HBM budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_09020_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def make_requests(seed, count, max_pairs=150, mlo=100, mhi=4000, pct=10):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(0, np.log(max_pairs))))
+        L = synth.log_uniform(seed + i, 0, n, mlo, mhi)
+        E = synth.thresholds(L, pct)
+        reads, refs, off = synth.pairs_varlen(seed * 1000 + i, 0, L,
+                                              synth.rate_recipe(0.15))
+        reqs.append((reads, refs, L, E, off))
+    return reqs
+
+
+def oracle_of(req):
+    reads, refs, L, E, off = req
+    return oracle.filter_batch(reads, refs, L, E, offsets=off)
+
+
+@pytest.fixture(scope="module")
+def reqs():
+    return make_requests(81, 14)
+
+
+def test_alone_equals_mix_equals_oracle(reqs):
+    with binding.Server(0, hbm_budget_bytes=2 << 30, slots=3) as S:
+        alone = []
+        for r in reqs:
+            t = S.submit(r[0], r[1], r[2], r[3])
+            assert S.wait(t) == binding.SS_OK
+            rc, a, o, lat = S.fetch(t)
+            assert rc == binding.SS_OK and lat > 0
+            alone.append((a, o))
+        # the mix: all requests submitted from four client threads at once
+        tickets = [None] * len(reqs)
+
+        def client(k):
+            for i in range(k, len(reqs), 4):
+                r = reqs[i]
+                tickets[i] = S.submit(r[0], r[1], r[2], r[3])
+
+        th = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        mix = []
+        for t in tickets:
+            assert S.wait(t) == binding.SS_OK
+            rc, a, o, _ = S.fetch(t)
+            assert rc == binding.SS_OK
+            mix.append((a, o))
+        st = S.stats()
+        assert st["requests_done"] == 2 * len(reqs)
+        assert st["latency_p99_s"] >= st["latency_p50_s"] > 0
+    for (a1, o1), (a2, o2), r in zip(alone, mix, reqs):
+        assert (a1 == a2).all() and (o1 == o2).all()
+        oa, oo = oracle_of(r)
+        assert (a1 == oa).all() and (o1 == oo).all()
+
+
+def test_poisoned_request_fails_alone(reqs):
+    bad = list(reqs[2])
+    bad_reads = bad[0].copy()
+    bad_reads[len(bad_reads) // 2] = ord("N")
+    bad[0] = bad_reads
+    with binding.Server(0, hbm_budget_bytes=1 << 30, slots=1) as S:
+        t0 = S.submit(*reqs[0][:4])
+        t1 = S.submit(bad[0], bad[1], bad[2], bad[3])
+        t2 = S.submit(*reqs[1][:4])
+        for t in (t0, t1, t2):
+            S.wait(t)
+        rc0, a0, o0, _ = S.fetch(t0)
+        rc1, a1, o1, _ = S.fetch(t1)
+        rc2, a2, o2, _ = S.fetch(t2)
+    assert rc0 == binding.SS_OK and rc2 == binding.SS_OK
+    assert rc1 == binding.SS_ERR_INVALID_BASE
+    assert (o1 == -1).any()
+    for (a, o), r in (((a0, o0), reqs[0]), ((a2, o2), reqs[1])):
+        oa, oo = oracle_of(r)
+        assert (a == oa).all() and (o == oo).all()
+
+
+def test_batches_overlap_on_the_device():
+    """A long request is running when short ones arrive: they are admitted
+    to other slots and run beside it."""
+    L = np.full(1200, 30000, np.int32)
+    E = np.full(1200, 3000, np.int32)
+    reads, refs, _ = synth.pairs_varlen(90, 0, L, synth.rate_recipe(0.2))
+    short = make_requests(91, 6, max_pairs=20, mlo=100, mhi=300)
+    with binding.Server(0, hbm_budget_bytes=4 << 30, slots=3) as S:
+        tl = S.submit(reads, refs, L, E)
+        deadline = time.time() + 10
+        while S.stats()["batches"] < 1 and time.time() < deadline:
+            time.sleep(0.001)
+        ts = [S.submit(r[0], r[1], r[2], r[3]) for r in short]
+        for t in ts:
+            assert S.wait(t) == binding.SS_OK
+        long_done_first = S.poll(tl) != binding.SS_ERR_BUSY
+        assert S.wait(tl) == binding.SS_OK
+        st = S.stats()
+        outs = [S.fetch(t) for t in ts]
+        S.fetch(tl)
+    assert st["max_inflight"] >= 2
+    assert not long_done_first, "short requests waited for the long one"
+    for (rc, a, o, _), r in zip(outs, short):
+        oa, oo = oracle_of(r)
+        assert rc == binding.SS_OK and (a == oa).all() and (o == oo).all()
+
+
+def test_admission_by_budget():
+    with binding.Server(0, hbm_budget_bytes=1 << 20, slots=2) as S:
+        L = np.full(100, 10000, np.int32)
+        E = np.full(100, 10, np.int32)
+        reads = np.full(L.sum(), ord("A"), np.uint8)
+        with pytest.raises(binding.SSError) as ei:
+            S.submit(reads, reads, L, E)
+        assert ei.value.code == binding.SS_ERR_OOM
+        small = make_requests(92, 3, max_pairs=10, mlo=100, mhi=200)
+        ts = [S.submit(r[0], r[1], r[2], r[3]) for r in small]
+        for t, r in zip(ts, small):
+            assert S.wait(t) == binding.SS_OK
+            rc, a, o, _ = S.fetch(t)
+            oa, oo = oracle_of(r)
+            assert (a == oa).all() and (o == oo).all()
