@@ -66,6 +66,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the batched and served forms")
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "batched"],
+                    help="batched: only the persistent launch of the uneven "
+                         "batch (for profiling)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival window of each offered load")
+    ap.add_argument("--batched-pairs", type=int, default=2_000_000,
+                    help="pairs of the uneven batch")
     return ap.parse_args()
 
 
@@ -285,6 +295,296 @@ def config_dict(world: int, n_override: int | None = None) -> dict:
             "l2": "inputs larger than L2 (6 GB ASCII + 1.7 GB packed)"}
 
 
+# ---- batched and served forms (configurations beside the headline) ------------
+
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _time_ms(fn, reps: int, sync) -> float:
+    import torch
+    fn()
+    sync()
+    torch.cuda.synchronize()
+    a, z = _ev(), _ev()
+    a.record()
+    for _ in range(reps):
+        fn()
+    z.record()
+    torch.cuda.synchronize()
+    sync()
+    return a.elapsed_time(z) / reps
+
+
+def _pack_varlen(F, L, recipe, seed):
+    """Pairs of lengths L, generated and packed on the device; returns the
+    device packed buffers, word offsets, lengths and host byte offsets."""
+    import torch
+
+    from paper_1910_09020_gb300 import synth
+    reads, refs, off = synth.pairs_varlen(seed, 0, L, recipe)
+    words = (L.astype(np.int64) + 15) // 16
+    woff = np.zeros(len(L) + 1, np.int64)
+    np.cumsum(words, out=woff[1:])
+    dL = torch.from_numpy(L).cuda()
+    dwo = torch.from_numpy(woff[:-1].copy()).cuda()
+    doff = torch.from_numpy(off[:-1].copy()).cuda()
+    pq = torch.empty(int(woff[-1]), dtype=torch.int32, device="cuda")
+    pr = torch.empty_like(pq)
+    dq = torch.from_numpy(reads).cuda()
+    F.pack(dq, offsets=doff, lengths=dL, out=pq, out_offsets=dwo)
+    del dq
+    dr = torch.from_numpy(refs).cuda()
+    F.pack(dr, offsets=doff, lengths=dL, out=pr, out_offsets=dwo)
+    del dr
+    F.sync()
+    return pq, pr, dwo, dL, woff, (reads, refs, off)
+
+
+def _oracle_model(host, L, E, idx):
+    """Oracle time and the op model (survey's row-word model) on a sample
+    of pairs, by threshold group.  Returns (seconds, alu ops, xu ops,
+    cells)."""
+    import oracle
+    reads, refs, off = host
+    t = alu = xu = cells = 0.0
+    for e in np.unique(E[idx]):
+        sel = idx[E[idx] == e]
+        sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in sel])
+        sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in sel])
+        so = np.zeros(len(sel) + 1, np.int64)
+        np.cumsum(L[sel], out=so[1:])
+        t0 = time.perf_counter()
+        _, _, (c, w, it) = oracle.filter_batch(sub_r, sub_f, L[sel],
+                                               E[sel], offsets=so,
+                                               with_stats=True)
+        t += time.perf_counter() - t0
+        alu += w * K_WORD + it * (2 * int(e) + 1) * K_RED + it * K_ITER
+        xu += w
+        cells += c
+    return t, alu, xu, cells
+
+
+def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
+                per_length_too: bool = True, n: int = 2_000_000) -> dict:
+    """Uneven batch of 2M pairs, lengths log-uniform 64..10000, edit rate
+    U[0, 0.10], E = 5 % of each length: one bucketed persistent launch
+    (CUDA graph, autotuned) against one launch per distinct length."""
+    import torch
+
+    from paper_1910_09020_gb300 import binding, synth
+    seed = 1910_09020 + 4
+    L = np.sort(synth.log_uniform(seed, 0, n, 64, 10000)).astype(np.int32)
+    E = synth.thresholds(L, 5)
+    pq, pr, dwo, dL, woff, host = _pack_varlen(F, L, synth.rate_recipe(0.10),
+                                               seed)
+    dE = torch.from_numpy(E).cuda()
+    acc = torch.empty(n, dtype=torch.uint8, device="cuda")
+    obs = torch.empty(n, dtype=torch.int32, device="cuda")
+    rmax, k, _ = F.autotune(pq, pr, offsets=dwo, lengths=dL, E=dE, reps=2,
+                            out_accept=acc, out_obstacles=obs)
+    persistent = lambda: F.filter(pq, pr, offsets=dwo, lengths=dL, E=dE,
+                                  out_accept=acc, out_obstacles=obs)
+    t_p = _time_ms(persistent, 10, F.sync)
+    # per-length launches: pairs are sorted by length, so each distinct
+    # length is a fixed-stride block of the same packed buffers
+    starts = np.flatnonzero(np.r_[True, L[1:] != L[:-1]])
+    ends = np.r_[starts[1:], n]
+    acc2 = torch.empty_like(acc)
+    obs2 = torch.empty_like(obs)
+
+    def per_length():
+        for a, b in zip(starts, ends):
+            m = int(L[a])
+            F.filter(pq[int(woff[a]):], pr[int(woff[a]):], m=m, e=int(E[a]),
+                     n=int(b - a), out_accept=acc2[a:b],
+                     out_obstacles=obs2[a:b],
+                     flags=binding.SS_FLAG_NO_GRAPH)
+    if not per_length_too:
+        return {"persistent_graph_ms": t_p, "pairs": n}
+    t_l = _time_ms(per_length, 2, F.sync)
+    same = bool(torch.equal(acc, acc2) and torch.equal(obs, obs2))
+    bases = int(L.sum())
+    bytes_alg = float(np.sum(2 * ((L.astype(np.int64) + 3) // 4) + 5 + 16))
+    out = {
+        "workload": "2M pairs, lengths log-uniform 64..10000 bp, edit rate "
+                    "U[0,0.10] (80 % substitutions), E = 5 % of length",
+        "pairs": n, "bases": bases,
+        "persistent_graph": {"ms": t_p, "pairs_per_s": n / (t_p * 1e-3),
+                             "gbases_per_s": bases / (t_p * 1e-3) / 1e9,
+                             "tuning": {"rw_max_e": rmax, "cw_subgrid": k}},
+        "per_length_launches": {"ms": t_l, "pairs_per_s": n / (t_l * 1e-3),
+                                "groups": int(len(starts))},
+        "persistent_over_per_length": t_l / t_p,
+        "results_identical": same,
+        "accept_rate": float(acc.float().mean().item()),
+    }
+    t_hbm = bytes_alg / (hbm_gbs * 1e9)
+    roof = {"t_hbm_ms": 1e3 * t_hbm, "algorithmic_bytes": bytes_alg}
+    if want_cpu:
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(n, 1500, replace=False))
+        t_o, alu, xu, cells = _oracle_model(host, L, E, idx)
+        scale = n / len(idx)
+        t_alu = alu * scale / ipk["lop3"]
+        t_xu = xu * scale / ipk["bfind"]
+        roof.update({"t_alu_ms": 1e3 * t_alu, "t_xu_ms": 1e3 * t_xu,
+                     "alu_ops_per_pair": alu / len(idx),
+                     "cells_per_pair": cells / len(idx)})
+        import oracle
+        out["cpu_baseline"] = {
+            "value": len(idx) / t_o, "unit": "pairs/s", "kind": "oracle",
+            "cores": oracle.default_threads(),
+            "sample": f"{len(idx)} pairs drawn uniformly from the batch "
+                      f"({t_o:.1f} s)"}
+    t_bound = max(roof.get("t_alu_ms", 0), roof.get("t_xu_ms", 0),
+                  roof["t_hbm_ms"])
+    roof["bound"] = ("hbm" if t_bound == roof["t_hbm_ms"] else
+                     "alu" if t_bound == roof.get("t_alu_ms") else "xu")
+    roof["frac"] = t_bound / t_p
+    roof["note"] = ("ALU term: the row-word op model of the lazy maze; the "
+                    "warp/CTA kernels evaluate 32 rows per word op, so they "
+                    "can run faster than that model")
+    out["roofline"] = roof
+    del pq, pr
+    return out
+
+
+def run_two_lengths(F) -> dict:
+    """10M pairs of 250 bp and 10M of 150 bp, edit rate U[0, 0.12], E = 0 %
+    .. 10 % of length: two plain launches against one persistent graph."""
+    import torch
+
+    from paper_1910_09020_gb300 import synth
+    n3 = 10_000_000
+    seed = 1910_09020 + 3
+    rec = synth.rate_recipe(0.12)
+    bufs = []
+    for m, first in ((250, 0), (150, n3)):
+        r, f = synth.pairs_fixed(seed, first, n3, m, rec)
+        q = F.pack(torch.from_numpy(r.reshape(-1)).cuda(), m=m, n=n3)
+        g = F.pack(torch.from_numpy(f.reshape(-1)).cuda(), m=m, n=n3)
+        F.sync()
+        bufs.append((q, g))
+        del r, f
+    w250, w150 = 16, 10
+    allq = torch.cat([bufs[0][0], bufs[1][0]])
+    allr = torch.cat([bufs[0][1], bufs[1][1]])
+    offs = torch.cat([torch.arange(n3, dtype=torch.int64) * w250,
+                      n3 * w250 + torch.arange(n3, dtype=torch.int64) * w150]
+                     ).cuda()
+    lens = torch.cat([torch.full((n3,), 250, dtype=torch.int32),
+                      torch.full((n3,), 150, dtype=torch.int32)]).cuda()
+    a = torch.empty(2 * n3, dtype=torch.uint8, device="cuda")
+    o = torch.empty(2 * n3, dtype=torch.int32, device="cuda")
+    a2, o2 = torch.empty_like(a), torch.empty_like(o)
+    rows = []
+    same = True
+    for pct in range(0, 11):
+        e250, e150 = 250 * pct // 100, 150 * pct // 100
+        Es = torch.cat([torch.full((n3,), e250, dtype=torch.int32),
+                        torch.full((n3,), e150, dtype=torch.int32)]).cuda()
+
+        def plain():
+            F.filter(bufs[0][0], bufs[0][1], m=250, e=e250, n=n3,
+                     out_accept=a[:n3], out_obstacles=o[:n3])
+            F.filter(bufs[1][0], bufs[1][1], m=150, e=e150, n=n3,
+                     out_accept=a[n3:], out_obstacles=o[n3:])
+        persistent = lambda: F.filter(allq, allr, offsets=offs, lengths=lens,
+                                      E=Es, out_accept=a2, out_obstacles=o2)
+        tp = _time_ms(plain, 5, F.sync)
+        tb = _time_ms(persistent, 5, F.sync)
+        same &= bool(torch.equal(a, a2) and torch.equal(o, o2))
+        rows.append({"E_pct": pct, "E": [e250, e150],
+                     "plain_pairs_per_s": 2 * n3 / (tp * 1e-3),
+                     "persistent_pairs_per_s": 2 * n3 / (tb * 1e-3),
+                     "plain_ms": tp, "persistent_ms": tb})
+    return {"workload": "10M x 250 bp + 10M x 150 bp, edit rate U[0,0.12], "
+                        "E = 0..10 % of length",
+            "per_E": rows, "results_identical": same}
+
+
+def run_serving(seconds: float) -> dict:
+    """Requests of 1..4096 pairs (log-uniform), lengths log-uniform
+    100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
+    Poisson process at 30 %, 60 % and 90 % of the measured capacity."""
+    import torch
+
+    from paper_1910_09020_gb300 import binding, synth
+    pool = []
+    for i in range(96):
+        rng = np.random.default_rng(1910_09020 + 5 + i)
+        n = int(np.exp(rng.uniform(0, np.log(4096))))
+        L = synth.log_uniform(1910_09020 + 5000 + i, 0, n, 100, 100000)
+        E = synth.thresholds(L, 10)
+        reads, refs, _ = synth.pairs_varlen(1910_09020 + 50000 + i, 0, L,
+                                            synth.rate_recipe(0.15))
+        pinned = []
+        for a in (reads, refs):  # pinned host memory copies fastest
+            t = torch.empty(max(len(a), 1), dtype=torch.uint8,
+                            pin_memory=True)
+            t.numpy()[:len(a)] = a
+            pinned.append(t.numpy()[:len(a)])
+        pool.append((pinned[0], pinned[1], L, E))
+    slots = 2
+    out = {"workload": "requests of 1..4096 pairs (log-uniform), lengths "
+                       "log-uniform 100..100000 bp, edit rate U[0,0.15], "
+                       "E = 10 % of length, Poisson arrivals",
+           "slots": slots}
+    with binding.Server(0, hbm_budget_bytes=32 << 30, slots=slots) as S:
+        # capacity: the whole pool at once, twice (the first warms up)
+        for rep in range(2):
+            S.reset_stats()
+            t0 = time.perf_counter()
+            ts = [S.submit(*r) for r in pool]
+            for t in ts:
+                S.wait(t)
+            dt = time.perf_counter() - t0
+            for t in ts:
+                S.fetch(t)
+        pairs = sum(len(r[2]) for r in pool)
+        cap_pairs = pairs / dt
+        cap_req = len(pool) / dt
+        out["capacity"] = {"pairs_per_s": cap_pairs, "requests_per_s": cap_req,
+                           "gbases_per_s": sum(int(r[2].sum()) for r in pool)
+                           / dt / 1e9}
+        loads = []
+        for frac in (0.3, 0.6, 0.9):
+            rate = frac * cap_req
+            nreq = max(20, int(rate * seconds))
+            arr = synth.poisson_arrivals(1910_09020 + int(frac * 100), nreq,
+                                         rate)
+            pick = np.random.default_rng(int(frac * 1000)).integers(
+                0, len(pool), nreq)
+            S.reset_stats()
+            tickets = []
+            t0 = time.perf_counter()
+            for k in range(nreq):
+                delay = arr[k] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(S.submit(*pool[pick[k]]))
+            for t in tickets:
+                S.wait(t)
+            span = time.perf_counter() - t0
+            st = S.stats()
+            for t in tickets:
+                S.fetch(t)
+            npairs = int(sum(len(pool[i][2]) for i in pick))
+            loads.append({"offered_load": frac,
+                          "offered_requests_per_s": rate,
+                          "requests": nreq, "pairs": npairs,
+                          "pairs_per_s": npairs / span,
+                          "p50_s": st["latency_p50_s"],
+                          "p99_s": st["latency_p99_s"],
+                          "max_s": st["latency_max_s"],
+                          "batches": st["batches"],
+                          "max_inflight": st["max_inflight"]})
+        out["loads"] = loads
+    return out
+
+
 # ---- our arm ---------------------------------------------------------------------
 
 def run_ours(args):
@@ -449,6 +749,17 @@ def run_ours(args):
         "int_peaks_tops": {k: v / 1e12 for k, v in ipk.items()},
         "per_launch": per_launch,
     }
+    extras = {}
+    if not args.headline_only and world == 1:
+        del dq, dr, pq, pr
+        torch.cuda.empty_cache()
+        extras["persistent_uneven_batch"] = run_batched(
+            F, ipk, peaks["hbm_gbs"], not args.no_cpu,
+            n=args.batched_pairs)
+        torch.cuda.empty_cache()
+        extras["plain_vs_persistent_two_lengths"] = run_two_lengths(F)
+        torch.cuda.empty_cache()
+        extras["served"] = run_serving(args.serve_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s",
         "gbases_per_s": value * M / 1e9, "n_gpus": world,
@@ -462,6 +773,7 @@ def run_ours(args):
         "breakdown": {"pack_ms": pack_ms, "filter_ms": filter_ms,
                       "pack_gbs": n * PACK_BYTES_PER_PAIR / (pack_ms * 1e-3)
                       / 1e9, "generate_s": gen_s},
+        **extras,
     }
     print(json.dumps(line), flush=True)
     F.close()
@@ -471,10 +783,26 @@ def run_ours(args):
     return 0
 
 
+def run_batched_only(args):
+    """The persistent launch of the uneven batch alone (profiling aid)."""
+    import torch
+
+    from paper_1910_09020_gb300 import binding
+    torch.cuda.set_device(0)
+    F = binding.Filter(0, workspace_bytes=8 << 30)
+    out = run_batched(F, None, measured_peaks()["hbm_gbs"], False,
+                      per_length_too=False, n=args.batched_pairs)
+    print(json.dumps(out), flush=True)
+    F.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched_only(args)
     return run_ours(args)
 
 
