@@ -264,6 +264,7 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
     a.m = m;
     a.w16 = (m + 15) / 16;
     a.w16_magic = div_magic((uint32_t)std::max(a.w16, 1));
+    a.neg1 = 0xffffffffu;
     a.acc = acc;
     a.obs = obs;
     const size_t smem =

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(128) k_rw_bucket(const CwArgs a)
             const int w16 = (m + 15) >> 4;
             const GlobalSeq q{a.ps.reads + off, w16};
             const GlobalSeq r{a.ps.refs + off, w16};
-            const int cnt = rw_route<EMAX, false>(q, r, m, E);
+            const int cnt = rw_route<EMAX, false>(q, r, m, E, a.neg1);
             a.ps.acc[p] = (uint8_t)(cnt <= E);
             a.ps.obs[p] = cnt;
         }

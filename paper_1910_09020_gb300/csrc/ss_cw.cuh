@@ -144,6 +144,7 @@ struct CwArgs {
     BucketWs ws;
     int cls;
     int slice_words;  // shared words per staged pair
+    uint32_t neg1 = 0xffffffffu;  // passed at run time (see rw_route)
 };
 
 // Warp per pair; blockDim.x / 32 warps, each with its own slice.

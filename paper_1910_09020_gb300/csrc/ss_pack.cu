@@ -70,30 +70,89 @@ __device__ __forceinline__ uint32_t pack16(const uint8_t *__restrict__ src,
     return lo | (hi << 16);
 }
 
-// Fixed stride: pair p at byte p*m, output at word p*w16.
-__global__ void k_pack_fixed(const uint8_t *__restrict__ ascii, int64_t n,
-                             int32_t m, int32_t w16, uint32_t w16_magic,
-                             uint32_t *__restrict__ out, int *status)
+// Fixed stride: pair p at byte p*m, output at word p*w16.  A CTA writes
+// kPackWords consecutive output words; the ASCII bytes behind them are one
+// contiguous span, which the CTA first copies to shared memory with 16-byte
+// loads (every thread keeps several loads in flight), then each thread builds
+// its words from shared memory.
+constexpr int kPackThreads = 256;
+constexpr int kPackWords = 1024;  // output words per CTA (4 per thread)
+constexpr int kPackSpan = kPackWords * 16 + 32;  // staged bytes, with slack
+
+__global__ void __launch_bounds__(kPackThreads)
+    k_pack_fixed(const uint8_t *__restrict__ ascii, int64_t n, int32_t m,
+                 int32_t w16, uint32_t w16_magic, uint32_t *__restrict__ out,
+                 int *status)
 {
+    __shared__ __align__(16) uint8_t span[kPackSpan];
     const int64_t total = n * (int64_t)w16;
-    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t g0 = (int64_t)blockIdx.x * kPackWords;
     if (g0 >= total)
         return;
-    // pair/word of the block's first word; the rest by 32-bit magic division
-    const int64_t p0 = g0 / w16;
-    const uint32_t w0 = (uint32_t)(g0 - p0 * w16);
-    const int64_t g = g0 + threadIdx.x;
+    const int64_t g1 = min(g0 + (int64_t)kPackWords, total);  // exclusive
+    const int64_t pa = g0 / w16;
+    const int wa = (int)(g0 - pa * w16);
+    const int64_t pb = (g1 - 1) / w16;
+    const int wb = (int)(g1 - 1 - pb * w16);
+    const int64_t b0 = pa * m + 16 * (int64_t)wa;             // first byte
+    const int64_t b1 = pb * m + min(16 * (wb + 1), m);         // end byte
+    const int64_t base = b0 & ~(int64_t)15;
+    const int64_t limit = n * (int64_t)m;                      // input size
+    // stage [base, b1) -- full 16-byte chunks inside the input, bytes else
+    const int chunks = (int)((b1 - base + 15) >> 4);
+    const uint4 *src = reinterpret_cast<const uint4 *>(ascii + base);
+    uint4 *dst = reinterpret_cast<uint4 *>(span);
+    const bool aligned = ((uintptr_t)ascii & 15) == 0;
+    for (int c = threadIdx.x; c < chunks; c += kPackThreads) {
+        const int64_t at = base + 16 * (int64_t)c;
+        if (aligned && at + 16 <= limit) {
+            dst[c] = __ldg(src + c);
+        } else {
+            for (int k = 0; k < 16; ++k)
+                span[16 * c + k] = at + k < limit ? __ldg(ascii + at + k)
+                                                  : (uint8_t)0x41;
+        }
+    }
+    __syncthreads();
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(span);
     bool bad = false;
-    if (g < total) {
-        const uint32_t off = w0 + threadIdx.x;
-        const uint32_t dp = fast_div(off, (uint32_t)w16, w16_magic);
-        const int64_t p = p0 + dp;
-        const int w = (int)(off - dp * (uint32_t)w16);
-        const uint8_t *src = ascii + p * (int64_t)m + (int64_t)w * 16;
-        const int len = min(16, m - w * 16);
-        bool valid;
-        out[g] = pack16(src, len, ((uintptr_t)src & 3) == 0, valid);
-        bad = !valid;
+    const uint32_t first = (uint32_t)wa;
+#pragma unroll
+    for (int k = 0; k < kPackWords / kPackThreads; ++k) {
+        const int j = k * kPackThreads + threadIdx.x;
+        const int64_t g = g0 + j;
+        if (g >= g1)
+            break;
+        // pair and word of output g, relative to the CTA's first pair
+        const uint32_t rel = first + (uint32_t)j;
+        const uint32_t dp = fast_div(rel, (uint32_t)w16, w16_magic);
+        const int w = (int)(rel - dp * (uint32_t)w16);
+        const int64_t p = pa + dp;
+        const int off = (int)(p * m + 16 * (int64_t)w - base);
+        const int len = min(16, m - 16 * w);
+        const int a = off >> 2, sh = (off & 3) * 8;
+        uint32_t x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            x[q] = funnel_r(s32[a + q], s32[a + q + 1], (uint32_t)sh);
+        uint32_t lo = 0, hi = 0;
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // bytes past the sequence's end count as 'A' (code 0)
+            const int keep = len - 4 * q;
+            uint32_t v = x[q];
+            if (keep < 4) {
+                const uint32_t km = keep <= 0 ? 0u : (0xffffffffu >> (32 - 8 * keep));
+                v = (v & km) | (0x41414141u & ~km);
+            }
+            uint32_t l4, h4;
+            ok &= codes4(v, l4, h4);
+            lo |= l4 << (4 * q);
+            hi |= h4 << (4 * q);
+        }
+        out[g] = lo | (hi << 16);
+        bad |= !ok;
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
         atomicOr(status, kStatusInvalidBase);
@@ -143,9 +202,10 @@ cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,
         return cudaSuccess;
     const int32_t w16 = (m + 15) / 16;
     const int64_t total = n * (int64_t)w16;
-    const int threads = 256;
-    const int64_t blocks = (total + threads - 1) / threads;
-    k_pack_fixed<<<(unsigned)blocks, threads, 0, st>>>(
+    const int64_t blocks = (total + kPackWords - 1) / kPackWords;
+    if (blocks > 0x7fffffff)
+        return cudaErrorInvalidValue;
+    k_pack_fixed<<<(unsigned)blocks, kPackThreads, 0, st>>>(
         ascii, n, m, w16, div_magic((uint32_t)w16), out, status);
     return cudaGetLastError();
 }

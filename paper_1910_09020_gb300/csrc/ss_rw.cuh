@@ -66,8 +66,10 @@ struct GlobalSeq {
 
 // Route one pair of length m with threshold E (E == EMAX when EXACT);
 // returns min(count, E+1).  Rows |s| > min(E, EMAX) are never built.
+// neg1 must hold 0xffffffff: negation is done as a multiply by it, which
+// issues on the FMA pipe and leaves the busier ALU pipe to the logic ops.
 template <int EMAX, bool EXACT, class Seq>
-SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E)
+SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
 {
     constexpr int NR = 2 * EMAX + 1;
     const int W32 = (m + 31) >> 5;
@@ -120,13 +122,13 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E)
                 for (int r = 0; r < NR; ++r) {
                     const uint32_t x = (Z[r] & M) |
                                        (0u - (uint32_t)((deadbits >> r) & 1u));
-                    A &= x | (0u - x);
+                    A &= x | (x * neg1);
                 }
             } else {
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const uint32_t x = Z[r] & M;
-                    A &= x | (0u - x);
+                    A &= x | (x * neg1);
                 }
             }
             if (A == 0u) {
@@ -171,40 +173,116 @@ struct RwUniformArgs {
     int32_t m;
     int32_t w16;
     uint32_t w16_magic;
+    uint32_t neg1;          // 0xffffffff (see rw_route)
     uint8_t *acc;
     int32_t *obs;
 };
 
+// Predicted routing cost of a staged pair: mismatches on the main diagonal
+// over its first 32 bases (0..31).  Random pairs score high and are
+// rejected early; similar pairs score low and route to the end.
+__device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
+                                           const uint32_t *sr, int ld,
+                                           int w16)
+{
+    int mism = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (i < w16) {
+            const uint32_t x = sq[i * ld] ^ sr[i * ld];
+            mism += __popc((x | (x >> 16)) & 0xffffu);
+        }
+    return mism < 31 ? mism : 31;
+}
+
 // Plain launch: uniform m and E, one thread per pair, one CTA per T pairs.
+// The CTA stages its pairs (128-bit loads when aligned), orders them by a
+// predicted routing cost so that each warp holds pairs of similar cost (the
+// warp then diverges less), routes them, and writes each result at the
+// pair's own index.
 template <int E>
 __global__ void __launch_bounds__(128)
     k_rw_uniform(const RwUniformArgs a)
 {
     extern __shared__ uint32_t smem[];
-    const int T = blockDim.x;
+    __shared__ int s_cnt[32];
+    __shared__ uint8_t s_perm[128];
+    const int T = blockDim.x;  // 128
     const int ld = T + 1;
+    const int t = threadIdx.x;
     const int64_t p0 = (int64_t)blockIdx.x * T;
     const int64_t left = a.n - p0;
     const int np = left < T ? (int)left : T;
     uint32_t *sQ = smem;
     uint32_t *sR = smem + (size_t)a.w16 * ld;
-    const int total = np * a.w16;
-    const uint32_t *gq = a.reads + p0 * a.w16;
-    const uint32_t *gr = a.refs + p0 * a.w16;
-    for (int idx = threadIdx.x; idx < total; idx += T) {
-        const uint32_t t = fast_div((uint32_t)idx, (uint32_t)a.w16,
+    const int w16 = a.w16;
+    const int total = np * w16;
+    const uint32_t *gq = a.reads + p0 * w16;
+    const uint32_t *gr = a.refs + p0 * w16;
+    if (t < 32)
+        s_cnt[t] = 0;
+    // stage, transposed: packed word i of pair u at [i * ld + u]
+    int done = 0;
+    if (((((uintptr_t)gq) | ((uintptr_t)gr)) & 15) == 0) {
+        const int nv = total >> 2;
+        const uint4 *vq = reinterpret_cast<const uint4 *>(gq);
+        const uint4 *vr = reinterpret_cast<const uint4 *>(gr);
+        for (int v = t; v < nv; v += T) {
+            const uint4 q = __ldg(vq + v), r = __ldg(vr + v);
+            const uint32_t idx = (uint32_t)v * 4u;
+            uint32_t u = fast_div(idx, (uint32_t)w16, a.w16_magic);
+            uint32_t i = idx - u * (uint32_t)w16;
+            const uint32_t qq[4] = {q.x, q.y, q.z, q.w};
+            const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sQ[i * ld + u] = qq[c];
+                sR[i * ld + u] = rr[c];
+                if (++i == (uint32_t)w16) {
+                    i = 0;
+                    ++u;
+                }
+            }
+        }
+        done = nv * 4;
+    }
+    for (int idx = done + t; idx < total; idx += T) {
+        const uint32_t u = fast_div((uint32_t)idx, (uint32_t)w16,
                                     a.w16_magic);
-        const uint32_t i = (uint32_t)idx - t * (uint32_t)a.w16;
-        sQ[i * ld + t] = __ldg(gq + idx);
-        sR[i * ld + t] = __ldg(gr + idx);
+        const uint32_t i = (uint32_t)idx - u * (uint32_t)w16;
+        sQ[i * ld + u] = __ldg(gq + idx);
+        sR[i * ld + u] = __ldg(gr + idx);
     }
     __syncthreads();
-    if (threadIdx.x < np) {
-        const SmemSeq q{sQ + threadIdx.x, ld, a.w16};
-        const SmemSeq r{sR + threadIdx.x, ld, a.w16};
-        const int cnt = rw_route<E, true>(q, r, a.m, E);
-        a.acc[p0 + threadIdx.x] = (uint8_t)(cnt <= E);
-        a.obs[p0 + threadIdx.x] = cnt;
+    // counting sort of the CTA's pairs by predicted cost
+    int key = 0, rank = 0;
+    if (t < np) {
+        key = rw_cost_key(sQ + t, sR + t, ld, w16);
+        rank = atomicAdd(&s_cnt[key], 1);
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int c = s_cnt[t];
+        int x = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (t >= off)
+                x += y;
+        }
+        s_cnt[t] = x - c;  // exclusive start of bucket t
+    }
+    __syncthreads();
+    if (t < np)
+        s_perm[s_cnt[key] + rank] = (uint8_t)t;
+    __syncthreads();
+    if (t < np) {
+        const int u = s_perm[t];
+        const SmemSeq q{sQ + u, ld, w16};
+        const SmemSeq r{sR + u, ld, w16};
+        const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
+        a.acc[p0 + u] = (uint8_t)(cnt <= E);
+        a.obs[p0 + u] = cnt;
     }
 }
 

@@ -16,7 +16,8 @@ template <int E>
 int exact_one(const uint32_t *q, const uint32_t *r, int m)
 {
     const int w16 = (m + 15) / 16;
-    return rw_route<E, true>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E);
+    return rw_route<E, true>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E,
+                             0xffffffffu);
 }
 
 template <int... Es>
@@ -32,7 +33,8 @@ template <int EMAX>
 int runtime_one(const uint32_t *q, const uint32_t *r, int m, int E)
 {
     const int w16 = (m + 15) / 16;
-    return rw_route<EMAX, false>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E);
+    return rw_route<EMAX, false>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E,
+                                 0xffffffffu);
 }
 
 template <int K>

@@ -1,0 +1,158 @@
+"""Parity at the benchmark's full sizes, in the launch configurations
+bench.py times, on sampled outputs the oracle computes one by one:
+
+* 30M x 100 bp, E = 0, 2, ..., 10, plain launches (the headline sweep);
+* 10M x 250 bp + 10M x 150 bp at E = 0 %, 5 %, 10 %, plain and persistent;
+* the uneven 2M-pair batch (64..10000 bp, E = 5 %), one bucketed graph;
+* full-shape served requests (up to 4096 pairs, 100..100000 bp, E = 10 %).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_09020_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1910_09020
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU test without a GPU"
+    return torch
+
+
+def _check_sample(acc, obs, idx, reads, refs, m, E, what):
+    oa, oo = oracle.filter_batch(reads[idx], refs[idx], m, E)
+    ga, go = acc[idx], obs[idx]
+    bad = np.nonzero((ga != oa) | (go != oo))[0]
+    assert len(bad) == 0, (what, idx[bad[:5]], ga[bad[:5]], oa[bad[:5]])
+
+
+def test_headline_sweep_30M_sampled():
+    torch = _torch()
+    n, m = 30_000_000, 100
+    hq = torch.empty(n * m, dtype=torch.uint8, pin_memory=True)
+    hr = torch.empty(n * m, dtype=torch.uint8, pin_memory=True)
+    synth.pairs_fixed(SEED + 2, 0, n, m, synth.SHORT_POISSON,
+                      out=(hq.numpy(), hr.numpy()))
+    reads, refs = hq.numpy().reshape(n, m), hr.numpy().reshape(n, m)
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 20000),
+                                    np.arange(0, 300), np.arange(n - 300, n)]))
+    with binding.Filter(0) as F:
+        q = F.pack(hq.cuda(), m=m, n=n)
+        r = F.pack(hr.cuda(), m=m, n=n)
+        for E in (0, 2, 4, 6, 8, 10):
+            acc, obs = F.filter(q, r, m=m, e=E, n=n, sync=True)
+            _check_sample(acc.cpu().numpy(), obs.cpu().numpy(), idx, reads,
+                          refs, m, E, f"sweep E={E}")
+
+
+def test_two_lengths_20M_sampled_both_forms():
+    torch = _torch()
+    n3 = 10_000_000
+    rec = synth.rate_recipe(0.12)
+    r250 = synth.pairs_fixed(SEED + 3, 0, n3, 250, rec)
+    r150 = synth.pairs_fixed(SEED + 3, n3, n3, 150, rec)
+    rng = np.random.default_rng(2)
+    i250 = np.unique(rng.integers(0, n3, 6000))
+    i150 = np.unique(rng.integers(0, n3, 6000))
+    with binding.Filter(0, workspace_bytes=2 << 30) as F:
+        bufs = []
+        for (rd, rf), m in ((r250, 250), (r150, 150)):
+            bufs.append((F.pack(torch.from_numpy(rd.reshape(-1)).cuda(), m=m,
+                                n=n3),
+                         F.pack(torch.from_numpy(rf.reshape(-1)).cuda(), m=m,
+                                n=n3)))
+        allq = torch.cat([bufs[0][0], bufs[1][0]])
+        allr = torch.cat([bufs[0][1], bufs[1][1]])
+        offs = torch.cat([torch.arange(n3, dtype=torch.int64) * 16,
+                          n3 * 16 + torch.arange(n3, dtype=torch.int64) * 10]
+                         ).cuda()
+        lens = torch.cat([torch.full((n3,), 250, dtype=torch.int32),
+                          torch.full((n3,), 150, dtype=torch.int32)]).cuda()
+        for pct in (0, 5, 10):
+            e250, e150 = 250 * pct // 100, 150 * pct // 100
+            a1, o1 = F.filter(bufs[0][0], bufs[0][1], m=250, e=e250, n=n3,
+                              sync=True)
+            a2, o2 = F.filter(bufs[1][0], bufs[1][1], m=150, e=e150, n=n3,
+                              sync=True)
+            Es = torch.cat([torch.full((n3,), e250, dtype=torch.int32),
+                            torch.full((n3,), e150, dtype=torch.int32)]).cuda()
+            ab, ob = F.filter(allq, allr, offsets=offs, lengths=lens, E=Es,
+                              sync=True)
+            assert torch.equal(torch.cat([a1, a2]), ab)
+            assert torch.equal(torch.cat([o1, o2]), ob)
+            _check_sample(a1.cpu().numpy(), o1.cpu().numpy(), i250, r250[0],
+                          r250[1], 250, e250, f"250 bp {pct}%")
+            _check_sample(a2.cpu().numpy(), o2.cpu().numpy(), i150, r150[0],
+                          r150[1], 150, e150, f"150 bp {pct}%")
+
+
+def test_uneven_2M_batch_sampled():
+    torch = _torch()
+    n = 2_000_000
+    L = np.sort(synth.log_uniform(SEED + 4, 0, n, 64, 10000)).astype(np.int32)
+    E = synth.thresholds(L, 5)
+    reads, refs, off = synth.pairs_varlen(SEED + 4, 0, L,
+                                          synth.rate_recipe(0.10))
+    words = (L.astype(np.int64) + 15) // 16
+    woff = np.zeros(n + 1, np.int64)
+    np.cumsum(words, out=woff[1:])
+    with binding.Filter(0, workspace_bytes=2 << 30) as F:
+        dL = torch.from_numpy(L).cuda()
+        dwo = torch.from_numpy(woff[:-1].copy()).cuda()
+        doff = torch.from_numpy(off[:-1].copy()).cuda()
+        pq = torch.empty(int(woff[-1]), dtype=torch.int32, device="cuda")
+        pr = torch.empty_like(pq)
+        F.pack(torch.from_numpy(reads).cuda(), offsets=doff, lengths=dL,
+               out=pq, out_offsets=dwo)
+        F.pack(torch.from_numpy(refs).cuda(), offsets=doff, lengths=dL,
+               out=pr, out_offsets=dwo)
+        F.autotune(pq, pr, offsets=dwo, lengths=dL,
+                   E=torch.from_numpy(E).cuda(), reps=1)
+        acc, obs = F.filter(pq, pr, offsets=dwo, lengths=dL,
+                            E=torch.from_numpy(E).cuda(), sync=True)
+        acc, obs = acc.cpu().numpy(), obs.cpu().numpy()
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 2500),
+                                    np.arange(n - 50, n)]))
+    sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in idx])
+    sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in idx])
+    so = np.zeros(len(idx) + 1, np.int64)
+    np.cumsum(L[idx], out=so[1:])
+    oa, oo = oracle.filter_batch(sub_r, sub_f, L[idx], E[idx], offsets=so)
+    assert (acc[idx] == oa).all() and (obs[idx] == oo).all()
+
+
+def test_served_full_shape_requests_sampled():
+    reqs = []
+    for i in range(6):
+        rng = np.random.default_rng(SEED + 5 + i)
+        n = int(np.exp(rng.uniform(0, np.log(4096))))
+        L = synth.log_uniform(SEED + 5000 + i, 0, n, 100, 100000)
+        E = synth.thresholds(L, 10)
+        reads, refs, off = synth.pairs_varlen(SEED + 50000 + i, 0, L,
+                                              synth.rate_recipe(0.15))
+        reqs.append((reads, refs, L, E, off))
+    with binding.Server(0, hbm_budget_bytes=16 << 30, slots=2) as S:
+        ts = [S.submit(r[0], r[1], r[2], r[3]) for r in reqs]
+        outs = []
+        for t in ts:
+            assert S.wait(t) == binding.SS_OK
+            outs.append(S.fetch(t))
+    rng = np.random.default_rng(4)
+    for (rc, acc, obs, _), (reads, refs, L, E, off) in zip(outs, reqs):
+        assert rc == binding.SS_OK
+        # sample: a few pairs per request, the longest included
+        k = min(len(L), 6)
+        idx = np.unique(np.concatenate([rng.integers(0, len(L), k),
+                                        [int(np.argmax(L))]]))
+        sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in idx])
+        sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in idx])
+        so = np.zeros(len(idx) + 1, np.int64)
+        np.cumsum(L[idx], out=so[1:])
+        oa, oo = oracle.filter_batch(sub_r, sub_f, L[idx], E[idx], offsets=so)
+        assert (acc[idx] == oa).all() and (obs[idx] == oo).all()
