@@ -17,20 +17,23 @@
 namespace ssk {
 
 // Four ASCII bytes -> 4 code-bit-0 bits, 4 code-bit-1 bits; false if any
-// byte is not a base.  Missing bytes must be passed as 'A'.
+// byte is not a base.  Missing bytes must be passed as 'A'.  With
+// y = x ^ (x >> 1), code bit 0 = y bit 1 and code bit 1 = y bit 2 of every
+// byte (bit 5, the case bit, does not enter), so one shift and one XOR
+// serve both bits.
 __device__ __forceinline__ bool codes4(uint32_t x, uint32_t &lo4,
                                        uint32_t &hi4)
 {
-    const uint32_t v = x | 0x20202020u;
-    const uint32_t k0 = ((v >> 1) ^ (v >> 2)) & 0x01010101u;
-    const uint32_t k1 = ((v >> 2) ^ (v >> 3)) & 0x01010101u;
-    // canonical lower-case letter per code: 'a' + {0, 2, 6, 19}[code]
-    const uint32_t canon =
-        0x61616161u + (k0 << 1) + k1 * 6u + (k0 & k1) * 11u;
-    // gather bits at 0, 8, 16, 24 into bits 0..3 (no carries can occur)
+    const uint32_t y = x ^ (x >> 1);
+    const uint32_t k0 = (y >> 1) & 0x01010101u;
+    const uint32_t k1 = (y >> 2) & 0x01010101u;
+    // gather bits 0, 8, 16, 24 into bits 0..3 (no carries can occur)
     lo4 = (k0 * 0x10204080u) >> 28;
     hi4 = (k1 * 0x10204080u) >> 28;
-    return v == canon;
+    // canonical lower-case letter per code: 'a' + {0, 2, 6, 19}[code]
+    const uint32_t canon =
+        0x61616161u + k0 * 2u + k1 * 6u + (k0 & k1) * 11u;
+    return (x | 0x20202020u) == canon;
 }
 
 // Pack up to 16 bases starting at src (len in 1..16).
@@ -116,43 +119,48 @@ __global__ void __launch_bounds__(kPackThreads)
     __syncthreads();
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(span);
     bool bad = false;
-    const uint32_t first = (uint32_t)wa;
+    // byte offset in the span of the CTA's first pair
+    const int off0 = (int)(pa * m - base);
 #pragma unroll
     for (int k = 0; k < kPackWords / kPackThreads; ++k) {
         const int j = k * kPackThreads + threadIdx.x;
-        const int64_t g = g0 + j;
-        if (g >= g1)
-            break;
-        // pair and word of output g, relative to the CTA's first pair
-        const uint32_t rel = first + (uint32_t)j;
-        const uint32_t dp = fast_div(rel, (uint32_t)w16, w16_magic);
-        const int w = (int)(rel - dp * (uint32_t)w16);
-        const int64_t p = pa + dp;
-        const int off = (int)(p * m + 16 * (int64_t)w - base);
-        const int len = min(16, m - 16 * w);
-        const int a = off >> 2, sh = (off & 3) * 8;
-        uint32_t x[4];
+        if (g0 + j < g1) {
+            // pair (relative to the CTA's first) and word of output g0 + j
+            const uint32_t rel = (uint32_t)wa + (uint32_t)j;
+            const uint32_t dp = fast_div(rel, (uint32_t)w16, w16_magic);
+            const int w = (int)(rel - dp * (uint32_t)w16);
+            const int off = off0 + (int)dp * m + 16 * w;
+            const int len = m - 16 * w;  // >= 16 except on a pair's last word
+            const int a = off >> 2;
+            const uint32_t sh = (uint32_t)(off & 3) * 8u;
+            uint32_t x[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            x[q] = funnel_r(s32[a + q], s32[a + q + 1], (uint32_t)sh);
-        uint32_t lo = 0, hi = 0;
-        bool ok = true;
+            for (int q = 0; q < 4; ++q)
+                x[q] = funnel_r(s32[a + q], s32[a + q + 1], sh);
+            if (len < 16) {
+                // bytes past the sequence's end count as 'A' (code 0)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            // bytes past the sequence's end count as 'A' (code 0)
-            const int keep = len - 4 * q;
-            uint32_t v = x[q];
-            if (keep < 4) {
-                const uint32_t km = keep <= 0 ? 0u : (0xffffffffu >> (32 - 8 * keep));
-                v = (v & km) | (0x41414141u & ~km);
+                for (int q = 0; q < 4; ++q) {
+                    const int keep = len - 4 * q;
+                    const uint32_t km =
+                        keep <= 0 ? 0u
+                                  : (keep >= 4 ? 0xffffffffu
+                                               : (0xffffffffu >> (32 - 8 * keep)));
+                    x[q] = (x[q] & km) | (0x41414141u & ~km);
+                }
             }
-            uint32_t l4, h4;
-            ok &= codes4(v, l4, h4);
-            lo |= l4 << (4 * q);
-            hi |= h4 << (4 * q);
+            uint32_t lo = 0, hi = 0;
+            bool ok = true;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t l4, h4;
+                ok &= codes4(x[q], l4, h4);
+                lo += l4 << (4 * q);
+                hi += h4 << (4 * q);
+            }
+            out[g0 + j] = lo | (hi << 16);
+            bad |= !ok;
         }
-        out[g] = lo | (hi << 16);
-        bad |= !ok;
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
         atomicOr(status, kStatusInvalidBase);

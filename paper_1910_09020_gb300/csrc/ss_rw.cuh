@@ -31,6 +31,7 @@
 //    all-obstacle rows, which never bound the longest run.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "ss_device.cuh"
 
@@ -72,9 +73,12 @@ template <int EMAX, bool EXACT, class Seq>
 SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
 {
     constexpr int NR = 2 * EMAX + 1;
+    // bitmask of rows that met an obstacle since the checkpoint (crossing)
+    using RowBits = typename std::conditional<(NR <= 32), uint32_t,
+                                              uint64_t>::type;
     const int W32 = (m + 31) >> 5;
     uint32_t Z[NR];
-    uint64_t deadbits = 0;  // rows that met an obstacle since c (crossing)
+    RowBits deadbits = 0;
 
     uint32_t qlo_p = 0u, qhi_p = 0u, qlo_c, qhi_c, qlo_n, qhi_n;
     Qs.planes(0, qlo_c, qhi_c);
@@ -87,7 +91,14 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
         uint32_t rlo, rhi;
         Rs.planes(k, rlo, rhi);
         const bool edge = (k == 0) || (base + 32 + EMAX > m);
-        // Eq. 1 for the 32 columns of word k, every row.
+        // "Q base exists" plane around word k (bits of Q indices in 0..m-1),
+        // shifted with each row like Q itself: Eq. 1 case 4.
+        const uint32_t v_p = k == 0 ? 0u : 0xffffffffu;
+        const uint32_t v_c = mask_below(m - base);
+        const uint32_t v_n = mask_below(m - base - 32);
+        // Eq. 1 for the 32 columns of word k, every row.  Columns past m are
+        // not masked: whatever they hold can only place the longest run's end
+        // at or beyond m, which is read as "reached the destination".
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int s = r - EMAX;
@@ -99,13 +110,13 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
                 ql = funnel_l(qlo_p, qlo_c, -s);
                 qh = funnel_l(qhi_p, qhi_c, -s);
             }
-            uint32_t z = (ql ^ rlo) | (qh ^ rhi);
+            uint32_t z;
             if (edge) {
-                // case 4: Q index below 1 (word 0 only) or above m; columns
-                // past m act as a sentinel (tested as "reached the end").
-                if (s < 0)
-                    z |= mask_below(-s - base);
-                z |= mask_from((s > 0 ? m - s : m) - base);
+                const uint32_t qv = s >= 0 ? funnel_r(v_c, v_n, s)
+                                           : funnel_l(v_p, v_c, -s);
+                z = (ql ^ rlo) | (qh ^ rhi) | ~qv;
+            } else {
+                z = (ql ^ rlo) | (qh ^ rhi);
             }
             if (!EXACT && (s > E || -s > E))
                 z = 0xffffffffu;  // row outside this pair's 2E+1
@@ -120,8 +131,9 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
                 // met an obstacle since the checkpoint do not count
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    const uint32_t x = (Z[r] & M) |
-                                       (0u - (uint32_t)((deadbits >> r) & 1u));
+                    const uint32_t x =
+                        (Z[r] & M) |
+                        (0u - (uint32_t)((deadbits >> r) & (RowBits)1));
                     A &= x | (x * neg1);
                 }
             } else {
@@ -133,10 +145,10 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
             }
             if (A == 0u) {
                 // a live row runs past the word end: remember the others
-                uint64_t d = deadbits;
+                RowBits d = deadbits;
 #pragma unroll
                 for (int r = 0; r < NR; ++r)
-                    d |= (uint64_t)((Z[r] & M) != 0u) << r;
+                    d |= (RowBits)((Z[r] & M) != 0u) << r;
                 deadbits = d;
                 break;
             }
