@@ -749,6 +749,24 @@ def run_ours(args):
         "int_peaks_tops": {k: v / 1e12 for k, v in ipk.items()},
         "per_launch": per_launch,
     }
+    # accuracy of the decisions just timed (Section 3.2's rates), against the
+    # banded edit-distance verifier; outside the timed region
+    accuracy = []
+    for t, E in enumerate(SWEEP):
+        ed = F.edit_distance(pq, pr, m=M, e=E, n=n)
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+            enable_timing=True)
+        ev_a.record()
+        F.edit_distance(pq, pr, m=M, e=E, n=n, out=ed)
+        ev_b.record()
+        ta, fa, fr, tr = F.confusion(acc[t], ed, e=E)
+        accuracy.append({"E": E, "true_accepts": ta, "false_accepts": fa,
+                         "false_rejects": fr, "true_rejects": tr,
+                         "false_accept_rate": fa / max(fa + tr, 1),
+                         "false_reject_rate": fr / max(fr + ta, 1),
+                         "verifier_ms": ev_a.elapsed_time(ev_b)})
+    F.sync()
+
     extras = {}
     if not args.headline_only and world == 1:
         del dq, dr, pq, pr
@@ -773,6 +791,7 @@ def run_ours(args):
         "breakdown": {"pack_ms": pack_ms, "filter_ms": filter_ms,
                       "pack_gbs": n * PACK_BYTES_PER_PAIR / (pack_ms * 1e-3)
                       / 1e9, "generate_s": gen_s},
+        "accuracy": accuracy,
         **extras,
     }
     print(json.dumps(line), flush=True)

@@ -170,6 +170,26 @@ int ss_autotune(ss_ctx *ctx, const void *reads, const void *refs,
                 uint8_t *out_accept, int32_t *out_obstacles, int reps,
                 float *best_ms);
 
+/* ---- accuracy harness (Section 3.2: false accept / false reject rates
+ * against an aligner's ground truth) ----------------------------------------
+ * ss_edit_distance_banded: for n fixed-stride SS_FMT_PACKED2 pairs of length
+ * m, writes out_ed[p] = min(ED(Q_p, R_p), e + 1) (device int32[n]), the exact
+ * Levenshtein distance whenever it is <= e (banded DP over the 2e+1
+ * diagonals; any alignment of cost <= e stays inside them).  e <= 31, else
+ * SS_ERR_UNSUPPORTED.
+ * ss_filter_confusion: out_counts (device uint64[4]) receives, over n pairs
+ * with filter decisions accept[] and capped distances ed[] at threshold e:
+ * [0] accepted & ED <= e (true accepts), [1] accepted & ED > e (false
+ * accepts), [2] rejected & ED <= e (false rejects; 0 for a lossless filter),
+ * [3] rejected & ED > e (true rejects).  Both are asynchronous on `stream`.
+ * Return SS_OK, SS_ERR_INVALID_ARG, SS_ERR_UNSUPPORTED or SS_ERR_CUDA. */
+int ss_edit_distance_banded(ss_ctx *ctx, const void *reads, const void *refs,
+                            int format, int32_t m, int32_t e, int64_t n,
+                            void *stream, int32_t *out_ed);
+int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
+                        const int32_t *ed, int64_t n, int32_t e,
+                        void *stream, uint64_t *out_counts);
+
 /* ---- allocation-free entry point (the paper has no counterpart) -------
  * For callers that cannot allocate device memory: a service that reserves
  * all of a GPU's memory up front through its own allocator (an extra

@@ -37,7 +37,8 @@ EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
-    "ss_autotune", "ss_filter_batch_noalloc", "ss_server_create",
+    "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
+    "ss_filter_confusion", "ss_server_create",
     "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
     "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
 )
@@ -108,6 +109,9 @@ def load(build_if_needed: bool = True):
     lib.ss_get_counters.argtypes = [P, ctypes.POINTER(Counters)]
     lib.ss_filter_batch_noalloc.argtypes = [P, P, P, P, I32, P, I32, I64, P,
                                             P, P]
+    lib.ss_edit_distance_banded.argtypes = [P, P, P, ctypes.c_int, I32, I32,
+                                            I64, P, P]
+    lib.ss_filter_confusion.argtypes = [P, P, P, I64, I32, P, P]
     lib.ss_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, SZ,
                                      ctypes.c_int]
     lib.ss_server_submit.argtypes = [P, P, P, P, P, I64,
@@ -343,6 +347,29 @@ class Filter:
 
     def set_tuning(self, rw_max_e: int, cw_subgrid: int):
         _check(ss_set_tuning(self.ctx, rw_max_e, cw_subgrid), "ss_set_tuning")
+
+    def edit_distance(self, reads, refs, *, m: int, e: int, n=None,
+                      out=None, stream=None):
+        """min(ED, e+1) of fixed-stride packed pairs (device int32[n])."""
+        import torch
+        n = reads.shape[0] if n is None else n
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=reads.device)
+        rc = load().ss_edit_distance_banded(
+            self.ctx, _ptr(reads) or None, _ptr(refs) or None, SS_FMT_PACKED2,
+            m, e, n, _stream_handle(stream) or None, _ptr(out) or None)
+        _check(rc, "ss_edit_distance_banded")
+        return out
+
+    def confusion(self, accept, ed, *, e: int, stream=None):
+        """(true accepts, false accepts, false rejects, true rejects)."""
+        import torch
+        counts = torch.zeros(4, dtype=torch.int64, device=accept.device)
+        rc = load().ss_filter_confusion(
+            self.ctx, _ptr(accept), _ptr(ed), accept.shape[0], e,
+            _stream_handle(stream) or None, _ptr(counts))
+        _check(rc, "ss_filter_confusion")
+        return tuple(int(x) for x in counts.cpu().tolist())
 
     def sync(self, stream=None):
         """Wait for the stream (default: torch's current stream) and raise

@@ -617,6 +617,42 @@ int ss_get_counters(const ss_ctx *ctx, ss_counters *out)
     return SS_OK;
 }
 
+int ss_edit_distance_banded(ss_ctx *ctx, const void *reads, const void *refs,
+                            int format, int32_t m, int32_t e, int64_t n,
+                            void *stream, int32_t *out_ed)
+{
+    if (!ctx || n < 0 || m < 0 || e < 0)
+        return SS_ERR_INVALID_ARG;
+    if (format != SS_FMT_PACKED2)
+        return SS_ERR_INVALID_ARG;
+    if (e > ssk::kEdMaxE)
+        return SS_ERR_UNSUPPORTED;
+    if (n == 0)
+        return SS_OK;
+    if (!reads || !refs || !out_ed)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SS_CUDA(ssk::launch_ed_banded(e, (const uint32_t *)reads,
+                                  (const uint32_t *)refs, n, m, out_ed,
+                                  ctx->sm_count, pick_stream(stream)));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
+int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
+                        const int32_t *ed, int64_t n, int32_t e,
+                        void *stream, uint64_t *out_counts)
+{
+    if (!ctx || n < 0 || e < 0 || !out_counts || (n > 0 && (!accept || !ed)))
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SS_CUDA(ssk::launch_confusion(accept, ed, n, e,
+                                  (unsigned long long *)out_counts,
+                                  ctx->sm_count, pick_stream(stream)));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
 int ss_set_tuning(ss_ctx *ctx, int rw_max_e, int cw_subgrid)
 {
     if (!ctx || (rw_max_e != 15 && rw_max_e != 31) ||

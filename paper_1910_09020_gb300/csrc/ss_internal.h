@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <utility>
 
 namespace ssk {
 
@@ -42,6 +43,15 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
                             cudaStream_t st, cudaStream_t side,
                             cudaEvent_t fork, cudaEvent_t join,
                             int *launches);
+
+// Accuracy harness (ss_verify.cu): banded edit distance, E <= kEdMaxE.
+constexpr int kEdMaxE = 31;
+cudaError_t launch_ed_banded(int E, const uint32_t *reads,
+                             const uint32_t *refs, int64_t n, int32_t m,
+                             int32_t *ed, int sm_count, cudaStream_t st);
+cudaError_t launch_confusion(const uint8_t *acc, const int32_t *ed,
+                             int64_t n, int E, unsigned long long *counts,
+                             int sm_count, cudaStream_t st);
 
 // Per-translation-unit dispatchers (E ranges).
 cudaError_t launch_rw_uniform_e0(int E, const RwUniformArgs &a, size_t smem,

@@ -7,6 +7,7 @@
 
 #include "ss_cw.cuh"
 #include "ss_rw.cuh"
+#include "ss_verify.cuh"
 
 using namespace ssk;
 
@@ -60,9 +61,25 @@ int cw_one(const uint32_t *q, const uint32_t *r, int m, int E)
     return count;
 }
 
+template <int... Es>
+int ed_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
+                std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    const int w16 = (m + 15) / 16;
+    ((E == Es ? (out = ed_banded<Es>(q, r, m, w16), 0) : 0), ...);
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
+
+// Banded edit distance of the accuracy harness: min(ED, E+1), E <= 31.
+int emu_ed(const uint32_t *q, const uint32_t *r, int m, int E)
+{
+    return ed_dispatch(E, q, r, m, std::make_integer_sequence<int, 32>{});
+}
 
 // Plain-kernel routine with compile-time E (0..31).
 int emu_rw_exact(const uint32_t *q, const uint32_t *r, int m, int E)

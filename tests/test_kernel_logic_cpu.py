@@ -98,3 +98,13 @@ def test_class_table_covers_the_shapes(emu):
     assert emu.emu_class_of(5, -1) == -2
     assert emu.emu_class_of(200000, 500) == -3
     assert emu.emu_class_of(200000, 20) == 4  # small E: any length
+
+
+@pytest.mark.parametrize("m", [1, 5, 16, 17, 40, 100, 150])
+def test_banded_edit_distance_matches_oracle(emu, m):
+    """Accuracy-harness verifier: min(ED, E+1) against the oracle's DP."""
+    for Q, R in pairs(700 + m, 40, m, synth.rate_recipe(0.2)):
+        q, r = packed(Q), packed(R)
+        ed = oracle.edit_distance(Q, R)
+        for E in (0, 1, 2, 5, 10, 20, 31):
+            assert emu.emu_ed(P(q), P(r), m, E) == min(ed, E + 1), (m, E)
