@@ -97,6 +97,7 @@ class Oracle:
         lib.sso_maze.argtypes = [P, P, i64, i64, P]
         lib.sso_filter.argtypes = [P, P, i64, i64, ctypes.c_int, P, P, P]
         lib.sso_min_obstacles.argtypes = [P, P, i64, i64, P]
+        lib.sso_filter_submaze.argtypes = [P, P, i64, i64, i64, i64, P, P]
         lib.sso_edit_distance.argtypes = [P, i64, P, i64]
         lib.sso_edit_distance.restype = i64
         lib.sso_filter_batch.argtypes = [P, P, P, P, P, i64, ctypes.c_int,
@@ -143,6 +144,18 @@ class Oracle:
         if with_stats:
             return res, (st.cells, st.words, st.iterations)
         return res
+
+    def filter_submaze(self, Q, R, E: int, t: int, y: int) -> Result:
+        """Snake-on-Chip decomposition (Section 2.5) into t-column
+        sub-mazes, at most y obstacles each."""
+        q, r = _bytes(Q), _bytes(R)
+        acc = ctypes.c_uint8()
+        obs = ctypes.c_int64()
+        rc = self.lib.sso_filter_submaze(_p(q), _p(r), len(Q), E, t, y,
+                                         ctypes.byref(acc), ctypes.byref(obs))
+        if rc != OK:
+            raise ValueError(f"oracle submaze error {rc}")
+        return Result(bool(acc.value), int(obs.value))
 
     def min_obstacles(self, Q, R, E: int) -> int:
         q, r = _bytes(Q), _bytes(R)
@@ -242,6 +255,10 @@ def maze(Q, R, E):
 
 def filter_pair(Q, R, E, stop_above_E=True, with_stats=False):
     return get().filter_pair(Q, R, E, stop_above_E, with_stats)
+
+
+def filter_submaze(Q, R, E, t, y):
+    return get().filter_submaze(Q, R, E, t, y)
 
 
 def min_obstacles(Q, R, E):

@@ -156,6 +156,47 @@ int sso_filter(const uint8_t *Q, const uint8_t *R, int64_t m, int64_t E,
     return SSO_OK;
 }
 
+int sso_filter_submaze(const uint8_t *Q, const uint8_t *R, int64_t m,
+                       int64_t E, int64_t t, int64_t y, uint8_t *accept,
+                       int64_t *obstacles)
+{
+    if (m < 0 || E < 0 || t < 1 || y < 1)
+        return SSO_ERR_INVALID_ARG;
+    if (!valid_sequence(Q, m) || !valid_sequence(R, m))
+        return SSO_ERR_INVALID_BASE;
+    int64_t count = 0;
+    for (int64_t first = 1; first <= m && count <= E; first += t) {
+        const int64_t last = first + t - 1 < m ? first + t - 1 : m;
+        /* the greedy of Section 2.4 on columns first..last */
+        int64_t checkpoint = first, segments = 0;
+        while (checkpoint <= last && segments < y) {
+            int64_t longest = 0;
+            for (int64_t i = 1; i <= 2 * E + 1; ++i) {
+                int64_t len = 0;
+                for (int64_t j = checkpoint; j <= last; ++j) {
+                    if (sso_cell(Q, R, m, E, i, j) != 0)
+                        break;
+                    ++len;
+                }
+                if (len > longest)
+                    longest = len;
+            }
+            if (checkpoint + longest > last)
+                break; /* reached the sub-maze's last column */
+            segments += 1;
+            checkpoint = checkpoint + longest + 1;
+        }
+        count += segments;
+    }
+    if (count > E + 1)
+        count = E + 1;
+    if (accept)
+        *accept = (uint8_t)(count <= E);
+    if (obstacles)
+        *obstacles = count;
+    return SSO_OK;
+}
+
 int sso_min_obstacles(const uint8_t *Q, const uint8_t *R, int64_t m,
                       int64_t E, int64_t *out)
 {

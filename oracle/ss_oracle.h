@@ -58,6 +58,19 @@ int sso_filter(const uint8_t *Q, const uint8_t *R, int64_t m, int64_t E,
                int stop_above_E, uint8_t *accept, int64_t *obstacles,
                sso_stats *stats);
 
+/* Snake-on-Chip's decomposition (Section 2.5): the maze is cut into
+ * sub-mazes of t consecutive columns (the last may be narrower), each routed
+ * independently by the greedy of Section 2.4 from its first column to its
+ * last (a run reaching the sub-maze's last column ends it without an
+ * obstacle).  Reading of the y "module instances per sub-maze": at most y
+ * escape segments are routed per sub-maze, so a sub-maze contributes at most
+ * y obstacles.  Sub-maze counts are summed, stopping once the sum exceeds
+ * E; accept = (sum <= E), obstacles = min(sum, E+1).  The decomposition can
+ * only underestimate the full greedy count (the paper says so). */
+int sso_filter_submaze(const uint8_t *Q, const uint8_t *R, int64_t m,
+                       int64_t E, int64_t t, int64_t y, uint8_t *accept,
+                       int64_t *obstacles);
+
 /* Minimum number of obstacles over every chain of non-overlapping escape
  * segments that links column 1 to the destination terminal (the optimum
  * Theorem 2 says the greedy reaches), by dynamic programming over

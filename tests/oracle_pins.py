@@ -344,6 +344,42 @@ def pin_batch_matches_single(O):
         assert (bool(acc[p]), int(obs[p])) == r, p
 
 
+# ---- Snake-on-Chip decomposition (Section 2.5) -------------------------------
+
+def pin_submaze_worked_example(O):
+    g = load_golden()
+    Q, R, E = g["Q"], g["R"], int(g["E"])
+    for t, y in ((4, 3), (4, 1), (3, 3), (3, 1)):
+        got = O.filter_submaze(Q, R, E, t, y).obstacles
+        assert got == int(g[f"submaze_t{t}_y{y}"]), (t, y, got)
+
+
+def pin_submaze_reduces_to_full(O):
+    """One sub-maze spanning the whole maze with no segment cap is the
+    greedy of Section 2.4."""
+    for Q, R in random_pairs(23, 150, 120, 12):
+        m = len(Q)
+        for E in (0, 2, 5):
+            assert O.filter_submaze(Q, R, E, m, m + 1) == \
+                O.filter_pair(Q, R, E), (Q, R, E)
+
+
+def pin_submaze_underestimates(O):
+    """Cutting the maze can only lose obstacles (Section 2.5): the count is
+    at most the full greedy's, so no pair the full filter accepts is
+    rejected; a larger segment cap never lowers it."""
+    for Q, R in random_pairs(24, 150, 200, 15):
+        for E in (1, 4, 10):
+            full = O.filter_pair(Q, R, E, stop_above_E=False).obstacles
+            for t in (1, 3, 8, 31):
+                prev = -1
+                for y in (1, 2, 3, 100):
+                    sub = O.filter_submaze(Q, R, E, t, y).obstacles
+                    assert sub <= min(full, E + 1), (Q, R, E, t, y)
+                    assert sub >= prev
+                    prev = sub
+
+
 ALL_PINS = [
     pin_worked_example_maze, pin_worked_example_decision,
     pin_column6_orientation, pin_row_count, pin_identical, pin_E0,
@@ -352,4 +388,6 @@ ALL_PINS = [
     pin_optimality, pin_lower_bound_random, pin_lower_bound_exhaustive,
     pin_edit_distance_textbook, pin_edit_distance_bfs, pin_case_and_invalid,
     pin_pack_reference, pin_batch_matches_single,
+    pin_submaze_worked_example, pin_submaze_reduces_to_full,
+    pin_submaze_underestimates,
 ]

@@ -59,6 +59,13 @@ MUTANTS = {
     "pack_planes_swapped": (
         "(lo << (j % 16)) | (hi << (16 + j % 16))",
         "(hi << (j % 16)) | (lo << (16 + j % 16))"),
+    # sub-maze: one column too wide (sub-mazes overlap)
+    "submaze_off_by_one": (
+        "const int64_t last = first + t - 1 < m ? first + t - 1 : m;",
+        "const int64_t last = first + t < m ? first + t : m;"),
+    # sub-maze: the segment cap ignored
+    "submaze_no_cap": ("while (checkpoint <= last && segments < y) {",
+                       "while (checkpoint <= last) {"),
     # min-obstacle DP: a segment may hold two obstacles
     "dp_two_obstacles": (
         "                if (sso_cell(Q, R, m, E, i, e) != 0)\n"
