@@ -190,6 +190,25 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
                         const int32_t *ed, int64_t n, int32_t e,
                         void *stream, uint64_t *out_counts);
 
+/* ---- downstream pass-through: the accepted pairs (Section 2.4 step 5,
+ * "sequence alignment is needed") for an aligner ------------------------------
+ * ss_compact_accepted: out_index (device int64[n]) receives, in increasing
+ * order, the indices p with accept[p] != 0; *out_count (device int64) their
+ * number.  Uses context workspace (8 bytes per 4096 pairs); asynchronous.
+ * ss_gather_pairs: for fixed-stride SS_FMT_PACKED2 pairs of length m, copies
+ * pair index[i] of reads/refs to slot i of out_reads/out_refs for every
+ * i < min(*count, n) (device count, so it can follow ss_compact_accepted
+ * without a host round trip); reads/refs hold n pairs and out_reads/out_refs
+ * n slots of ceil(m/16) words; indices outside 0..n-1 are skipped.  Both
+ * return SS_OK,
+ * SS_ERR_INVALID_ARG, SS_ERR_OOM or SS_ERR_CUDA. */
+int ss_compact_accepted(ss_ctx *ctx, const uint8_t *accept, int64_t n,
+                        void *stream, int64_t *out_index, int64_t *out_count);
+int ss_gather_pairs(ss_ctx *ctx, const void *reads, const void *refs,
+                    int32_t m, const int64_t *index, const int64_t *count,
+                    int64_t n, void *stream, void *out_reads,
+                    void *out_refs);
+
 /* ---- allocation-free entry point (the paper has no counterpart) -------
  * For callers that cannot allocate device memory: a service that reserves
  * all of a GPU's memory up front through its own allocator (an extra

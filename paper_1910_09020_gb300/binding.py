@@ -38,7 +38,8 @@ EXPORTED = (
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
-    "ss_filter_confusion", "ss_server_create",
+    "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
+    "ss_server_create",
     "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
     "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
 )
@@ -112,6 +113,8 @@ def load(build_if_needed: bool = True):
     lib.ss_edit_distance_banded.argtypes = [P, P, P, ctypes.c_int, I32, I32,
                                             I64, P, P]
     lib.ss_filter_confusion.argtypes = [P, P, P, I64, I32, P, P]
+    lib.ss_compact_accepted.argtypes = [P, P, I64, P, P, P]
+    lib.ss_gather_pairs.argtypes = [P, P, P, I32, P, P, I64, P, P, P]
     lib.ss_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, SZ,
                                      ctypes.c_int]
     lib.ss_server_submit.argtypes = [P, P, P, P, P, I64,
@@ -360,6 +363,35 @@ class Filter:
             m, e, n, _stream_handle(stream) or None, _ptr(out) or None)
         _check(rc, "ss_edit_distance_banded")
         return out
+
+    def compact(self, accept, stream=None):
+        """Indices of accepted pairs, in order: (device int64[n] buffer,
+        device int64 count)."""
+        import torch
+        n = accept.shape[0]
+        idx = torch.empty(max(n, 1), dtype=torch.int64, device=accept.device)
+        cnt = torch.empty(1, dtype=torch.int64, device=accept.device)
+        rc = load().ss_compact_accepted(self.ctx, _ptr(accept) or None, n,
+                                        _stream_handle(stream) or None,
+                                        _ptr(idx), _ptr(cnt))
+        _check(rc, "ss_compact_accepted")
+        return idx, cnt
+
+    def gather(self, reads, refs, index, count, *, m: int, n: int,
+               stream=None):
+        """Dense packed copies of the pairs listed in index[:count] (n slots
+        of ceil(m/16) words each)."""
+        import torch
+        w16 = ss_packed_words(m)
+        out_q = torch.zeros(max(n * w16, 1), dtype=torch.int32,
+                            device=reads.device)
+        out_r = torch.zeros_like(out_q)
+        rc = load().ss_gather_pairs(self.ctx, _ptr(reads), _ptr(refs), m,
+                                    _ptr(index), _ptr(count), n,
+                                    _stream_handle(stream) or None,
+                                    _ptr(out_q), _ptr(out_r))
+        _check(rc, "ss_gather_pairs")
+        return out_q, out_r
 
     def confusion(self, accept, ed, *, e: int, stream=None):
         """(true accepts, false accepts, false rejects, true rejects)."""

@@ -653,6 +653,38 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
     return SS_OK;
 }
 
+int ss_compact_accepted(ss_ctx *ctx, const uint8_t *accept, int64_t n,
+                        void *stream, int64_t *out_index, int64_t *out_count)
+{
+    if (!ctx || n < 0 || !out_count || (n > 0 && (!accept || !out_index)))
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SS_TRY(ensure_workspace(ctx, ssk::compact_ws_bytes(n)));
+    SS_CUDA(ssk::launch_compact(accept, n, (int64_t *)ctx->ws, out_index,
+                                out_count, pick_stream(stream)));
+    ctx->counters.launches += 3;
+    return SS_OK;
+}
+
+int ss_gather_pairs(ss_ctx *ctx, const void *reads, const void *refs,
+                    int32_t m, const int64_t *index, const int64_t *count,
+                    int64_t n, void *stream, void *out_reads,
+                    void *out_refs)
+{
+    if (!ctx || n < 0 || m < 0 || !count)
+        return SS_ERR_INVALID_ARG;
+    if (n > 0 && (!reads || !refs || !index || !out_reads || !out_refs))
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SS_CUDA(ssk::launch_gather_pairs((const uint32_t *)reads,
+                                     (const uint32_t *)refs, m, index, count,
+                                     n, (uint32_t *)out_reads,
+                                     (uint32_t *)out_refs, ctx->sm_count,
+                                     pick_stream(stream)));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
 int ss_set_tuning(ss_ctx *ctx, int rw_max_e, int cw_subgrid)
 {
     if (!ctx || (rw_max_e != 15 && rw_max_e != 31) ||

@@ -1,0 +1,173 @@
+// ss_compact.cu -- downstream pass-through: the pairs the filter accepts
+// ("sequence alignment is needed", Section 2.4 step 5) compacted, in order,
+// into an index list an aligner can consume, and their packed sequences
+// gathered into dense buffers.
+//
+// Three passes, no host synchronisation: per-CTA counts of accepted pairs,
+// an exclusive scan of the CTA counts (one CTA), and a scatter in which each
+// CTA writes its accepted indices at its offset, ranks inside the CTA coming
+// from warp ballots.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ss_device.cuh"
+#include "ss_internal.h"
+
+namespace ssk {
+
+constexpr int kCompactThreads = 256;
+constexpr int kCompactItems = 16;  // pairs per thread
+constexpr int kCompactChunk = kCompactThreads * kCompactItems;
+
+__global__ void __launch_bounds__(kCompactThreads)
+    k_compact_count(const uint8_t *__restrict__ acc, int64_t n,
+                    int64_t *__restrict__ block_counts)
+{
+    __shared__ int warp_sums[kCompactThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kCompactChunk;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < kCompactItems; ++k) {
+        const int64_t p = base + k * kCompactThreads + threadIdx.x;
+        c += (p < n && acc[p]) ? 1 : 0;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0)
+        warp_sums[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w)
+            t += warp_sums[w];
+        block_counts[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of nb CTA counts in place; writes the total to *total.
+__global__ void __launch_bounds__(1024)
+    k_compact_scan(int64_t *__restrict__ block_counts, int64_t nb,
+                   int64_t *__restrict__ total)
+{
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t lo = t * per, hi = lo + per < nb ? lo + per : nb;
+    int64_t s = 0;
+    for (int64_t b = lo; b < hi; ++b)
+        s += block_counts[b];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - s;
+    for (int64_t b = lo; b < hi; ++b) {
+        const int64_t c = block_counts[b];
+        block_counts[b] = run;
+        run += c;
+    }
+    if (t == 1023)
+        *total = part[1023];
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+    k_compact_scatter(const uint8_t *__restrict__ acc, int64_t n,
+                      const int64_t *__restrict__ block_offsets,
+                      int64_t *__restrict__ out_index)
+{
+    __shared__ int warp_base[kCompactThreads / 32];
+    __shared__ int64_t running;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kCompactChunk;
+    if (threadIdx.x == 0)
+        running = block_offsets[blockIdx.x];
+    __syncthreads();
+    for (int k = 0; k < kCompactItems; ++k) {
+        const int64_t p = base + k * kCompactThreads + threadIdx.x;
+        const bool a = p < n && acc[p];
+        const unsigned ballot = __ballot_sync(0xffffffffu, a);
+        if (lane == 0)
+            warp_base[warp] = __popc(ballot);
+        __syncthreads();
+        // prefix over the warps of this round (in index order)
+        int before = 0, round = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) {
+            const int c = warp_base[w];
+            before += w < warp ? c : 0;
+            round += c;
+        }
+        if (a)
+            out_index[running + before +
+                      __popc(ballot & ((1u << lane) - 1u))] = p;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            running += round;
+        __syncthreads();
+    }
+}
+
+// Dense copy of the selected fixed-stride pairs: slot i <- pair index[i],
+// for i < min(*count, n); the outputs hold n slots and the sources n pairs.
+__global__ void k_gather_pairs(const uint32_t *__restrict__ reads,
+                               const uint32_t *__restrict__ refs, int w16,
+                               const int64_t *__restrict__ index,
+                               const int64_t *__restrict__ count,
+                               uint32_t *__restrict__ out_reads,
+                               uint32_t *__restrict__ out_refs, int64_t n)
+{
+    const int64_t c = *count;
+    const int64_t cnt = c < n ? (c > 0 ? c : 0) : n;  // outputs hold n slots
+    const int64_t total = cnt * w16;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+         g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = g / w16;
+        const int w = (int)(g - i * w16);
+        const int64_t src = index[i];
+        if (src < 0 || src >= n)
+            continue;
+        out_reads[g] = reads[src * w16 + w];
+        out_refs[g] = refs[src * w16 + w];
+    }
+}
+
+size_t compact_ws_bytes(int64_t n)
+{
+    return (size_t)((n + kCompactChunk - 1) / kCompactChunk + 1) * 8 + 256;
+}
+
+cudaError_t launch_compact(const uint8_t *acc, int64_t n, int64_t *ws,
+                           int64_t *out_index, int64_t *out_count,
+                           cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaMemsetAsync(out_count, 0, sizeof(int64_t), st);
+    const int64_t nb = (n + kCompactChunk - 1) / kCompactChunk;
+    if (nb > 0x7fffffff)
+        return cudaErrorInvalidValue;
+    k_compact_count<<<(unsigned)nb, kCompactThreads, 0, st>>>(acc, n, ws);
+    k_compact_scan<<<1, 1024, 0, st>>>(ws, nb, out_count);
+    k_compact_scatter<<<(unsigned)nb, kCompactThreads, 0, st>>>(acc, n, ws,
+                                                                out_index);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pairs(const uint32_t *reads, const uint32_t *refs,
+                                int32_t m, const int64_t *index,
+                                const int64_t *count, int64_t n,
+                                uint32_t *out_reads, uint32_t *out_refs,
+                                int sm_count, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int w16 = (m + 15) / 16;
+    k_gather_pairs<<<sm_count * 8, 256, 0, st>>>(reads, refs, w16, index,
+                                                 count, out_reads, out_refs,
+                                                 n);
+    return cudaGetLastError();
+}
+
+}  // namespace ssk

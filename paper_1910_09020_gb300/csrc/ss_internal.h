@@ -53,6 +53,17 @@ cudaError_t launch_confusion(const uint8_t *acc, const int32_t *ed,
                              int64_t n, int E, unsigned long long *counts,
                              int sm_count, cudaStream_t st);
 
+// Compaction of accepted pairs (ss_compact.cu).
+size_t compact_ws_bytes(int64_t n);
+cudaError_t launch_compact(const uint8_t *acc, int64_t n, int64_t *ws,
+                           int64_t *out_index, int64_t *out_count,
+                           cudaStream_t st);
+cudaError_t launch_gather_pairs(const uint32_t *reads, const uint32_t *refs,
+                                int32_t m, const int64_t *index,
+                                const int64_t *count, int64_t n,
+                                uint32_t *out_reads, uint32_t *out_refs,
+                                int sm_count, cudaStream_t st);
+
 // Per-translation-unit dispatchers (E ranges).
 cudaError_t launch_rw_uniform_e0(int E, const RwUniformArgs &a, size_t smem,
                                  unsigned grid, cudaStream_t st);
