@@ -190,6 +190,22 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
                         const int32_t *ed, int64_t n, int32_t e,
                         void *stream, uint64_t *out_counts);
 
+/* ---- sub-maze approximate mode (Section 2.5, Snake-on-Chip) -------------
+ * The maze is cut into sub-mazes of t consecutive columns (the last may be
+ * narrower); each is routed independently by the greedy of Section 2.4 from
+ * its first column to its last, counting at most y escape segments (the
+ * reading taken of the paper's "y module instances per sub-maze"); the
+ * counts are summed and capped at e+1.  accept = (sum <= e).  The paper
+ * notes that this can only underestimate the exact count (more false
+ * accepts, never a false reject); t >= m with y > e gives the exact filter.
+ * Fixed-stride SS_FMT_PACKED2 pairs of length m; min(e, m-1) <= 31 (else
+ * SS_ERR_UNSUPPORTED); t, y >= 1.  Returns SS_OK, SS_ERR_INVALID_ARG,
+ * SS_ERR_UNSUPPORTED or SS_ERR_CUDA. */
+int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
+                      int format, int32_t m, int32_t e, int32_t t, int32_t y,
+                      int64_t n, void *stream, uint8_t *out_accept,
+                      int32_t *out_obstacles);
+
 /* ---- downstream pass-through: the accepted pairs (Section 2.4 step 5,
  * "sequence alignment is needed") for an aligner ------------------------------
  * ss_compact_accepted: out_index (device int64[n]) receives, in increasing

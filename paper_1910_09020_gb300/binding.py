@@ -39,6 +39,7 @@ EXPORTED = (
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
+    "ss_filter_submaze",
     "ss_server_create",
     "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
     "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
@@ -114,6 +115,8 @@ def load(build_if_needed: bool = True):
                                             I64, P, P]
     lib.ss_filter_confusion.argtypes = [P, P, P, I64, I32, P, P]
     lib.ss_compact_accepted.argtypes = [P, P, I64, P, P, P]
+    lib.ss_filter_submaze.argtypes = [P, P, P, ctypes.c_int, I32, I32, I32,
+                                      I32, I64, P, P, P]
     lib.ss_gather_pairs.argtypes = [P, P, P, I32, P, P, I64, P, P, P]
     lib.ss_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, SZ,
                                      ctypes.c_int]
@@ -363,6 +366,21 @@ class Filter:
             m, e, n, _stream_handle(stream) or None, _ptr(out) or None)
         _check(rc, "ss_edit_distance_banded")
         return out
+
+    def filter_submaze(self, reads, refs, *, m: int, e: int, t: int, y: int,
+                       n=None, stream=None):
+        """Sub-maze approximate mode (Section 2.5) on fixed-stride packed
+        pairs; returns (accept, obstacles)."""
+        import torch
+        n = reads.shape[0] if n is None else n
+        acc = torch.empty(max(n, 1), dtype=torch.uint8, device=reads.device)
+        obs = torch.empty(max(n, 1), dtype=torch.int32, device=reads.device)
+        rc = load().ss_filter_submaze(self.ctx, _ptr(reads), _ptr(refs),
+                                      SS_FMT_PACKED2, m, e, t, y, n,
+                                      _stream_handle(stream) or None,
+                                      _ptr(acc), _ptr(obs))
+        _check(rc, "ss_filter_submaze")
+        return acc[:n], obs[:n]
 
     def compact(self, accept, stream=None):
         """Indices of accepted pairs, in order: (device int64[n] buffer,

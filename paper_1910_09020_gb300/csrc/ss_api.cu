@@ -653,6 +653,36 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
     return SS_OK;
 }
 
+int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
+                      int format, int32_t m, int32_t e, int32_t t, int32_t y,
+                      int64_t n, void *stream, uint8_t *out_accept,
+                      int32_t *out_obstacles)
+{
+    if (!ctx || n < 0 || m < 0 || e < 0 || t < 1 || y < 1)
+        return SS_ERR_INVALID_ARG;
+    if (format != SS_FMT_PACKED2)
+        return SS_ERR_INVALID_ARG;
+    if (ssk::eff_threshold(m, e) > 31)
+        return SS_ERR_UNSUPPORTED;
+    if (n == 0)
+        return SS_OK;
+    if (!reads || !refs || !out_accept || !out_obstacles)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick_stream(stream);
+    if (m == 0) {
+        SS_CUDA(cudaMemsetAsync(out_accept, 1, (size_t)n, st));
+        SS_CUDA(cudaMemsetAsync(out_obstacles, 0, (size_t)n * 4, st));
+        return SS_OK;
+    }
+    SS_CUDA(ssk::launch_submaze((const uint32_t *)reads,
+                                (const uint32_t *)refs, n, m, e, t, y,
+                                out_accept, out_obstacles, ctx->sm_count,
+                                st));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
 int ss_compact_accepted(ss_ctx *ctx, const uint8_t *accept, int64_t n,
                         void *stream, int64_t *out_index, int64_t *out_count)
 {

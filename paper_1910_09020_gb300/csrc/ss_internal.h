@@ -53,6 +53,12 @@ cudaError_t launch_confusion(const uint8_t *acc, const int32_t *ed,
                              int64_t n, int E, unsigned long long *counts,
                              int sm_count, cudaStream_t st);
 
+// Sub-maze approximate mode (ss_submaze.cu), E' <= 31.
+cudaError_t launch_submaze(const uint32_t *reads, const uint32_t *refs,
+                           int64_t n, int32_t m, int32_t E, int32_t t,
+                           int32_t y, uint8_t *acc, int32_t *obs,
+                           int sm_count, cudaStream_t st);
+
 // Compaction of accepted pairs (ss_compact.cu).
 size_t compact_ws_bytes(int64_t n);
 cudaError_t launch_compact(const uint8_t *acc, int64_t n, int64_t *ws,

@@ -41,5 +41,7 @@ def load():
     lib.emu_cw.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_class_of.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.emu_ed.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
+    lib.emu_submaze.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int]
     _lib = lib
     return lib

@@ -7,6 +7,7 @@
 
 #include "ss_cw.cuh"
 #include "ss_rw.cuh"
+#include "ss_submaze.cuh"
 #include "ss_verify.cuh"
 
 using namespace ssk;
@@ -74,6 +75,22 @@ int ed_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
 }  // namespace
 
 extern "C" {
+
+// Sub-maze approximate mode: t-column sub-mazes, at most y obstacles each.
+int emu_submaze(const uint32_t *q, const uint32_t *r, int m, int E, int t,
+                int y)
+{
+    const int w16 = (m + 15) / 16;
+    const GlobalSeq Q{q, w16}, R{r, w16};
+    const int Ee = eff_threshold(m, E);
+    if (Ee <= 3)
+        return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
+    if (Ee <= 7)
+        return submaze_route<7>(Q, R, m, E, t, y, 0xffffffffu);
+    if (Ee <= 15)
+        return submaze_route<15>(Q, R, m, E, t, y, 0xffffffffu);
+    return submaze_route<31>(Q, R, m, E, t, y, 0xffffffffu);
+}
 
 // Banded edit distance of the accuracy harness: min(ED, E+1), E <= 31.
 int emu_ed(const uint32_t *q, const uint32_t *r, int m, int E)

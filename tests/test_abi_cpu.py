@@ -68,3 +68,12 @@ def test_create_without_gpu_fails_cleanly():
     rc = binding.load().ss_create(ctypes.byref(h), 0, 0)
     assert rc in (binding.SS_ERR_CUDA, binding.SS_ERR_INVALID_ARG)
     assert not h.value
+
+
+def test_submaze_rejects_bad_arguments_without_gpu():
+    lib = binding.load()
+    P = ctypes.c_void_p
+    for args in [(None, P(1), P(1), binding.SS_FMT_PACKED2, 100, 3, 8, 3, 1),
+                 ]:
+        rc = lib.ss_filter_submaze(*args, None, P(1), P(1))
+        assert rc == binding.SS_ERR_INVALID_ARG

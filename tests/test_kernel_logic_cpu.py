@@ -108,3 +108,17 @@ def test_banded_edit_distance_matches_oracle(emu, m):
         ed = oracle.edit_distance(Q, R)
         for E in (0, 1, 2, 5, 10, 20, 31):
             assert emu.emu_ed(P(q), P(r), m, E) == min(ed, E + 1), (m, E)
+
+
+@pytest.mark.parametrize("t", [1, 3, 8, 31, 32, 33, 77, 1000])
+def test_submaze_matches_oracle(emu, t):
+    rng = np.random.default_rng(t)
+    for i in range(40):
+        m = int(rng.integers(1, 180))
+        Q, R = pairs(800 + i, 1, m, synth.rate_recipe(0.12))[0]
+        q, r = packed(Q), packed(R)
+        for E in (0, 2, 5, 15, 31):
+            for y in (1, 3, 1000):
+                got = emu.emu_submaze(P(q), P(r), m, E, t, y)
+                want = oracle.filter_submaze(Q, R, E, t, y).obstacles
+                assert got == want, (m, E, t, y)
