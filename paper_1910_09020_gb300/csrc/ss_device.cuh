@@ -73,6 +73,21 @@ SS_HD void planes_of(uint32_t p0, uint32_t p1, uint32_t &lo, uint32_t &hi)
 #endif
 }
 
+// Byte permute: byte i of the result is byte (s >> 4i) & 7 of the 8-byte
+// value b:a (selector nibbles 0..7 only).
+SS_HD uint32_t prmt(uint32_t a, uint32_t b, uint32_t s)
+{
+#ifdef __CUDA_ARCH__
+    return __byte_perm(a, b, s);
+#else
+    const uint64_t v = ((uint64_t)b << 32) | a;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; ++i)
+        r |= (uint32_t)((v >> (8 * ((s >> (4 * i)) & 7u))) & 0xffu) << (8 * i);
+    return r;
+#endif
+}
+
 // Bits t >= lim of a 32-column word set (lim <= 0: all, lim >= 32: none).
 SS_HD uint32_t mask_from(int lim)
 {

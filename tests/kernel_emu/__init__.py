@@ -41,6 +41,10 @@ def load():
     lib.emu_cw.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.emu_class_of.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.emu_ed.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
+    lib.emu_pack_chunk.argtypes = [P, P]
+    lib.emu_pack_chunk.restype = ctypes.c_uint32
+    lib.emu_pack_window.argtypes = [ctypes.c_uint32] * 3
+    lib.emu_pack_window.restype = ctypes.c_uint32
     lib.emu_submaze.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int]
     _lib = lib

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "ss_cw.cuh"
+#include "ss_pack.cuh"
 #include "ss_rw.cuh"
 #include "ss_submaze.cuh"
 #include "ss_verify.cuh"
@@ -75,6 +76,25 @@ int ed_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
 }  // namespace
 
 extern "C" {
+
+// Pack arithmetic: 16 ASCII bytes -> packed word, error bits.
+uint32_t emu_pack_chunk(const uint8_t *b16, uint32_t *err)
+{
+    uint32_t x[4];
+    for (int q = 0; q < 4; ++q)
+        x[q] = (uint32_t)b16[4 * q] | ((uint32_t)b16[4 * q + 1] << 8) |
+               ((uint32_t)b16[4 * q + 2] << 16) |
+               ((uint32_t)b16[4 * q + 3] << 24);
+    uint32_t e = 0;
+    const uint32_t r = pack_chunk(x, e);
+    *err = e;
+    return r;
+}
+
+uint32_t emu_pack_window(uint32_t c0, uint32_t c1, uint32_t r)
+{
+    return pack_window(c0, c1, r);
+}
 
 // Sub-maze approximate mode: t-column sub-mazes, at most y obstacles each.
 int emu_submaze(const uint32_t *q, const uint32_t *r, int m, int E, int t,

@@ -53,6 +53,41 @@ def test_pack_varlen_matches_reference_packer(F):
         assert (got[poff[p]:poff[p + 1]] == want).all(), p
 
 
+@pytest.mark.parametrize("m,shift", [(37, 0), (100, 0), (128, 0),
+                                     (100, 1), (100, 4), (23, 3)])
+def test_pack_many_ctas_and_unaligned_input(F, m, shift):
+    """Enough pairs for hundreds of CTAs (each staging its own span of the
+    byte stream), with the input both 16-byte aligned and not."""
+    torch = torch_cuda()
+    n = 40000
+    reads, _ = synth.pairs_fixed(202 + m, 0, n, m, synth.SHORT_POISSON)
+    rng = np.random.default_rng(m + shift)
+    lower = rng.random(reads.shape) < 0.5
+    reads = np.where(lower, reads | 0x20, reads).astype(np.uint8)
+    buf = torch.zeros(n * m + 64, dtype=torch.uint8, device="cuda")
+    buf[shift:shift + n * m] = to_dev(reads.reshape(-1))
+    packed = F.pack(buf[shift:shift + n * m], m=m, n=n)
+    F.sync()
+    got = packed.cpu().numpy().view(np.uint32).reshape(n, -1)
+    for p in range(n):
+        want = oracle.pack_reference(reads[p].tobytes())
+        assert (got[p] == want).all(), p
+
+
+@pytest.mark.parametrize("where", ["first", "cta_edge", "last"])
+def test_pack_invalid_base_anywhere_latches(F, where):
+    n, m = 40000, 100
+    reads, _ = synth.pairs_fixed(9, 0, n, m, synth.SHORT_UNIFORM_K)
+    flat = reads.reshape(-1).copy()
+    pos = {"first": 0, "cta_edge": 1024 * 16 - 1, "last": n * m - 1}[where]
+    flat[pos] = ord("u")
+    F.pack(to_dev(flat), m=m, n=n)
+    with pytest.raises(binding.SSError) as ei:
+        F.sync()
+    assert ei.value.code == binding.SS_ERR_INVALID_BASE
+    F.sync()
+
+
 def test_pack_invalid_base_latches(F):
     reads, _ = synth.pairs_fixed(3, 0, 64, 100, synth.SHORT_UNIFORM_K)
     reads[17, 55] = ord("N")

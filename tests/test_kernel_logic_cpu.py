@@ -122,3 +122,42 @@ def test_submaze_matches_oracle(emu, t):
                 got = emu.emu_submaze(P(q), P(r), m, E, t, y)
                 want = oracle.filter_submaze(Q, R, E, t, y).obstacles
                 assert got == want, (m, E, t, y)
+
+
+CODE = {c: i for i, c in enumerate(b"ACGT")}
+CODE.update({c: i for i, c in enumerate(b"acgt")})
+
+
+def test_pack_chunk_every_byte_value_every_position(emu):
+    """Validity rule and code gather of the pack kernels on all 256 byte
+    values at each of the 16 positions, against the oracle's packer."""
+    err = ctypes.c_uint32()
+    for pos in range(16):
+        for b in range(256):
+            buf = bytearray(b"A" * 16)
+            buf[pos] = b
+            arr = np.frombuffer(bytes(buf), np.uint8).copy()
+            got = emu.emu_pack_chunk(P(arr), ctypes.byref(err))
+            assert (err.value == 0) == (b in CODE), (pos, b)
+            if b in CODE:
+                assert got == int(oracle.pack_reference(bytes(buf))[0]), (pos, b)
+
+
+def test_pack_chunk_and_window_random_streams(emu):
+    rng = np.random.default_rng(3)
+    err = ctypes.c_uint32()
+    for _ in range(200):
+        s = rng.choice(list(b"ACGTacgt"), 64).astype(np.uint8).tobytes()
+        arr = np.frombuffer(s, np.uint8).copy()
+        chunks = []
+        for k in range(4):
+            sub = arr[16 * k:16 * k + 16].copy()
+            w = emu.emu_pack_chunk(P(sub), ctypes.byref(err))
+            assert err.value == 0
+            assert w == int(oracle.pack_reference(s[16 * k:16 * k + 16])[0])
+            chunks.append(w)
+        for k in range(3):
+            for r in range(16):
+                got = emu.emu_pack_window(chunks[k], chunks[k + 1], r)
+                start = 16 * k + r
+                assert got == int(oracle.pack_reference(s[start:start + 16])[0])
