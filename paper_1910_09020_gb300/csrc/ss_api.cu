@@ -14,7 +14,7 @@
 #include "ss_bucket.cuh"
 #include "ss_device.cuh"
 #include "ss_internal.h"
-#include "ss_rw.cuh"
+#include "ss_rw_launch.cuh"
 
 namespace {
 
@@ -218,7 +218,7 @@ int filter_packed(ss_ctx *ctx, const ssk::PairSet &ps, int flags,
     const bool uniform = !ps.offsets && !ps.lengths && !ps.Es;
     if (uniform && mode != SS_MODE_BUCKETED && plain_ok(ps.m, ps.e)) {
         SS_CUDA(ssk::launch_rw_uniform(ps.e, ps.reads, ps.refs, ps.n, ps.m,
-                                       ps.acc, ps.obs, st));
+                                       ps.acc, ps.obs, ctx->d_status, st));
         ctx->counters.launches += 1;
         return SS_OK;
     }
@@ -253,32 +253,80 @@ ssk::PairSet make_pairs(const void *reads, const void *refs,
 
 namespace ssk {
 
+namespace {
+bool g_rw_ready = false;
+}  // namespace
+
+cudaError_t rw_init()
+{
+    if (g_rw_ready)
+        return cudaSuccess;
+    cudaError_t e;
+    if ((e = rw_init_e0()) != cudaSuccess ||
+        (e = rw_init_e1()) != cudaSuccess ||
+        (e = rw_init_e2()) != cudaSuccess ||
+        (e = rw_init_e3()) != cudaSuccess)
+        return e;
+    g_rw_ready = true;
+    return cudaSuccess;
+}
+
 cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
                               const uint32_t *refs, int64_t n, int32_t m,
-                              uint8_t *acc, int32_t *obs, cudaStream_t st)
+                              uint8_t *acc, int32_t *obs, int *status,
+                              cudaStream_t st)
 {
-    RwUniformArgs a;
-    a.reads = reads;
-    a.refs = refs;
-    a.n = n;
-    a.m = m;
-    a.w16 = (m + 15) / 16;
-    a.w16_magic = div_magic((uint32_t)std::max(a.w16, 1));
-    a.neg1 = 0xffffffffu;
-    a.acc = acc;
-    a.obs = obs;
-    const size_t smem =
-        (size_t)2 * (size_t)std::max(a.w16, 1) * (kRwThreads + 1) * 4;
-    const int64_t grid = (n + kRwThreads - 1) / kRwThreads;
-    if (grid > 0x7fffffff)
+    if (!g_rw_ready || E < 0 || E > kRwMaxE)
         return cudaErrorInvalidValue;
+    RwLaunch L{};
+    const int w16 = std::max((m + 15) / 16, 1);
+    const int64_t ntiles = (n + kRwThreads - 1) / kRwThreads;
+    if (w16 <= kRwPipeMaxW16) {
+        L.pipe = true;
+        RwPipeArgs &a = L.pa;
+        a.reads = reads;
+        a.refs = refs;
+        a.n = n;
+        a.ntiles = ntiles;
+        a.m = m;
+        a.w16 = w16;
+        a.stages = rw_pipe_stages(w16);
+        a.bulk = ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15) == 0;
+        a.neg1 = 0xffffffffu;
+        a.acc = acc;
+        a.obs = obs;
+        a.status = status;
+        L.smem = rw_pipe_smem(w16);
+        const int64_t groups = (ntiles + kRwGroup - 1) / kRwGroup;
+        if (groups > 0x7fffffff)
+            return cudaErrorInvalidValue;
+        L.grid = (unsigned)groups;
+    } else {
+        L.pipe = false;
+        RwUniformArgs &a = L.sa;
+        a.reads = reads;
+        a.refs = refs;
+        a.n = n;
+        a.m = m;
+        a.w16 = w16;
+        a.w16_magic = div_magic((uint32_t)w16);
+        a.neg1 = 0xffffffffu;
+        a.acc = acc;
+        a.obs = obs;
+        L.smem = (size_t)2 * (size_t)w16 * (kRwThreads + 1) * 4;
+        if (ntiles > 0x7fffffff)
+            return cudaErrorInvalidValue;
+        L.grid = (unsigned)ntiles;
+    }
+    if (L.grid == 0)
+        return cudaSuccess;
     if (E <= 9)
-        return launch_rw_uniform_e0(E, a, smem, (unsigned)grid, st);
+        return launch_rw_uniform_e0(E, L, st);
     if (E <= 17)
-        return launch_rw_uniform_e1(E, a, smem, (unsigned)grid, st);
+        return launch_rw_uniform_e1(E, L, st);
     if (E <= 24)
-        return launch_rw_uniform_e2(E, a, smem, (unsigned)grid, st);
-    return launch_rw_uniform_e3(E, a, smem, (unsigned)grid, st);
+        return launch_rw_uniform_e2(E, L, st);
+    return launch_rw_uniform_e3(E, L, st);
 }
 
 }  // namespace ssk

@@ -280,7 +280,9 @@ cudaError_t bucket_init(int sm_count)
 {
     if (g_cfg.ready)
         return cudaSuccess;
-    cudaError_t e;
+    cudaError_t e = rw_init();
+    if (e != cudaSuccess)
+        return e;
     g_cfg.rw[0] = occupancy_per_sm(k_rw_bucket<1>, 128, 0);
     g_cfg.rw[1] = occupancy_per_sm(k_rw_bucket<3>, 128, 0);
     g_cfg.rw[2] = occupancy_per_sm(k_rw_bucket<7>, 128, 0);

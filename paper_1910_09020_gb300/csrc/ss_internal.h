@@ -7,6 +7,7 @@
 namespace ssk {
 
 struct RwUniformArgs;
+struct RwLaunch;
 struct PairSet;
 struct BucketWs;
 struct TuneParams;
@@ -24,10 +25,15 @@ cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
                                int *status, int sm_count, cudaStream_t st,
                                uint8_t *bad_flags = nullptr);
 
-// K3a plain launch for 0 <= E <= kRwMaxE, m <= kRwMaxM.
+// K3a plain launch for 0 <= E <= kRwMaxE, m <= kRwMaxM.  status: device
+// word for latched errors.
 cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
                               const uint32_t *refs, int64_t n, int32_t m,
-                              uint8_t *acc, int32_t *obs, cudaStream_t st);
+                              uint8_t *acc, int32_t *obs, int *status,
+                              cudaStream_t st);
+// Kernel attributes of the plain launches (once per process,
+// before any capture; called by bucket_init).
+cudaError_t rw_init();
 
 // K2 + K4: bucketed persistent form of a mixed batch.
 size_t bucket_ws_bytes(int64_t n);
@@ -70,14 +76,14 @@ cudaError_t launch_gather_pairs(const uint32_t *reads, const uint32_t *refs,
                                 uint32_t *out_reads, uint32_t *out_refs,
                                 int sm_count, cudaStream_t st);
 
-// Per-translation-unit dispatchers (E ranges).
-cudaError_t launch_rw_uniform_e0(int E, const RwUniformArgs &a, size_t smem,
-                                 unsigned grid, cudaStream_t st);
-cudaError_t launch_rw_uniform_e1(int E, const RwUniformArgs &a, size_t smem,
-                                 unsigned grid, cudaStream_t st);
-cudaError_t launch_rw_uniform_e2(int E, const RwUniformArgs &a, size_t smem,
-                                 unsigned grid, cudaStream_t st);
-cudaError_t launch_rw_uniform_e3(int E, const RwUniformArgs &a, size_t smem,
-                                 unsigned grid, cudaStream_t st);
+// Per-translation-unit dispatchers (E ranges 0-9, 10-17, 18-24, 25-31).
+cudaError_t launch_rw_uniform_e0(int E, const RwLaunch &L, cudaStream_t st);
+cudaError_t launch_rw_uniform_e1(int E, const RwLaunch &L, cudaStream_t st);
+cudaError_t launch_rw_uniform_e2(int E, const RwLaunch &L, cudaStream_t st);
+cudaError_t launch_rw_uniform_e3(int E, const RwLaunch &L, cudaStream_t st);
+cudaError_t rw_init_e0();
+cudaError_t rw_init_e1();
+cudaError_t rw_init_e2();
+cudaError_t rw_init_e3();
 
 }  // namespace ssk

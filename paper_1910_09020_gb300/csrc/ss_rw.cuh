@@ -20,11 +20,19 @@
 // obstacle since c are kept in a bitmask and count as all-obstacle rows
 // until the next obstacle is found, so runs spanning words are exact.
 //
-// Two launch forms share rw_route():
-//  * k_rw_uniform<E>: the plain launch (uniform m and E).  A CTA stages its
+// Three launch forms share rw_route():
+//  * k_rw_uniform<E>: the plain launch (uniform m and E, m <= 256).  Each
+//    CTA routes a group of kRwGroup consecutive tiles of 128 pairs; a ring
+//    of 2-3 shared-memory stages is filled by bulk asynchronous copies (one
+//    per sequence per tile, completing on an mbarrier), so the next tiles'
+//    HBM reads are in flight while the current tile is routed.  Groups, not
+//    a persistent grid: the block scheduler hands out groups as SMs free
+//    up, which balances the uneven routing cost of the groups.  Waits are
+//    bounded: on timeout the CTA latches kStatusTimeout, drains its copies
+//    in flight and returns.
+//  * k_rw_staged<E>: the plain launch for longer reads; a CTA stages its
 //    pairs' packed words in shared memory, transposed (word i of the CTA's
-//    pair t at [i * ld + t], ld = T + 1) so per-thread reads are
-//    conflict-free; results are written coalesced.
+//    pair t at [i * ld + t], ld = T + 1), with no pipelining.
 //  * k_rw_bucket<EMAX>: persistent launch over one bucket of a mixed batch
 //    (runtime E <= EMAX, any m); each thread reads its pair straight from
 //    global memory (contiguous words, L1-cached).  Rows with |s| > E are
@@ -34,6 +42,7 @@
 #include <type_traits>
 
 #include "ss_device.cuh"
+#include "ss_internal.h"
 
 namespace ssk {
 
@@ -48,6 +57,19 @@ struct SmemSeq {
         const int i = 2 * k;
         const uint32_t p0 = i < w16 ? s[i * ld] : 0u;
         const uint32_t p1 = i + 1 < w16 ? s[(i + 1) * ld] : 0u;
+        planes_of(p0, p1, lo, hi);
+    }
+};
+
+// Packed words of one sequence, contiguous in shared memory.
+struct SmemSeqC {
+    const uint32_t *s;
+    int w16;
+    SS_HD void planes(int k, uint32_t &lo, uint32_t &hi) const
+    {
+        const int i = 2 * k;
+        const uint32_t p0 = i < w16 ? s[i] : 0u;
+        const uint32_t p1 = i + 1 < w16 ? s[i + 1] : 0u;
         planes_of(p0, p1, lo, hi);
     }
 };
@@ -207,14 +229,14 @@ __device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
     return mism < 31 ? mism : 31;
 }
 
-// Plain launch: uniform m and E, one thread per pair, one CTA per T pairs.
-// The CTA stages its pairs (128-bit loads when aligned), orders them by a
-// predicted routing cost so that each warp holds pairs of similar cost (the
-// warp then diverges less), routes them, and writes each result at the
-// pair's own index.
+// Plain launch for long reads: uniform m and E, one thread per pair, one CTA
+// per T pairs.  The CTA stages its pairs (128-bit loads when aligned), orders
+// them by a predicted routing cost so that each warp holds pairs of similar
+// cost (the warp then diverges less), routes them, and writes each result at
+// the pair's own index.
 template <int E>
 __global__ void __launch_bounds__(128)
-    k_rw_uniform(const RwUniformArgs a)
+    k_rw_staged(const RwUniformArgs a)
 {
     extern __shared__ uint32_t smem[];
     __shared__ int s_cnt[32];
@@ -295,6 +317,159 @@ __global__ void __launch_bounds__(128)
         const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
         a.acc[p0 + u] = (uint8_t)(cnt <= E);
         a.obs[p0 + u] = cnt;
+    }
+}
+
+constexpr int kRwMaxStages = 3;
+constexpr int kRwGroup = 8;                  // tiles per CTA
+constexpr int kRwPipeMaxW16 = 16;            // m <= 256
+constexpr uint64_t kRwWaitNs = 2000000000ull;  // 2 s per stage wait
+
+// Stages and dynamic shared memory of the pipelined kernel for w16 words.
+SS_HD int rw_pipe_stages(int w16) { return w16 <= 8 ? 3 : 2; }
+SS_HD size_t rw_pipe_smem(int w16)
+{
+    return (size_t)rw_pipe_stages(w16) * 2u * kRwThreads * (size_t)w16 * 4u;
+}
+
+struct RwPipeArgs {
+    const uint32_t *reads;  // packed, pair p at word p * w16
+    const uint32_t *refs;
+    int64_t n;
+    int64_t ntiles;         // ceil(n / kRwThreads)
+    int32_t m;
+    int32_t w16;
+    int32_t stages;         // 1..kRwMaxStages
+    int32_t bulk;           // inputs 16-byte aligned: full tiles bulk-copied
+    uint32_t neg1;          // 0xffffffff (see rw_route)
+    uint8_t *acc;
+    int32_t *obs;
+    int *status;
+};
+
+// Order the tile's pairs by predicted cost (counting sort on the CTA):
+// returns the pair this thread routes.  s_cnt must be zero on entry.
+__device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
+                                            const uint32_t *sR, int w16,
+                                            int np, int *s_cnt,
+                                            uint8_t *s_perm)
+{
+    const int t = threadIdx.x;
+    int key = 0, rank = 0;
+    if (t < np) {
+        key = rw_cost_key(sQ + t * w16, sR + t * w16, 1, w16);
+        rank = atomicAdd(&s_cnt[key], 1);
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int c = s_cnt[t];
+        int x = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (t >= off)
+                x += y;
+        }
+        s_cnt[t] = x - c;  // exclusive start of bucket t
+    }
+    __syncthreads();
+    if (t < np)
+        s_perm[s_cnt[key] + rank] = (uint8_t)t;
+    __syncthreads();
+    return s_perm[t];
+}
+
+// Plain launch: uniform m <= 256 and E; CTA b routes tiles kRwGroup * b ..
+// kRwGroup * b + kRwGroup - 1 of kRwThreads pairs each, from pair-major
+// shared-memory stages filled by bulk copies.
+template <int E>
+__global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ __align__(8) uint64_t full[kRwMaxStages];
+    __shared__ int s_cnt[32];
+    __shared__ uint8_t s_perm[kRwThreads];
+    const int t = threadIdx.x;
+    const int w16 = a.w16;
+    const int S = a.stages;
+    const uint32_t tile_words = (uint32_t)kRwThreads * (uint32_t)w16;
+    const uint32_t tile_bytes = tile_words * 4u;
+    // tile j < kRwGroup of this CTA is global tile kRwGroup * blockIdx.x + j;
+    // it is bulk-copied iff the inputs are aligned and the tile is full
+    auto tile_of = [&](int64_t j) {
+        return j < kRwGroup ? (int64_t)blockIdx.x * kRwGroup + j : a.ntiles;
+    };
+    auto by_copy = [&](int64_t tile) {
+        return a.bulk && tile < a.ntiles &&
+               (tile + 1) * (int64_t)kRwThreads <= a.n;
+    };
+    auto issue = [&](int s, int64_t tile) {
+        uint32_t *dq = smem + (size_t)s * 2u * tile_words;
+        mbar_arrive_expect_tx(&full[s], 2u * tile_bytes);
+        bulk_load(dq, a.reads + tile * tile_words, tile_bytes, &full[s]);
+        bulk_load(dq + tile_words, a.refs + tile * tile_words, tile_bytes,
+                  &full[s]);
+    };
+    if (t == 0) {
+        for (int s = 0; s < S; ++s)
+            mbar_init(&full[s], 1);
+        mbar_init_fence();
+    }
+    if (t < 32)
+        s_cnt[t] = 0;
+    __syncthreads();
+    if (t == 0)
+        for (int j = 0; j < S; ++j)
+            if (by_copy(tile_of(j)))
+                issue(j, tile_of(j));
+    for (int64_t j = 0;; ++j) {
+        const int64_t tile = tile_of(j);
+        if (tile >= a.ntiles)
+            break;
+        const int s = (int)(j % S);
+        uint32_t *sQ = smem + (size_t)s * 2u * tile_words;
+        uint32_t *sR = sQ + tile_words;
+        const int64_t p0 = tile * kRwThreads;
+        const int np = (int)min((int64_t)kRwThreads, a.n - p0);
+        if (by_copy(tile)) {
+            const bool ok = mbar_wait_bounded(
+                &full[s], (uint32_t)((j / S) & 1), kRwWaitNs);
+            if (__syncthreads_or(!ok)) {
+                if (t == 0) {
+                    atomicOr(a.status, kStatusTimeout);
+                    // drain the copies still in flight into this CTA
+                    for (int64_t k = j; k < j + S; ++k)
+                        if (by_copy(tile_of(k)))
+                            mbar_wait_bounded(&full[k % S],
+                                              (uint32_t)((k / S) & 1),
+                                              kRwWaitNs);
+                }
+                return;
+            }
+        } else {
+            const uint32_t *gq = a.reads + p0 * w16;
+            const uint32_t *gr = a.refs + p0 * w16;
+            for (int idx = t; idx < np * w16; idx += kRwThreads) {
+                sQ[idx] = __ldg(gq + idx);
+                sR[idx] = __ldg(gr + idx);
+            }
+            __syncthreads();
+        }
+        int u = t;
+        if (E >= 2)
+            u = rw_sort_tile(sQ, sR, w16, np, s_cnt, s_perm);
+        if (t < np) {
+            const SmemSeqC q{sQ + u * w16, w16};
+            const SmemSeqC r{sR + u * w16, w16};
+            const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
+            a.acc[p0 + u] = (uint8_t)(cnt <= E);
+            a.obs[p0 + u] = cnt;
+        }
+        if (E >= 2 && t < 32)
+            s_cnt[t] = 0;
+        __syncthreads();  // stage s and the sort buffers are free again
+        if (t == 0 && by_copy(tile_of(j + S)))
+            issue(s, tile_of(j + S));
     }
 }
 

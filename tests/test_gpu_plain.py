@@ -136,6 +136,42 @@ def test_uniform_parity_all_E(F, m):
             assert_same(acc, obs, oacc, oobs, f"m={m} E={E} {name}")
 
 
+@pytest.mark.parametrize("m", [64, 100, 200])
+def test_many_tiles_per_cta_every_pair(F, m):
+    """Enough pairs for every persistent CTA to cycle its shared-memory ring
+    many times (with a partial last tile), every pair compared."""
+    n = 1_500_001
+    reads, refs = synth.pairs_fixed(55 + m, 0, n, m, synth.SHORT_POISSON)
+    q = F.pack(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack(to_dev(refs.reshape(-1)), m=m, n=n)
+    for E in (0, 3, 10):
+        acc, obs = F.filter(q, r, m=m, e=E, n=n, sync=True)
+        oacc, oobs = oracle_fixed(reads, refs, E)
+        assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                    f"m={m} E={E}")
+
+
+def test_unaligned_packed_input(F):
+    """Packed input not 16-byte aligned: tiles are loaded without bulk
+    copies."""
+    torch = torch_cuda()
+    n, m = 300_000, 100
+    reads, refs = synth.pairs_fixed(66, 0, n, m, synth.SHORT_POISSON)
+    w16 = binding.ss_packed_words(m)
+    q = F.pack(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack(to_dev(refs.reshape(-1)), m=m, n=n)
+    qb = torch.zeros(n * w16 + 4, dtype=torch.int32, device="cuda")
+    rb = torch.zeros(n * w16 + 4, dtype=torch.int32, device="cuda")
+    qb[1:1 + n * w16] = q
+    rb[3:3 + n * w16] = r
+    for E in (0, 2, 7):
+        acc, obs = F.filter(qb[1:1 + n * w16], rb[3:3 + n * w16], m=m, e=E,
+                            n=n, sync=True)
+        oacc, oobs = oracle_fixed(reads, refs, E)
+        assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                    f"unaligned E={E}")
+
+
 def test_edge_cases(F):
     rng = np.random.default_rng(0)
     m = 100
