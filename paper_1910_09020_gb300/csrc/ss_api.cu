@@ -291,13 +291,14 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
         a.m = m;
         a.w16 = w16;
         a.stages = rw_pipe_stages(w16);
+        a.group = kRwGroup;
         a.bulk = ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15) == 0;
         a.neg1 = 0xffffffffu;
         a.acc = acc;
         a.obs = obs;
         a.status = status;
         L.smem = rw_pipe_smem(w16);
-        const int64_t groups = (ntiles + kRwGroup - 1) / kRwGroup;
+        const int64_t groups = (ntiles + a.group - 1) / a.group;
         if (groups > 0x7fffffff)
             return cudaErrorInvalidValue;
         L.grid = (unsigned)groups;

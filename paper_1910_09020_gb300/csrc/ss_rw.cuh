@@ -326,7 +326,9 @@ constexpr int kRwPipeMaxW16 = 16;            // m <= 256
 constexpr uint64_t kRwWaitNs = 2000000000ull;  // 2 s per stage wait
 
 // Stages and dynamic shared memory of the pipelined kernel for w16 words.
-SS_HD int rw_pipe_stages(int w16) { return w16 <= 8 ? 3 : 2; }
+// Two stages: a third adds shared memory (fewer resident CTAs) and measured
+// no faster; more tiles per CTA than 8 unbalance the CTAs' routing cost.
+SS_HD int rw_pipe_stages(int) { return 2; }
 SS_HD size_t rw_pipe_smem(int w16)
 {
     return (size_t)rw_pipe_stages(w16) * 2u * kRwThreads * (size_t)w16 * 4u;
@@ -341,6 +343,7 @@ struct RwPipeArgs {
     int32_t w16;
     int32_t stages;         // 1..kRwMaxStages
     int32_t bulk;           // inputs 16-byte aligned: full tiles bulk-copied
+    int32_t group;          // tiles per CTA
     uint32_t neg1;          // 0xffffffff (see rw_route)
     uint8_t *acc;
     int32_t *obs;
@@ -379,8 +382,8 @@ __device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
     return s_perm[t];
 }
 
-// Plain launch: uniform m <= 256 and E; CTA b routes tiles kRwGroup * b ..
-// kRwGroup * b + kRwGroup - 1 of kRwThreads pairs each, from pair-major
+// Plain launch: uniform m <= 256 and E; CTA b routes tiles group * b ..
+// group * b + group - 1 of kRwThreads pairs each, from pair-major
 // shared-memory stages filled by bulk copies.
 template <int E>
 __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
@@ -394,10 +397,10 @@ __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
     const int S = a.stages;
     const uint32_t tile_words = (uint32_t)kRwThreads * (uint32_t)w16;
     const uint32_t tile_bytes = tile_words * 4u;
-    // tile j < kRwGroup of this CTA is global tile kRwGroup * blockIdx.x + j;
-    // it is bulk-copied iff the inputs are aligned and the tile is full
+    // tile j < group of this CTA is global tile group * blockIdx.x + j; it
+    // is bulk-copied iff the inputs are aligned and the tile is full
     auto tile_of = [&](int64_t j) {
-        return j < kRwGroup ? (int64_t)blockIdx.x * kRwGroup + j : a.ntiles;
+        return j < a.group ? (int64_t)blockIdx.x * a.group + j : a.ntiles;
     };
     auto by_copy = [&](int64_t tile) {
         return a.bulk && tile < a.ntiles &&
