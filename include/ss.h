@@ -144,6 +144,15 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
  * SS_OK. */
 int ss_sync(ss_ctx *ctx, void *stream);
 
+/* Self-test of the device-side failure path (not in the paper): launch one
+ * kernel that waits on an mbarrier nothing completes, with the same bounded
+ * wait the filter kernels use for their bulk copies (which give up after
+ * 2 s).  The wait gives up after limit_ns (1e3..1e10) and latches the
+ * timeout status, so the next ss_sync on `stream` returns SS_ERR_TIMEOUT and
+ * the context stays usable.  Returns SS_OK once launched, SS_ERR_INVALID_ARG
+ * or SS_ERR_CUDA. */
+int ss_check_wait_timeout(ss_ctx *ctx, int64_t limit_ns, void *stream);
+
 /* ---- batch scheduling of mixed batches (not in the paper: its GPU
  * version runs one thread per pair, Section 2.6) --------------------------
  * A batch with per-pair lengths or thresholds (or E > 31, or m > 1024) is

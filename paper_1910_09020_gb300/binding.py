@@ -39,7 +39,7 @@ EXPORTED = (
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
-    "ss_filter_submaze",
+    "ss_filter_submaze", "ss_check_wait_timeout",
     "ss_server_create",
     "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
     "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
@@ -115,6 +115,7 @@ def load(build_if_needed: bool = True):
                                             I64, P, P]
     lib.ss_filter_confusion.argtypes = [P, P, P, I64, I32, P, P]
     lib.ss_compact_accepted.argtypes = [P, P, I64, P, P, P]
+    lib.ss_check_wait_timeout.argtypes = [P, I64, P]
     lib.ss_filter_submaze.argtypes = [P, P, P, ctypes.c_int, I32, I32, I32,
                                       I32, I64, P, P, P]
     lib.ss_gather_pairs.argtypes = [P, P, P, I32, P, P, I64, P, P, P]
@@ -381,6 +382,13 @@ class Filter:
                                       _ptr(acc), _ptr(obs))
         _check(rc, "ss_filter_submaze")
         return acc[:n], obs[:n]
+
+    def check_wait_timeout(self, limit_ns: int, stream=None):
+        """Launch the bounded-wait self-test; the next sync raises
+        SSError(SS_ERR_TIMEOUT)."""
+        rc = load().ss_check_wait_timeout(self.ctx, int(limit_ns),
+                                          _stream_handle(stream) or None)
+        _check(rc, "ss_check_wait_timeout")
 
     def compact(self, accept, stream=None):
         """Indices of accepted pairs, in order: (device int64[n] buffer,

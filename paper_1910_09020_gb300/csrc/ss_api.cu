@@ -658,6 +658,17 @@ int ss_sync(ss_ctx *ctx, void *stream)
     return SS_OK;
 }
 
+int ss_check_wait_timeout(ss_ctx *ctx, int64_t limit_ns, void *stream)
+{
+    if (!ctx || limit_ns < 1000 || limit_ns > 10000000000LL)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick_stream(stream);
+    SS_CUDA(ssk::launch_wait_timeout((uint64_t)limit_ns, ctx->d_status, st));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
 int ss_get_counters(const ss_ctx *ctx, ss_counters *out)
 {
     if (!ctx || !out)

@@ -153,8 +153,11 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait for phase `parity` of `bar` to complete, for at most about limit_ns;
-// false on timeout.
+// Wait for phase `parity` of `bar` to complete, for at most about limit_ns
+// (and at most kWaitMaxPolls polls, should the timer not advance); false on
+// timeout.
+constexpr uint32_t kWaitMaxPolls = 1u << 22;
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
                                                   uint32_t parity,
                                                   uint64_t limit_ns)
@@ -162,12 +165,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
     if (mbar_try_wait(bar, parity))
         return true;
     const uint64_t t0 = global_ns();
-    for (;;) {
+    for (uint32_t polls = 0; polls < kWaitMaxPolls; ++polls) {
         if (mbar_try_wait(bar, parity))
             return true;
         if (global_ns() - t0 > limit_ns)
             return false;
     }
+    return false;
 }
 #endif
 

@@ -65,6 +65,10 @@ cudaError_t launch_submaze(const uint32_t *reads, const uint32_t *refs,
                            int32_t y, uint8_t *acc, int32_t *obs,
                            int sm_count, cudaStream_t st);
 
+// Bounded-wait self-test (ss_selftest.cu).
+cudaError_t launch_wait_timeout(uint64_t limit_ns, int *status,
+                                cudaStream_t st);
+
 // Compaction of accepted pairs (ss_compact.cu).
 size_t compact_ws_bytes(int64_t n);
 cudaError_t launch_compact(const uint8_t *acc, int64_t n, int64_t *ws,

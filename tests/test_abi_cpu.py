@@ -77,3 +77,9 @@ def test_submaze_rejects_bad_arguments_without_gpu():
                  ]:
         rc = lib.ss_filter_submaze(*args, None, P(1), P(1))
         assert rc == binding.SS_ERR_INVALID_ARG
+
+
+def test_wait_self_test_rejects_null_context():
+    lib = binding.load()
+    assert lib.ss_check_wait_timeout(None, 50_000_000, None) == \
+        binding.SS_ERR_INVALID_ARG
