@@ -17,6 +17,11 @@ Every function follows the paper (Alser et al., SneakySnake):
   filter bounds from below (Section 2.1).
 * :meth:`Oracle.pack_reference` -- the library's documented 2-bit format,
   written from that definition only (checks the pack kernel bit for bit).
+* :meth:`Oracle.filter_submaze` -- Snake-on-Chip's sub-maze decomposition
+  (Section 2.5).
+* :meth:`Oracle.cell2`, :meth:`Oracle.filter_unequal`,
+  :meth:`Oracle.filter_unequal_batch` -- pairs of different lengths with the
+  leading/trailing case-4 correction of Section 2.4.
 
 Module-level functions call the default instance built from ss_oracle.c.
 """
@@ -106,6 +111,11 @@ class Oracle:
                                                    ctypes.c_int, P]
         lib.sso_exhaustive_lower_bound.restype = i64
         lib.sso_pack_reference.argtypes = [P, i64, P]
+        lib.sso_cell2.argtypes = [P, i64, P, i64, i64, i64, i64]
+        lib.sso_cell2.restype = ctypes.c_int
+        lib.sso_filter2.argtypes = [P, i64, P, i64, i64, ctypes.c_int, P, P]
+        lib.sso_filter2_batch.argtypes = [P, P, P, P, P, P, P, i64,
+                                          ctypes.c_int, P, P]
         lib.sso_default_threads.restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -156,6 +166,45 @@ class Oracle:
         if rc != OK:
             raise ValueError(f"oracle submaze error {rc}")
         return Result(bool(acc.value), int(obs.value))
+
+    def cell2(self, Q, R, E: int, i: int, j: int) -> int:
+        """Z[i, j] for a query Q and a reference R of any lengths (1-based;
+        j indexes R)."""
+        q, r = _bytes(Q), _bytes(R)
+        return self.lib.sso_cell2(_p(q), len(Q), _p(r), len(R), E, i, j)
+
+    def filter_unequal(self, Q, R, E: int, stop_above_E: bool = True):
+        """The filter on a pair of possibly different lengths."""
+        q, r = _bytes(Q), _bytes(R)
+        acc = ctypes.c_uint8()
+        obs = ctypes.c_int64()
+        rc = self.lib.sso_filter2(_p(q), len(Q), _p(r), len(R), E,
+                                  int(stop_above_E), ctypes.byref(acc),
+                                  ctypes.byref(obs))
+        if rc != OK:
+            raise ValueError(f"oracle filter2 error {rc}")
+        return Result(bool(acc.value), int(obs.value))
+
+    def filter_unequal_batch(self, reads, read_off, read_len, refs, ref_off,
+                             ref_len, Es, threads: int = 0):
+        """Batch of filter_unequal over concatenated byte buffers."""
+        reads = np.ascontiguousarray(reads, dtype=np.uint8)
+        refs = np.ascontiguousarray(refs, dtype=np.uint8)
+        ro = np.ascontiguousarray(read_off, dtype=np.int64)
+        rl = np.ascontiguousarray(read_len, dtype=np.int32)
+        fo = np.ascontiguousarray(ref_off, dtype=np.int64)
+        fl = np.ascontiguousarray(ref_len, dtype=np.int32)
+        n = len(rl)
+        Es_arr = np.ascontiguousarray(
+            np.broadcast_to(np.asarray(Es, np.int32), (n,)))
+        acc = np.zeros(max(n, 1), dtype=np.uint8)
+        obs = np.zeros(max(n, 1), dtype=np.int32)
+        rc = self.lib.sso_filter2_batch(_p(reads), _p(ro), _p(rl), _p(refs),
+                                        _p(fo), _p(fl), _p(Es_arr), n,
+                                        threads, _p(acc), _p(obs))
+        if rc != OK:
+            raise ValueError(f"oracle filter2 batch error {rc}")
+        return acc[:n], obs[:n]
 
     def min_obstacles(self, Q, R, E: int) -> int:
         q, r = _bytes(Q), _bytes(R)
@@ -263,6 +312,20 @@ def filter_submaze(Q, R, E, t, y):
 
 def min_obstacles(Q, R, E):
     return get().min_obstacles(Q, R, E)
+
+
+def cell2(Q, R, E, i, j):
+    return get().cell2(Q, R, E, i, j)
+
+
+def filter_unequal(Q, R, E, stop_above_E=True):
+    return get().filter_unequal(Q, R, E, stop_above_E)
+
+
+def filter_unequal_batch(reads, read_off, read_len, refs, ref_off, ref_len,
+                         Es, threads=0):
+    return get().filter_unequal_batch(reads, read_off, read_len, refs,
+                                      ref_off, ref_len, Es, threads)
 
 
 def edit_distance(a, b):

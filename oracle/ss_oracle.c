@@ -385,6 +385,151 @@ int sso_filter_batch(const uint8_t *reads, const uint8_t *refs,
     return status;
 }
 
+/* ---- unequal lengths (Section 2.4, the leading/trailing correction) ------ */
+
+/* Eq. 1 for a query Q[1..mQ] and a reference R[1..mR]; column j = 1..mR
+ * compares R[j] with Q[q], q as in sso_cell.  A cell whose q falls outside
+ * 1..mQ is case 4.  With equal lengths such a cell is an obstacle (this is
+ * sso_cell).  With different lengths the obstacles case 4 puts before the
+ * query's first base (q < 1) or after its last (q > mQ) are the leading and
+ * trailing obstacles the paper deducts from the count: here they are not
+ * obstacles at all, so the net passes them free. */
+int sso_cell2(const uint8_t *Q, int64_t mQ, const uint8_t *R, int64_t mR,
+              int64_t E, int64_t i, int64_t j)
+{
+    int64_t q;
+    if (i == E + 1)
+        q = j;
+    else if (i >= 1 && i <= E)
+        q = j - i;
+    else
+        q = j + i - E - 1;
+    if (q < 1 || q > mQ)
+        return mQ == mR ? 1 : 0;
+    return base_of(Q[q - 1]) == base_of(R[j - 1]) ? 0 : 1;
+}
+
+/* Section 2.4 steps (1)-(5) on the maze of sso_cell2 (mR columns).  With
+ * mQ == mR this is sso_filter. */
+int sso_filter2(const uint8_t *Q, int64_t mQ, const uint8_t *R, int64_t mR,
+                int64_t E, int stop_above_E, uint8_t *accept,
+                int64_t *obstacles)
+{
+    if (mQ < 0 || mR < 0 || E < 0)
+        return SSO_ERR_INVALID_ARG;
+    if (!valid_sequence(Q, mQ) || !valid_sequence(R, mR))
+        return SSO_ERR_INVALID_BASE;
+    int64_t checkpoint = 1, count = 0;
+    while (checkpoint <= mR) {
+        /* step (2): the longest run of zeros from the checkpoint */
+        int64_t longest = 0;
+        for (int64_t i = 1; i <= 2 * E + 1; ++i) {
+            int64_t len = 0;
+            for (int64_t j = checkpoint; j <= mR; ++j) {
+                if (sso_cell2(Q, mQ, R, mR, E, i, j) != 0)
+                    break;
+                ++len;
+            }
+            if (len > longest)
+                longest = len;
+        }
+        if (checkpoint + longest > mR)
+            break; /* reached the destination */
+        count += 1;                            /* the obstacle after it */
+        checkpoint = checkpoint + longest + 1; /* step (3) */
+        if (stop_above_E && count > E)         /* step (4) */
+            break;
+    }
+    if (accept)
+        *accept = (uint8_t)(count <= E); /* step (5) */
+    if (obstacles)
+        *obstacles = count;
+    return SSO_OK;
+}
+
+typedef struct batch2_job {
+    const uint8_t *reads, *refs;
+    const int64_t *read_off, *ref_off;
+    const int32_t *read_len, *ref_len, *Es;
+    int64_t begin, end;
+    uint8_t *accept;
+    int32_t *obstacles;
+    int status;
+} batch2_job;
+
+static void *batch2_worker(void *arg)
+{
+    batch2_job *jb = (batch2_job *)arg;
+    jb->status = SSO_OK;
+    for (int64_t p = jb->begin; p < jb->end; ++p) {
+        uint8_t acc = 0;
+        int64_t obs = 0;
+        int rc = sso_filter2(jb->reads + jb->read_off[p], jb->read_len[p],
+                             jb->refs + jb->ref_off[p], jb->ref_len[p],
+                             jb->Es[p], 1, &acc, &obs);
+        if (rc != SSO_OK) {
+            if (jb->status == SSO_OK)
+                jb->status = rc;
+            jb->accept[p] = 0;
+            jb->obstacles[p] = -1;
+            continue;
+        }
+        jb->accept[p] = acc;
+        jb->obstacles[p] = (int32_t)obs;
+    }
+    return NULL;
+}
+
+int sso_filter2_batch(const uint8_t *reads, const int64_t *read_off,
+                      const int32_t *read_len, const uint8_t *refs,
+                      const int64_t *ref_off, const int32_t *ref_len,
+                      const int32_t *Es, int64_t n, int threads,
+                      uint8_t *accept, int32_t *obstacles)
+{
+    if (n < 0 || (n > 0 && (!reads || !refs || !read_off || !read_len ||
+                            !ref_off || !ref_len || !Es)))
+        return SSO_ERR_INVALID_ARG;
+    for (int64_t p = 0; p < n; ++p)
+        if (Es[p] < 0 || read_len[p] < 0 || ref_len[p] < 0)
+            return SSO_ERR_INVALID_ARG;
+    if (threads <= 0)
+        threads = sso_default_threads();
+    if (threads > n)
+        threads = n > 0 ? (int)n : 1;
+    batch2_job *jobs =
+        (batch2_job *)calloc((size_t)threads, sizeof(batch2_job));
+    pthread_t *tids = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !tids) {
+        free(jobs);
+        free(tids);
+        return SSO_ERR_INVALID_ARG;
+    }
+    for (int t = 0; t < threads; ++t) {
+        batch2_job *jb = &jobs[t];
+        jb->reads = reads;
+        jb->refs = refs;
+        jb->read_off = read_off;
+        jb->ref_off = ref_off;
+        jb->read_len = read_len;
+        jb->ref_len = ref_len;
+        jb->Es = Es;
+        jb->begin = n * t / threads;
+        jb->end = n * (t + 1) / threads;
+        jb->accept = accept;
+        jb->obstacles = obstacles;
+        pthread_create(&tids[t], NULL, batch2_worker, jb);
+    }
+    int status = SSO_OK;
+    for (int t = 0; t < threads; ++t) {
+        pthread_join(tids[t], NULL);
+        if (jobs[t].status != SSO_OK && status == SSO_OK)
+            status = jobs[t].status;
+    }
+    free(jobs);
+    free(tids);
+    return status;
+}
+
 /* ---- exhaustive lower-bound check -------------------------------------- */
 
 typedef struct exh_job {

@@ -71,6 +71,29 @@ int sso_filter_submaze(const uint8_t *Q, const uint8_t *R, int64_t m,
                        int64_t E, int64_t t, int64_t y, uint8_t *accept,
                        int64_t *obstacles);
 
+/* Unequal lengths (Section 2.4's correction for sequences of different
+ * length).  The maze has mR columns (one per reference base, as Eq. 1
+ * compares R[j]) and 2E+1 rows; a cell whose query index q falls outside
+ * 1..mQ is case 4.  Reading of "deduct the leading and trailing obstacles
+ * caused by the fourth case": when mQ != mR those cells (q < 1: before the
+ * query's first base; q > mQ: after its last) are not obstacles, so the net
+ * passes the sequences' overhanging ends free; when mQ == mR nothing changes
+ * (sso_cell2 == sso_cell, sso_filter2 == sso_filter). */
+int sso_cell2(const uint8_t *Q, int64_t mQ, const uint8_t *R, int64_t mR,
+              int64_t E, int64_t i, int64_t j);
+int sso_filter2(const uint8_t *Q, int64_t mQ, const uint8_t *R, int64_t mR,
+                int64_t E, int stop_above_E, uint8_t *accept,
+                int64_t *obstacles);
+/* Batch of sso_filter2 over host threads: pair p is Q = reads +
+ * read_off[p] (read_len[p] bases), R = refs + ref_off[p] (ref_len[p] bases),
+ * threshold Es[p].  Invalid pairs get obstacles -1 and the first error is
+ * returned. */
+int sso_filter2_batch(const uint8_t *reads, const int64_t *read_off,
+                      const int32_t *read_len, const uint8_t *refs,
+                      const int64_t *ref_off, const int32_t *ref_len,
+                      const int32_t *Es, int64_t n, int threads,
+                      uint8_t *accept, int32_t *obstacles);
+
 /* Minimum number of obstacles over every chain of non-overlapping escape
  * segments that links column 1 to the destination terminal (the optimum
  * Theorem 2 says the greedy reaches), by dynamic programming over

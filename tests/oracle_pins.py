@@ -14,7 +14,11 @@ Sources of truth (none of them is the oracle itself):
   force and by an independent dynamic program;
 * closed forms: identical pairs, E = 0, one substitution, one indel, the
   Hamming bound, monotonicity in E;
-* textbook edit distances and a breadth-first search over edit scripts.
+* textbook edit distances and a breadth-first search over edit scripts;
+* for pairs of different lengths: closed forms (a reference that extends the
+  query costs nothing), a banded semi-global dynamic program (no false
+  reject for approximate string matching) and Theorem 2's optimality on the
+  corrected maze.
 """
 from __future__ import annotations
 
@@ -380,6 +384,142 @@ def pin_submaze_underestimates(O):
                     prev = sub
 
 
+# ---- pairs of different lengths (Section 2.4's correction) ---------------------
+
+def _sg_band(Q: str, R: str, E: int) -> int:
+    """Edit distance of Q to a stretch of R that starts within R's first E+1
+    bases, every aligned position within E diagonals of the main one (the
+    rows of Eq. 1); the reference bases before and after the stretch are
+    free.  A plain dynamic program, independent of the oracle."""
+    mq, mr = len(Q), len(R)
+    inf = 10 ** 9
+    D = [[inf] * (mr + 1) for _ in range(mq + 1)]
+    for j in range(min(E, mr) + 1):
+        D[0][j] = 0
+    for i in range(1, mq + 1):
+        for j in range(mr + 1):
+            if abs(i - j) > E:
+                continue
+            best = inf
+            if j and abs(i - j) <= E and D[i - 1][j - 1] < inf:
+                best = min(best, D[i - 1][j - 1] + (Q[i - 1] != R[j - 1]))
+            if abs(i - 1 - j) <= E and D[i - 1][j] < inf:
+                best = min(best, D[i - 1][j] + 1)
+            if j and abs(i - j + 1) <= E and D[i][j - 1] < inf:
+                best = min(best, D[i][j - 1] + 1)
+            D[i][j] = best
+    ends = [D[mq][j] for j in range(mr + 1) if abs(mq - j) <= E]
+    return min(ends) if ends else inf
+
+
+def _unequal_pairs(seed: int, n: int, mmax: int):
+    rng = random.Random(seed)
+    out = []
+    for _ in range(n):
+        mq = rng.randint(1, mmax)
+        mr = mq + rng.choice([-3, -2, -1, 1, 2, 3, 5, 9])
+        if mr < 1:
+            mr = mq + 1
+        Q = rand_seq(rng, mq)
+        R = mutate(rng, Q, rng.randint(0, 3))
+        R = (R + rand_seq(rng, mr))[:mr]
+        out.append((Q, R))
+    return out
+
+
+def pin_unequal_equal_lengths_unchanged(O):
+    """The correction is for sequences of different length only: with equal
+    lengths the pair is filtered exactly as before."""
+    for Q, R in random_pairs(31, 200, 80, 10):
+        for E in (0, 1, 2, 4, 8):
+            assert O.filter_unequal(Q, R, E) == O.filter_pair(Q, R, E), \
+                (Q, R, E)
+
+
+def pin_unequal_free_flanks(O):
+    """Closed forms: the reference's bases before or after the query (within
+    the 2E+1 rows on the left) cost nothing, in either direction of the
+    length difference; at E = 0 the count is the Hamming distance of the
+    overlapping prefix."""
+    rng = random.Random(32)
+    for _ in range(60):
+        Q = rand_seq(rng, rng.randint(3, 60))
+        X = rand_seq(rng, rng.randint(1, 6))
+        Y = rand_seq(rng, rng.randint(1, 25))
+        for E in (0, 1, 3, 6):
+            assert O.filter_unequal(Q, Q + Y, E).obstacles == 0, (Q, Y, E)
+            assert O.filter_unequal(Q + Y, Q, E).obstacles == 0, (Q, Y, E)
+            if E >= len(X):
+                assert O.filter_unequal(Q, X + Q, E).obstacles == 0
+                assert O.filter_unequal(Q, X + Q + Y, E).obstacles == 0
+        R = rand_seq(rng, len(Q) + len(Y))
+        ham = sum(a != b for a, b in zip(Q, R))
+        assert O.filter_unequal(Q, R, 0, stop_above_E=False).obstacles == ham
+        assert O.filter_unequal(R, Q, 0, stop_above_E=False).obstacles == ham
+
+
+def pin_unequal_lower_bound_exhaustive(O):
+    """No false reject for approximate string matching: min(count, E+1) never
+    exceeds the banded semi-global distance, for every pair of ACGT strings
+    of lengths 1..3 and 1..4 that differ, and E <= 2."""
+    import itertools
+    for mq in range(1, 4):
+        for mr in range(1, 5):
+            if mq == mr:
+                continue
+            for q in itertools.product(ALPHA, repeat=mq):
+                Q = "".join(q)
+                for r in itertools.product(ALPHA, repeat=mr):
+                    R = "".join(r)
+                    for E in range(3):
+                        got = O.filter_unequal(Q, R, E).obstacles
+                        assert got <= min(_sg_band(Q, R, E), E + 1), \
+                            (Q, R, E, got)
+
+
+def pin_unequal_optimal(O):
+    """Theorem 2 on the corrected maze: the greedy count (routed to the end)
+    equals the minimum over every chain of escape segments, by a dynamic
+    program over checkpoints on the oracle's own cells."""
+    for Q, R in _unequal_pairs(33, 120, 40):
+        n = len(R)
+        for E in (0, 1, 2, 4):
+            Z = [[O.cell2(Q, R, E, i, j) for j in range(1, n + 1)]
+                 for i in range(1, 2 * E + 2)]
+            inf = 10 ** 9
+            best = [inf] * (n + 2)
+            best[1] = 0
+            for c in range(1, n + 1):
+                if best[c] >= inf:
+                    continue
+                for row in Z:
+                    e = c
+                    while e <= n and row[e - 1] == 0:
+                        e += 1
+                    nxt, cost = (n + 1, 0) if e > n else (e + 1, 1)
+                    best[nxt] = min(best[nxt], best[c] + cost)
+            want = min(best[n + 1:])
+            got = O.filter_unequal(Q, R, E, stop_above_E=False).obstacles
+            assert got == want, (Q, R, E, got, want)
+
+
+def pin_unequal_batch_matches_single(O):
+    pairs = _unequal_pairs(34, 150, 70)
+    reads = "".join(q for q, _ in pairs).encode()
+    refs = "".join(r for _, r in pairs).encode()
+    rl = np.array([len(q) for q, _ in pairs], np.int32)
+    fl = np.array([len(r) for _, r in pairs], np.int32)
+    ro = np.concatenate([[0], np.cumsum(rl)[:-1]]).astype(np.int64)
+    fo = np.concatenate([[0], np.cumsum(fl)[:-1]]).astype(np.int64)
+    Es = np.array([p % 7 for p in range(len(pairs))], np.int32)
+    acc, obs = O.filter_unequal_batch(np.frombuffer(reads, np.uint8), ro, rl,
+                                      np.frombuffer(refs, np.uint8), fo, fl,
+                                      Es, threads=3)
+    for p, (Q, R) in enumerate(pairs):
+        r = O.filter_unequal(Q, R, int(Es[p]))
+        assert (bool(acc[p]), int(obs[p])) == r, p
+
+
 ALL_PINS = [
     pin_worked_example_maze, pin_worked_example_decision,
     pin_column6_orientation, pin_row_count, pin_identical, pin_E0,
@@ -390,4 +530,7 @@ ALL_PINS = [
     pin_pack_reference, pin_batch_matches_single,
     pin_submaze_worked_example, pin_submaze_reduces_to_full,
     pin_submaze_underestimates,
+    pin_unequal_equal_lengths_unchanged, pin_unequal_free_flanks,
+    pin_unequal_lower_bound_exhaustive, pin_unequal_optimal,
+    pin_unequal_batch_matches_single,
 ]

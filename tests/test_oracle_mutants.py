@@ -66,6 +66,28 @@ MUTANTS = {
     # sub-maze: the segment cap ignored
     "submaze_no_cap": ("while (checkpoint <= last && segments < y) {",
                        "while (checkpoint <= last) {"),
+    # unequal lengths: the leading/trailing case-4 obstacles still counted
+    "unequal_no_correction": ("        return mQ == mR ? 1 : 0;",
+                              "        return 1;"),
+    # unequal lengths: the correction applied to equal lengths too
+    "unequal_always": ("        return mQ == mR ? 1 : 0;",
+                       "        return 0;"),
+    # unequal lengths: only the trailing ones deducted
+    "unequal_trailing_only": (
+        "    if (q < 1 || q > mQ)\n        return mQ == mR ? 1 : 0;",
+        "    if (q < 1)\n        return 1;\n"
+        "    if (q > mQ)\n        return mQ == mR ? 1 : 0;"),
+    # unequal lengths: only the leading ones deducted
+    "unequal_leading_only": (
+        "    if (q < 1 || q > mQ)\n        return mQ == mR ? 1 : 0;",
+        "    if (q > mQ)\n        return 1;\n"
+        "    if (q < 1)\n        return mQ == mR ? 1 : 0;"),
+    # unequal lengths: columns over the query instead of the reference
+    "unequal_columns_over_query": (
+        "            for (int64_t j = checkpoint; j <= mR; ++j) {\n"
+        "                if (sso_cell2",
+        "            for (int64_t j = checkpoint; j <= mQ; ++j) {\n"
+        "                if (sso_cell2"),
     # min-obstacle DP: a segment may hold two obstacles
     "dp_two_obstacles": (
         "                if (sso_cell(Q, R, m, E, i, e) != 0)\n"
