@@ -545,6 +545,52 @@ def run_submaze(F, pq, pr, n, acc, obs, t=8, y=3) -> dict:
     return {"t": t, "y": y, "pairs": n, "per_E": out}
 
 
+def run_unequal(F, n=2_000_000) -> dict:
+    """Reads of 100 bp against reference windows of 92..116 bp (the read
+    inside random flanks, or the window cut short): the filter for pairs of
+    different lengths, one launch per E."""
+    import torch
+
+    from paper_1910_09020_gb300 import synth
+    data = synth.pairs_unequal(SEED + 7, 0, n, M, synth.SHORT_POISSON, -8, 16)
+    reads, ro, rl, refs, fo, fl = data
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def packed(ascii_, off, lens):
+        words = (lens.astype(np.int64) + 15) // 16
+        woff = np.zeros(len(lens) + 1, np.int64)
+        np.cumsum(words, out=woff[1:])
+        out = torch.zeros(int(woff[-1]) + 4, dtype=torch.int32, device=dev)
+        F.pack(torch.from_numpy(ascii_).to(dev),
+               offsets=torch.from_numpy(off[:-1].astype(np.int64)).to(dev),
+               lengths=torch.from_numpy(lens.astype(np.int32)).to(dev),
+               out=out, out_offsets=torch.from_numpy(woff[:-1]).to(dev))
+        return out, torch.from_numpy(woff[:-1]).to(dev)
+
+    q, qo = packed(reads, ro, rl)
+    r, fo_d = packed(refs, fo, fl)
+    ql = torch.from_numpy(rl.astype(np.int32)).to(dev)
+    rlen = torch.from_numpy(fl.astype(np.int32)).to(dev)
+    F.sync()
+    out = []
+    for E in (2, 6, 10):
+        F.filter_unequal(q, qo, ql, r, fo_d, rlen, e=E)
+        a, b = _ev(), _ev()
+        a.record()
+        reps = 5
+        for _ in range(reps):
+            acc, obs = F.filter_unequal(q, qo, ql, r, fo_d, rlen, e=E)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out.append({"E": E, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+                    "accept_rate": float(acc.float().mean().item())})
+    F.sync()
+    return {"workload": f"{n // 1000000}M reads of {M} bp vs reference "
+                        f"windows of {M - 8}..{M + 16} bp (flanked or cut)",
+            "pairs": n, "per_E": out}
+
+
 def run_serving(seconds: float) -> dict:
     """Requests of 1..4096 pairs (log-uniform), lengths log-uniform
     100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
@@ -810,6 +856,7 @@ def run_ours(args):
     extras = {}
     if not args.headline_only and world == 1:
         extras["submaze_t8_y3"] = run_submaze(F, pq, pr, n, acc, obs)
+        extras["unequal_lengths"] = run_unequal(F)
         del dq, dr, pq, pr
         torch.cuda.empty_cache()
         extras["persistent_uneven_batch"] = run_batched(

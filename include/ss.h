@@ -199,6 +199,32 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
                         const int32_t *ed, int64_t n, int32_t e,
                         void *stream, uint64_t *out_counts);
 
+/* ---- pairs of different lengths (Section 2.4) ------------------------------
+ * Pair p: query (read) of read_len[p] bases at word read_off[p] of `reads`,
+ * reference of ref_len[p] bases at word ref_off[p] of `refs` (both
+ * SS_FMT_PACKED2, int64 word offsets, int32 lengths, device arrays),
+ * threshold E[p] (E = NULL: e for every pair).  The maze has ref_len[p]
+ * columns (Eq. 1 compares the reference base of each column with 2E+1 query
+ * bases).  With equal lengths the pair is filtered as by ss_filter_batch.
+ * When the lengths differ, the leading and trailing obstacles that case 4 of
+ * Eq. 1 causes -- cells whose query index falls before the query's first
+ * base or after its last -- are deducted, read as: those cells are not
+ * obstacles, so overhanging ends of either sequence cost nothing.  The
+ * count then never exceeds the edit distance of the query to the stretch of
+ * the reference it overlaps (no false reject for approximate string
+ * matching), and the greedy still finds the fewest obstacles (Theorem 2).
+ * Rows: min(E, m - 1) for equal lengths m; with different lengths E, or 0
+ * obstacles outright when E >= min(read_len, ref_len) (a diagonal that
+ * compares nothing).  More than 31 rows: obstacles -1, accept 0 and
+ * SS_ERR_UNSUPPORTED from the next ss_sync; a negative length or threshold:
+ * -1 and SS_ERR_INVALID_ARG.  Asynchronous on `stream`.  Returns SS_OK,
+ * SS_ERR_INVALID_ARG or SS_ERR_CUDA. */
+int ss_filter_unequal(ss_ctx *ctx, const void *reads, const int64_t *read_off,
+                      const int32_t *read_len, const void *refs,
+                      const int64_t *ref_off, const int32_t *ref_len,
+                      const int32_t *E, int32_t e, int64_t n, void *stream,
+                      uint8_t *out_accept, int32_t *out_obstacles);
+
 /* ---- sub-maze approximate mode (Section 2.5, Snake-on-Chip) -------------
  * The maze is cut into sub-mazes of t consecutive columns (the last may be
  * narrower); each is routed independently by the greedy of Section 2.4 from

@@ -39,7 +39,7 @@ EXPORTED = (
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
-    "ss_filter_submaze", "ss_check_wait_timeout",
+    "ss_filter_submaze", "ss_check_wait_timeout", "ss_filter_unequal",
     "ss_server_create",
     "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
     "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
@@ -116,6 +116,8 @@ def load(build_if_needed: bool = True):
     lib.ss_filter_confusion.argtypes = [P, P, P, I64, I32, P, P]
     lib.ss_compact_accepted.argtypes = [P, P, I64, P, P, P]
     lib.ss_check_wait_timeout.argtypes = [P, I64, P]
+    lib.ss_filter_unequal.argtypes = [P, P, P, P, P, P, P, P, I32, I64, P,
+                                      P, P]
     lib.ss_filter_submaze.argtypes = [P, P, P, ctypes.c_int, I32, I32, I32,
                                       I32, I64, P, P, P]
     lib.ss_gather_pairs.argtypes = [P, P, P, I32, P, P, I64, P, P, P]
@@ -381,6 +383,22 @@ class Filter:
                                       _stream_handle(stream) or None,
                                       _ptr(acc), _ptr(obs))
         _check(rc, "ss_filter_submaze")
+        return acc[:n], obs[:n]
+
+    def filter_unequal(self, reads, read_off, read_len, refs, ref_off,
+                       ref_len, *, e: int = 0, E=None, stream=None):
+        """Pairs of possibly different lengths (packed, device arrays of
+        word offsets and base lengths); returns (accept, obstacles)."""
+        import torch
+        n = read_len.shape[0]
+        dev = read_len.device
+        acc = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        obs = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        rc = load().ss_filter_unequal(
+            self.ctx, _ptr(reads), _ptr(read_off), _ptr(read_len), _ptr(refs),
+            _ptr(ref_off), _ptr(ref_len), _ptr(E), e, n,
+            _stream_handle(stream) or None, _ptr(acc), _ptr(obs))
+        _check(rc, "ss_filter_unequal")
         return acc[:n], obs[:n]
 
     def check_wait_timeout(self, limit_ns: int, stream=None):

@@ -713,6 +713,30 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
     return SS_OK;
 }
 
+int ss_filter_unequal(ss_ctx *ctx, const void *reads, const int64_t *read_off,
+                      const int32_t *read_len, const void *refs,
+                      const int64_t *ref_off, const int32_t *ref_len,
+                      const int32_t *E, int32_t e, int64_t n, void *stream,
+                      uint8_t *out_accept, int32_t *out_obstacles)
+{
+    if (!ctx || n < 0 || (!E && e < 0))
+        return SS_ERR_INVALID_ARG;
+    if (n == 0)
+        return SS_OK;
+    if (!reads || !refs || !read_off || !read_len || !ref_off || !ref_len ||
+        !out_accept || !out_obstacles)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick_stream(stream);
+    SS_CUDA(ssk::launch_unequal((const uint32_t *)reads, read_off, read_len,
+                                (const uint32_t *)refs, ref_off, ref_len, E,
+                                e, n, out_accept, out_obstacles,
+                                ctx->d_status, ctx->sm_count, st));
+    ctx->counters.launches += 1;
+    ctx->counters.pairs += n;
+    return SS_OK;
+}
+
 int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
                       int format, int32_t m, int32_t e, int32_t t, int32_t y,
                       int64_t n, void *stream, uint8_t *out_accept,

@@ -65,6 +65,14 @@ cudaError_t launch_submaze(const uint32_t *reads, const uint32_t *refs,
                            int32_t y, uint8_t *acc, int32_t *obs,
                            int sm_count, cudaStream_t st);
 
+// Pairs of different lengths (ss_unequal.cu).
+cudaError_t launch_unequal(const uint32_t *reads, const int64_t *read_off,
+                           const int32_t *read_len, const uint32_t *refs,
+                           const int64_t *ref_off, const int32_t *ref_len,
+                           const int32_t *E, int32_t e, int64_t n,
+                           uint8_t *acc, int32_t *obs, int *status,
+                           int sm_count, cudaStream_t st);
+
 // Bounded-wait self-test (ss_selftest.cu).
 cudaError_t launch_wait_timeout(uint64_t limit_ns, int *status,
                                 cudaStream_t st);

@@ -184,3 +184,34 @@ def thresholds(lengths: np.ndarray, percent: float) -> np.ndarray:
     # integer arithmetic on percent * 1000 keeps floor() exact
     num = lengths * int(round(percent * 1000))
     return (num // 100000).astype(np.int32)
+
+
+def pairs_unequal(seed: int, first: int, n: int, m: int, recipe: Recipe,
+                  delta_lo: int, delta_hi: int, threads: int = 0):
+    """Reads of m bases against reference windows of m + d bases, d uniform
+    in delta_lo..delta_hi per pair: for d >= 0 the window is the edited copy
+    of the read with random flanks of o and d - o bases (o uniform in
+    0..d); for d < 0 it is the edited copy cut to m + d bases.  Returns
+    (reads, read_offsets, read_lengths, refs, ref_offsets, ref_lengths),
+    offsets in bytes (n + 1 entries)."""
+    core_len = np.full(n, m, dtype=np.int32)
+    reads, core, _ = pairs_varlen(seed, first, core_len, recipe, threads)
+    core = core[:n * m].reshape(n, m) if m > 0 else core[:0].reshape(n, 0)
+    rng = np.random.default_rng([seed, first, n, 0x0E0A1])
+    d = rng.integers(delta_lo, delta_hi + 1, size=n)
+    o = (rng.random(n) * (np.maximum(d, 0) + 1)).astype(np.int64)
+    ref_len = np.maximum(m + d, 0).astype(np.int32)
+    ref_off = offsets_of(ref_len)
+    total = int(ref_off[-1])
+    alphabet = np.frombuffer(b"ACGT", dtype=np.uint8)
+    refs = alphabet[rng.integers(0, 4, size=max(total, 1), dtype=np.uint8)]
+    col = np.arange(m, dtype=np.int64)
+    chunk = max(1, (1 << 24) // max(m, 1))
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        start = ref_off[a:b] + np.where(d[a:b] >= 0, o[a:b], 0)
+        keep = col[None, :] < ref_len[a:b, None]  # d < 0: cut the tail
+        idx = start[:, None] + col[None, :]
+        refs[idx[keep]] = core[a:b][keep]
+    return (reads, offsets_of(core_len), core_len, refs[:total], ref_off,
+            ref_len)

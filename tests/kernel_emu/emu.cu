@@ -9,6 +9,7 @@
 #include "ss_pack.cuh"
 #include "ss_rw.cuh"
 #include "ss_submaze.cuh"
+#include "ss_unequal.cuh"
 #include "ss_verify.cuh"
 
 using namespace ssk;
@@ -94,6 +95,24 @@ uint32_t emu_pack_chunk(const uint8_t *b16, uint32_t *err)
 uint32_t emu_pack_window(uint32_t c0, uint32_t c1, uint32_t r)
 {
     return pack_window(c0, c1, r);
+}
+
+// Pairs of different lengths: count, or -2 when more than 31 rows.
+int emu_unequal(const uint32_t *q, int mQ, const uint32_t *r, int mR, int E)
+{
+    const GlobalSeq Q{q, (mQ + 15) / 16}, R{r, (mR + 15) / 16};
+    const int rows = unequal_rows(mQ, mR, E);
+    if (rows < 0)
+        return 0;
+    if (rows <= 3)
+        return rw_route2<3>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 7)
+        return rw_route2<7>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 15)
+        return rw_route2<15>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 31)
+        return rw_route2<31>(Q, mQ, R, mR, E, 0xffffffffu);
+    return -2;
 }
 
 // Sub-maze approximate mode: t-column sub-mazes, at most y obstacles each.

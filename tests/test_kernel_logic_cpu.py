@@ -161,3 +161,23 @@ def test_pack_chunk_and_window_random_streams(emu):
                 got = emu.emu_pack_window(chunks[k], chunks[k + 1], r)
                 start = 16 * k + r
                 assert got == int(oracle.pack_reference(s[start:start + 16])[0])
+
+
+def test_unequal_lengths_match_oracle(emu):
+    """Pairs of different lengths (and some equal): the library's routine
+    against oracle.filter_unequal."""
+    rng = np.random.default_rng(11)
+    for i in range(400):
+        mq = int(rng.integers(1, 300))
+        mr = max(1, mq + int(rng.choice([-40, -9, -3, -1, 0, 1, 2, 5, 17, 70])))
+        rec = synth.rate_recipe(float(rng.choice([0.02, 0.1, 0.3])))
+        Q, R = pairs(1200 + i, 1, max(mq, mr), rec)[0]
+        Q = Q[:mq]
+        R = R[:mr]
+        q, r = packed(Q), packed(R)
+        for E in (0, 1, 3, 7, 12, 31):
+            got = emu.emu_unequal(P(q), mq, P(r), mr, E)
+            if got == -2:
+                continue
+            want = oracle.filter_unequal(Q, R, E).obstacles
+            assert got == want, (mq, mr, E, got, want)
