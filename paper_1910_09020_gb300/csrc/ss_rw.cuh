@@ -212,21 +212,30 @@ struct RwUniformArgs {
     int32_t *obs;
 };
 
-// Predicted routing cost of a staged pair: mismatches on the main diagonal
-// over its first 32 bases (0..31).  Random pairs score high and are
-// rejected early; similar pairs score low and route to the end.
+// Predicted routing cost of a staged pair: the fewest mismatches over its
+// first 32 reference bases on the three central diagonals (s = -1, 0, +1),
+// capped at 31.  Random pairs score high and are rejected early; similar
+// pairs score low -- also those with an indel early on, which shift the
+// main diagonal -- and route to the end.  Words i of the pair are at
+// sq[i * ld], sr[i * ld].
 __device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
                                            const uint32_t *sr, int ld,
                                            int w16)
 {
-    int mism = 0;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-        if (i < w16) {
-            const uint32_t x = sq[i * ld] ^ sr[i * ld];
-            mism += __popc((x | (x >> 16)) & 0xffffu);
-        }
-    return mism < 31 ? mism : 31;
+    const uint32_t q0 = sq[0], q1 = w16 > 1 ? sq[ld] : 0u;
+    const uint32_t q2 = w16 > 2 ? sq[2 * ld] : 0u;
+    const uint32_t q3 = w16 > 3 ? sq[3 * ld] : 0u;
+    const uint32_t r0 = sr[0], r1 = w16 > 1 ? sr[ld] : 0u;
+    uint32_t qlo, qhi, qlo_n, qhi_n, rlo, rhi;
+    planes_of(q0, q1, qlo, qhi);
+    planes_of(q2, q3, qlo_n, qhi_n);
+    planes_of(r0, r1, rlo, rhi);
+    const uint32_t d0 = (qlo ^ rlo) | (qhi ^ rhi);
+    const uint32_t dp = (funnel_r(qlo, qlo_n, 1) ^ rlo) |
+                        (funnel_r(qhi, qhi_n, 1) ^ rhi);
+    const uint32_t dm = (((qlo << 1) ^ rlo) | ((qhi << 1) ^ rhi)) & ~1u;
+    const int k = imin(__popc(d0), imin(__popc(dp), __popc(dm)));
+    return k < 31 ? k : 31;
 }
 
 // Plain launch for long reads: uniform m and E, one thread per pair, one CTA
