@@ -213,11 +213,13 @@ struct RwUniformArgs {
 };
 
 // Predicted routing cost of a staged pair: the fewest mismatches over its
-// first 32 reference bases on the three central diagonals (s = -1, 0, +1),
+// first 32 reference bases on the five central diagonals (s = -2..2),
 // capped at 31.  Random pairs score high and are rejected early; similar
 // pairs score low -- also those with an indel early on, which shift the
-// main diagonal -- and route to the end.  Words i of the pair are at
-// sq[i * ld], sr[i * ld].
+// main diagonal -- and route to the end.  (A cost model over the oracle's
+// per-word iteration counts ranked 5 diagonals above 1, 3, 7 and 9, and
+// above wider windows of bases.)  Words i of the pair are at sq[i * ld],
+// sr[i * ld].
 __device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
                                            const uint32_t *sr, int ld,
                                            int w16)
@@ -230,11 +232,15 @@ __device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
     planes_of(q0, q1, qlo, qhi);
     planes_of(q2, q3, qlo_n, qhi_n);
     planes_of(r0, r1, rlo, rhi);
-    const uint32_t d0 = (qlo ^ rlo) | (qhi ^ rhi);
-    const uint32_t dp = (funnel_r(qlo, qlo_n, 1) ^ rlo) |
-                        (funnel_r(qhi, qhi_n, 1) ^ rhi);
-    const uint32_t dm = (((qlo << 1) ^ rlo) | ((qhi << 1) ^ rhi)) & ~1u;
-    const int k = imin(__popc(d0), imin(__popc(dp), __popc(dm)));
+    int k = __popc((qlo ^ rlo) | (qhi ^ rhi));
+#pragma unroll
+    for (int s = 1; s <= 2; ++s) {
+        const uint32_t up = (funnel_r(qlo, qlo_n, s) ^ rlo) |
+                            (funnel_r(qhi, qhi_n, s) ^ rhi);
+        const uint32_t dn = (((qlo << s) ^ rlo) | ((qhi << s) ^ rhi)) &
+                            (0xffffffffu << s);
+        k = imin(k, imin(__popc(up), __popc(dn)));
+    }
     return k < 31 ? k : 31;
 }
 
