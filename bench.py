@@ -772,6 +772,19 @@ def run_ours(args):
         # the device path and the host path must agree
         same = (torch.equal(hacc, acc.cpu()) and torch.equal(hobs, obs.cpu()))
         e2e["matches_device_path"] = bool(same)
+        # the host link's own rate: one pinned host -> device copy of the
+        # same input bytes (the e2e path cannot beat bytes / this rate)
+        a, b = _ev(), _ev()
+        torch.cuda.synchronize()
+        a.record()
+        dq.copy_(hq, non_blocking=True)
+        dr.copy_(hr, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        h2d_gbs = 2 * n * M / (a.elapsed_time(b) * 1e-3) / 1e9
+        e2e["h2d_copy_gbs"] = h2d_gbs
+        e2e["copy_bound_pairs_per_s"] = (
+            world * pairs_per_step / (2 * n * M / (h2d_gbs * 1e9)))
 
     if rank != 0:
         F.close()

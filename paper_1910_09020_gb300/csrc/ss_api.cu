@@ -559,9 +559,13 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     const size_t per_pair = 2 * seq_in +
                             (format == SS_FMT_ASCII ? 2 * packed : 0) +
                             (size_t)n_e * 5 + (all_plain ? 0 : 2);
-    // two pipeline slots, each holding one chunk
+    // two pipeline slots, each holding one chunk.  The copies in bound the
+    // pipeline (the host link is slower than the filter), so the time not
+    // overlapped is the first chunk's copy and the last chunk's compute and
+    // copy back: chunks of 2M pairs keep both short and each launch still
+    // fills the GPU.
     int64_t chunk = (int64_t)(ctx->budget / (2 * per_pair + 2048));
-    chunk = std::min<int64_t>(chunk, (int64_t)1 << 22);
+    chunk = std::min<int64_t>(chunk, (int64_t)1 << 21);
     chunk = std::min(chunk, n);
     if (chunk < 1)
         return SS_ERR_OOM;
