@@ -61,16 +61,16 @@ struct SmemSeq {
     }
 };
 
-// Packed words of one sequence, contiguous in shared memory.
-struct SmemSeqC {
+// Packed words of one sequence, contiguous in shared memory that extends at
+// least 4 words past the sequence (the next pair's words or padding): no
+// bounds check.  rw_route reads at most 4 words past ceil(m/16), and what it
+// finds there only touches columns >= m (reference) or bits that the
+// query-base-exists plane marks as case 4 (query).
+struct SmemSeqPad {
     const uint32_t *s;
-    int w16;
     SS_HD void planes(int k, uint32_t &lo, uint32_t &hi) const
     {
-        const int i = 2 * k;
-        const uint32_t p0 = i < w16 ? s[i] : 0u;
-        const uint32_t p1 = i + 1 < w16 ? s[i + 1] : 0u;
-        planes_of(p0, p1, lo, hi);
+        planes_of(s[2 * k], s[2 * k + 1], lo, hi);
     }
 };
 
@@ -344,9 +344,11 @@ constexpr uint64_t kRwWaitNs = 2000000000ull;  // 2 s per stage wait
 // Two stages: a third adds shared memory (fewer resident CTAs) and measured
 // no faster; more tiles per CTA than 8 unbalance the CTAs' routing cost.
 SS_HD int rw_pipe_stages(int) { return 2; }
+constexpr int kRwPadWords = 4;  // read past the last pair of the ring
 SS_HD size_t rw_pipe_smem(int w16)
 {
-    return (size_t)rw_pipe_stages(w16) * 2u * kRwThreads * (size_t)w16 * 4u;
+    return ((size_t)rw_pipe_stages(w16) * 2u * kRwThreads * (size_t)w16 +
+            kRwPadWords) * 4u;
 }
 
 struct RwPipeArgs {
@@ -477,8 +479,8 @@ __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
         if (E >= 2)
             u = rw_sort_tile(sQ, sR, w16, np, s_cnt, s_perm);
         if (t < np) {
-            const SmemSeqC q{sQ + u * w16, w16};
-            const SmemSeqC r{sR + u * w16, w16};
+            const SmemSeqPad q{sQ + u * w16};
+            const SmemSeqPad r{sR + u * w16};
             const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
             a.acc[p0 + u] = (uint8_t)(cnt <= E);
             a.obs[p0 + u] = cnt;
