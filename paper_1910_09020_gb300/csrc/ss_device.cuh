@@ -184,7 +184,14 @@ SS_HD uint32_t mask_from(int lim)
 // Bits t < lim set (lim <= 0: none, lim >= 32: all).
 SS_HD uint32_t mask_below(int lim)
 {
+#ifdef __CUDA_ARCH__
+    // shl.b32 clamps shift amounts above 32 to 32 (giving 0)
+    uint32_t b;
+    asm("shl.b32 %0, 1, %1;" : "=r"(b) : "r"((uint32_t)imax(lim, 0)));
+    return b - 1u;
+#else
     return lim <= 0 ? 0u : (lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u));
+#endif
 }
 
 // ceil(2^32 / d) for d >= 2 (0 for d <= 1, where fast_div returns x):

@@ -112,10 +112,13 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
         const int base = k << 5;
         uint32_t rlo, rhi;
         Rs.planes(k, rlo, rhi);
-        const bool edge = (k == 0) || (base + 32 + EMAX > m);
+        // Eq. 1 case 4 on the columns below m: row s < 0 reads query
+        // indices below 0 only in word 0, row s > 0 reads indices past m
+        // only within 32 + s columns of m, and row 0 never leaves 0..m-1.
+        const bool lo_edge = k == 0;
+        const bool hi_edge = base + 32 + EMAX > m;
         // "Q base exists" plane around word k (bits of Q indices in 0..m-1),
-        // shifted with each row like Q itself: Eq. 1 case 4.
-        const uint32_t v_p = k == 0 ? 0u : 0xffffffffu;
+        // shifted with each row like Q itself
         const uint32_t v_c = mask_below(m - base);
         const uint32_t v_n = mask_below(m - base - 32);
         // Eq. 1 for the 32 columns of word k, every row.  Columns past m are
@@ -132,14 +135,11 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
                 ql = funnel_l(qlo_p, qlo_c, -s);
                 qh = funnel_l(qhi_p, qhi_c, -s);
             }
-            uint32_t z;
-            if (edge) {
-                const uint32_t qv = s >= 0 ? funnel_r(v_c, v_n, s)
-                                           : funnel_l(v_p, v_c, -s);
-                z = (ql ^ rlo) | (qh ^ rhi) | ~qv;
-            } else {
-                z = (ql ^ rlo) | (qh ^ rhi);
-            }
+            uint32_t z = (ql ^ rlo) | (qh ^ rhi);
+            if (s < 0 && lo_edge)
+                z |= ~funnel_l(0u, v_c, -s);
+            else if (s > 0 && hi_edge)
+                z |= ~funnel_r(v_c, v_n, s);
             if (!EXACT && (s > E || -s > E))
                 z = 0xffffffffu;  // row outside this pair's 2E+1
             Z[r] = z;
