@@ -75,35 +75,53 @@ __global__ void __launch_bounds__(kPackThreads)
     // chunks [cb, cb + nc): the span, plus one (windows read chunk k+1)
     const int nc = (int)(((b1 + 15) >> 4) - cb) + 1;
     const int64_t limit = n * (int64_t)m;  // input bytes
-    const bool aligned = ((uintptr_t)ascii & 15) == 0;
+    // every chunk of the span whole, 16-byte aligned and inside the input:
+    // the common case, one uniform branch for the CTA
+    const bool fast = ((uintptr_t)ascii & 15) == 0 &&
+                      (cb + nc) * 16 <= limit;
     uint32_t err = 0;
     // phase 1: chunks -> code stream
     uint32_t x[kPackIter][4];
+    if (fast) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(ascii) + cb;
 #pragma unroll
-    for (int i = 0; i < kPackIter; ++i) {
-        const int c = (int)threadIdx.x + i * kPackThreads;
-        const int64_t at = (cb + c) * 16;
-        if (c < nc) {
-            if (aligned && at + 16 <= limit) {
-                const uint4 v =
-                    __ldg(reinterpret_cast<const uint4 *>(ascii + at));
+        for (int i = 0; i < kPackIter; ++i) {
+            const int c = (int)threadIdx.x + i * kPackThreads;
+            if (c < nc) {
+                const uint4 v = __ldg(src + c);
                 x[i][0] = v.x;
                 x[i][1] = v.y;
                 x[i][2] = v.z;
                 x[i][3] = v.w;
-            } else {
-                // the input's last partial chunk, or an unaligned input:
-                // bytes past the end count as 'A'
+            }
+        }
+    } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t w = 0;
-                    for (int b = 0; b < 4; ++b) {
-                        const int64_t j = at + 4 * q + b;
-                        const uint32_t ch =
-                            j < limit ? (uint32_t)__ldg(ascii + j) : 0x41u;
-                        w |= ch << (8 * b);
+        for (int i = 0; i < kPackIter; ++i) {
+            const int c = (int)threadIdx.x + i * kPackThreads;
+            const int64_t at = (cb + c) * 16;
+            if (c < nc) {
+                if (((uintptr_t)ascii & 15) == 0 && at + 16 <= limit) {
+                    const uint4 v =
+                        __ldg(reinterpret_cast<const uint4 *>(ascii + at));
+                    x[i][0] = v.x;
+                    x[i][1] = v.y;
+                    x[i][2] = v.z;
+                    x[i][3] = v.w;
+                } else {
+                    // the input's last partial chunk, or an unaligned input:
+                    // bytes past the end count as 'A'
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t w = 0;
+                        for (int b = 0; b < 4; ++b) {
+                            const int64_t j = at + 4 * q + b;
+                            const uint32_t ch =
+                                j < limit ? (uint32_t)__ldg(ascii + j) : 0x41u;
+                            w |= ch << (8 * b);
+                        }
+                        x[i][q] = w;
                     }
-                    x[i][q] = w;
                 }
             }
         }
@@ -127,11 +145,10 @@ __global__ void __launch_bounds__(kPackThreads)
             const uint32_t w = rel - dp * (uint32_t)w16;
             const uint32_t o = o0 + dp * (uint32_t)m + 16u * w;
             const uint32_t kk = o >> 4;
-            uint32_t v = pack_window(code[kk], code[kk + 1], o & 15u);
-            const int len = m - 16 * (int)w;  // < 16 on a pair's last word
-            if (len < 16)
-                v &= ((1u << len) - 1u) * 0x10001u;
-            out[g0 + j] = v;
+            const uint32_t v = pack_window(code[kk], code[kk + 1], o & 15u);
+            // codes past the pair's end (its last word) are zero, no branch
+            const uint32_t keep = mask_below(m - 16 * (int)w) & 0xffffu;
+            out[g0 + j] = v & (keep * 0x10001u);
         }
     }
     if (__any_sync(0xffffffffu, err != 0u) && (threadIdx.x & 31) == 0)
