@@ -54,7 +54,7 @@ constexpr int kPackChunks = kPackWords + 4;  // code-stream words per CTA
 constexpr int kPackIter = (kPackChunks + kPackThreads - 1) / kPackThreads;
 
 // Fixed stride: pair p at byte p*m, output at word p*w16.
-__global__ void __launch_bounds__(kPackThreads)
+__global__ void __launch_bounds__(kPackThreads, 8)
     k_pack_fixed(const uint8_t *__restrict__ ascii, int64_t n, int32_t m,
                  int32_t w16, uint32_t w16_magic, uint32_t *__restrict__ out,
                  int *status)
