@@ -537,7 +537,10 @@ def run_submaze(F, pq, pr, n, acc, obs, t=8, y=3) -> dict:
         lost = int((acc[k].to(torch.int32) - sacc.to(torch.int32)).clamp(min=0)
                    .sum().item())
         above = int((sobs > obs[k]).sum().item())
+        gbs = n * FILTER_BYTES_PER_PAIR / (ms * 1e-3) / 1e9
         out.append({"E": E, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+                    "hbm_gbs": gbs,
+                    "hbm_frac": gbs / measured_peaks()["hbm_gbs"],
                     "accepts": int(sacc.sum(dtype=torch.int64).item()),
                     "exact_accepts": int(acc[k].sum(dtype=torch.int64).item()),
                     "added_accepts": extra, "lost_accepts": lost,
@@ -572,6 +575,11 @@ def run_unequal(F, n=2_000_000) -> dict:
     ql = torch.from_numpy(rl.astype(np.int32)).to(dev)
     rlen = torch.from_numpy(fl.astype(np.int32)).to(dev)
     F.sync()
+    # algorithmic bytes per launch: both packed sequences, their word
+    # offsets and lengths (8 + 4 B each), and the two results
+    words = int(((rl.astype(np.int64) + 15) // 16).sum()
+                + ((fl.astype(np.int64) + 15) // 16).sum())
+    nbytes = 4 * words + n * (2 * 12 + 5)
     out = []
     for E in (2, 6, 10):
         F.filter_unequal(q, qo, ql, r, fo_d, rlen, e=E)
@@ -583,7 +591,10 @@ def run_unequal(F, n=2_000_000) -> dict:
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
+        gbs = nbytes / (ms * 1e-3) / 1e9
         out.append({"E": E, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+                    "hbm_gbs": gbs,
+                    "hbm_frac": gbs / measured_peaks()["hbm_gbs"],
                     "accept_rate": float(acc.float().mean().item())})
     F.sync()
     return {"workload": f"{n // 1000000}M reads of {M} bp vs reference "
