@@ -244,6 +244,39 @@ __device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
     return k < 31 ? k : 31;
 }
 
+// Order the tile's pairs by predicted cost (counting sort on the CTA):
+// returns the pair this thread routes.  Word i of the tile's pair u is at
+// sQ[u * pair_ld + i * word_ld] (likewise sR).  s_cnt must be zero on entry.
+__device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
+                                            const uint32_t *sR, int pair_ld,
+                                            int word_ld, int w16, int np,
+                                            int *s_cnt, uint8_t *s_perm)
+{
+    const int t = threadIdx.x;
+    int key = 0, rank = 0;
+    if (t < np) {
+        key = rw_cost_key(sQ + t * pair_ld, sR + t * pair_ld, word_ld, w16);
+        rank = atomicAdd(&s_cnt[key], 1);
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int c = s_cnt[t];
+        int x = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (t >= off)
+                x += y;
+        }
+        s_cnt[t] = x - c;  // exclusive start of bucket t
+    }
+    __syncthreads();
+    if (t < np)
+        s_perm[s_cnt[key] + rank] = (uint8_t)t;
+    __syncthreads();
+    return s_perm[t];
+}
+
 // Plain launch for long reads: uniform m and E, one thread per pair, one CTA
 // per T pairs.  The CTA stages its pairs (128-bit loads when aligned), orders
 // them by a predicted routing cost so that each warp holds pairs of similar
@@ -303,30 +336,9 @@ __global__ void __launch_bounds__(128)
         sR[i * ld + u] = __ldg(gr + idx);
     }
     __syncthreads();
-    // counting sort of the CTA's pairs by predicted cost
-    int key = 0, rank = 0;
+    // order the CTA's pairs by predicted cost
+    const int u = rw_sort_tile(sQ, sR, 1, ld, w16, np, s_cnt, s_perm);
     if (t < np) {
-        key = rw_cost_key(sQ + t, sR + t, ld, w16);
-        rank = atomicAdd(&s_cnt[key], 1);
-    }
-    __syncthreads();
-    if (t < 32) {
-        const int c = s_cnt[t];
-        int x = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, off);
-            if (t >= off)
-                x += y;
-        }
-        s_cnt[t] = x - c;  // exclusive start of bucket t
-    }
-    __syncthreads();
-    if (t < np)
-        s_perm[s_cnt[key] + rank] = (uint8_t)t;
-    __syncthreads();
-    if (t < np) {
-        const int u = s_perm[t];
         const SmemSeq q{sQ + u, ld, w16};
         const SmemSeq r{sR + u, ld, w16};
         const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
@@ -335,7 +347,7 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-constexpr int kRwMaxStages = 3;
+constexpr int kRwMaxStages = 2;
 constexpr int kRwGroup = 8;                  // tiles per CTA
 constexpr int kRwPipeMaxW16 = 16;            // m <= 256
 constexpr uint64_t kRwWaitNs = 2000000000ull;  // 2 s per stage wait
@@ -366,38 +378,6 @@ struct RwPipeArgs {
     int32_t *obs;
     int *status;
 };
-
-// Order the tile's pairs by predicted cost (counting sort on the CTA):
-// returns the pair this thread routes.  s_cnt must be zero on entry.
-__device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
-                                            const uint32_t *sR, int w16,
-                                            int np, int *s_cnt,
-                                            uint8_t *s_perm)
-{
-    const int t = threadIdx.x;
-    int key = 0, rank = 0;
-    if (t < np) {
-        key = rw_cost_key(sQ + t * w16, sR + t * w16, 1, w16);
-        rank = atomicAdd(&s_cnt[key], 1);
-    }
-    __syncthreads();
-    if (t < 32) {
-        const int c = s_cnt[t];
-        int x = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, off);
-            if (t >= off)
-                x += y;
-        }
-        s_cnt[t] = x - c;  // exclusive start of bucket t
-    }
-    __syncthreads();
-    if (t < np)
-        s_perm[s_cnt[key] + rank] = (uint8_t)t;
-    __syncthreads();
-    return s_perm[t];
-}
 
 // Plain launch: uniform m <= 256 and E; CTA b routes tiles group * b ..
 // group * b + group - 1 of kRwThreads pairs each, from pair-major
@@ -477,7 +457,7 @@ __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
         }
         int u = t;
         if (E >= 2)
-            u = rw_sort_tile(sQ, sR, w16, np, s_cnt, s_perm);
+            u = rw_sort_tile(sQ, sR, w16, 1, w16, np, s_cnt, s_perm);
         if (t < np) {
             const SmemSeqPad q{sQ + u * w16};
             const SmemSeqPad r{sR + u * w16};
