@@ -602,6 +602,54 @@ def run_unequal(F, n=2_000_000) -> dict:
             "pairs": n, "per_E": out}
 
 
+def run_compaction(F, pq, pr, acc, n, E) -> dict:
+    """The accepted pairs of one sweep launch compacted into an index list
+    and gathered into dense packed buffers (the aligner's input)."""
+    import torch
+
+    from paper_1910_09020_gb300 import binding
+    lib = binding.load()
+    w16 = binding.ss_packed_words(M)
+    idx = torch.empty(n, dtype=torch.int64, device=pq.device)
+    cnt = torch.empty(1, dtype=torch.int64, device=pq.device)
+    gq = torch.empty(n * w16, dtype=torch.int32, device=pq.device)
+    gr = torch.empty_like(gq)
+    st = torch.cuda.current_stream().cuda_stream
+
+    def compact():
+        binding._check(lib.ss_compact_accepted(
+            F.ctx, acc.data_ptr(), n, st, idx.data_ptr(), cnt.data_ptr()),
+            "ss_compact_accepted")
+
+    def gather():
+        binding._check(lib.ss_gather_pairs(
+            F.ctx, pq.data_ptr(), pr.data_ptr(), M, idx.data_ptr(),
+            cnt.data_ptr(), n, st, gq.data_ptr(), gr.data_ptr()),
+            "ss_gather_pairs")
+
+    compact()
+    gather()
+    torch.cuda.synchronize()
+    c = int(cnt.item())
+    out = {"E": E, "pairs": n, "accepted": c}
+    for name, fn, nbytes in (
+            ("compact", compact, 2 * n + 8 * c + 8),
+            # per accepted pair: its index read, its words read and written
+            ("gather", gather, c * (8 + 16 * w16))):
+        a, b = _ev(), _ev()
+        a.record()
+        for _ in range(5):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 5
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "hbm_gbs": gbs,
+                     "hbm_frac": gbs / measured_peaks()["hbm_gbs"]}
+    F.sync()
+    return out
+
+
 def run_serving(seconds: float) -> dict:
     """Requests of 1..4096 pairs (log-uniform), lengths log-uniform
     100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
@@ -881,6 +929,8 @@ def run_ours(args):
     if not args.headline_only and world == 1:
         extras["submaze_t8_y3"] = run_submaze(F, pq, pr, n, acc, obs)
         extras["unequal_lengths"] = run_unequal(F)
+        k4 = SWEEP.index(4)
+        extras["compaction"] = run_compaction(F, pq, pr, acc[k4], n, 4)
         del dq, dr, pq, pr
         torch.cuda.empty_cache()
         extras["persistent_uneven_batch"] = run_batched(

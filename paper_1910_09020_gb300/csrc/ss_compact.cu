@@ -112,25 +112,43 @@ __global__ void __launch_bounds__(kCompactThreads)
 
 // Dense copy of the selected fixed-stride pairs: slot i <- pair index[i],
 // for i < min(*count, n); the outputs hold n slots and the sources n pairs.
+// A warp copies 32 slots at a time: lane l holds slot i0 + l's source
+// index, and the 32 * w16 words are spread over the lanes in output order,
+// so every store instruction writes 32 consecutive words.
 __global__ void k_gather_pairs(const uint32_t *__restrict__ reads,
                                const uint32_t *__restrict__ refs, int w16,
+                               uint32_t w16_magic,
                                const int64_t *__restrict__ index,
                                const int64_t *__restrict__ count,
                                uint32_t *__restrict__ out_reads,
                                uint32_t *__restrict__ out_refs, int64_t n)
 {
+    const int lane = threadIdx.x & 31;
     const int64_t c = *count;
     const int64_t cnt = c < n ? (c > 0 ? c : 0) : n;  // outputs hold n slots
-    const int64_t total = cnt * w16;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-         g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = g / w16;
-        const int w = (int)(g - i * w16);
-        const int64_t src = index[i];
-        if (src < 0 || src >= n)
-            continue;
-        out_reads[g] = reads[src * w16 + w];
-        out_refs[g] = refs[src * w16 + w];
+    const int64_t warp =
+        ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i0 = warp * 32; i0 < cnt; i0 += nwarps * 32) {
+        const int np = (int)(cnt - i0 < 32 ? cnt - i0 : 32);
+        const int64_t my_src = lane < np ? index[i0 + lane] : -1;
+        const int total = np * w16;
+        for (int t0 = 0; t0 < total; t0 += 32) {  // warp-uniform
+            const int t = t0 + lane;
+            const uint32_t tc = (uint32_t)(t < total ? t : total - 1);
+            // the magic quotient is exact while tc * w16 < 2^32, i.e. for
+            // w16 < 11585; longer sequences divide plainly
+            const uint32_t p = w16 < 11585
+                                   ? fast_div(tc, (uint32_t)w16, w16_magic)
+                                   : tc / (uint32_t)w16;
+            const int w = (int)(tc - p * (uint32_t)w16);
+            const int64_t src = __shfl_sync(0xffffffffu, my_src, (int)p);
+            if (t < total && src >= 0 && src < n) {
+                const int64_t o = (i0 + p) * w16 + w;
+                out_reads[o] = __ldg(reads + src * w16 + w);
+                out_refs[o] = __ldg(refs + src * w16 + w);
+            }
+        }
     }
 }
 
@@ -164,9 +182,11 @@ cudaError_t launch_gather_pairs(const uint32_t *reads, const uint32_t *refs,
     if (n <= 0)
         return cudaSuccess;
     const int w16 = (m + 15) / 16;
-    k_gather_pairs<<<sm_count * 8, 256, 0, st>>>(reads, refs, w16, index,
-                                                 count, out_reads, out_refs,
-                                                 n);
+    if (w16 == 0)
+        return cudaSuccess;
+    k_gather_pairs<<<sm_count * 8, 256, 0, st>>>(
+        reads, refs, w16, div_magic((uint32_t)w16), index, count, out_reads,
+        out_refs, n);
     return cudaGetLastError();
 }
 
