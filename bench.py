@@ -505,10 +505,21 @@ def run_two_lengths(F) -> dict:
         tp = _time_ms(plain, 5, F.sync)
         tb = _time_ms(persistent, 5, F.sync)
         same &= bool(torch.equal(a, a2) and torch.equal(o, o2))
+        # accuracy of these decisions against the banded edit distance
+        conf = [0, 0, 0, 0]
+        for (q, g), (m, e), sl in (((bufs[0]), (250, e250), slice(0, n3)),
+                                    ((bufs[1]), (150, e150),
+                                     slice(n3, 2 * n3))):
+            ed = F.edit_distance(q, g, m=m, e=e, n=n3)
+            for k, v in enumerate(F.confusion(a[sl], ed, e=e)):
+                conf[k] += v
+        ta, fa, fr, tr = conf
         rows.append({"E_pct": pct, "E": [e250, e150],
                      "plain_pairs_per_s": 2 * n3 / (tp * 1e-3),
                      "persistent_pairs_per_s": 2 * n3 / (tb * 1e-3),
-                     "plain_ms": tp, "persistent_ms": tb})
+                     "plain_ms": tp, "persistent_ms": tb,
+                     "false_accepts": fa, "false_rejects": fr,
+                     "false_accept_rate": fa / max(fa + tr, 1)})
     return {"workload": "10M x 250 bp + 10M x 150 bp, edit rate U[0,0.12], "
                         "E = 0..10 % of length",
             "per_E": rows, "results_identical": same}
