@@ -429,6 +429,21 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
         "results_identical": same,
         "accept_rate": float(acc.float().mean().item()),
     }
+    # accuracy of every decision against the warp-per-pair banded verifier
+    # (E <= 511 covers the whole batch), outside the timed region
+    a, b = _ev(), _ev()
+    a.record()
+    ed = F.edit_distance_varlen(pq, pr, dwo, dL, dE)
+    b.record()
+    F.sync()
+    close = ed <= dE
+    accd = acc.bool()
+    fa = int((accd & ~close).sum().item())
+    fr = int((~accd & close).sum().item())
+    tr = int((~accd & ~close).sum().item())
+    out["accuracy"] = {"false_accepts": fa, "false_rejects": fr,
+                       "false_accept_rate": fa / max(fa + tr, 1),
+                       "verifier_ms": a.elapsed_time(b)}
     t_hbm = bytes_alg / (hbm_gbs * 1e9)
     roof = {"t_hbm_ms": 1e3 * t_hbm, "algorithmic_bytes": bytes_alg}
     if want_cpu:

@@ -198,6 +198,18 @@ int ss_edit_distance_banded(ss_ctx *ctx, const void *reads, const void *refs,
 int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
                         const int32_t *ed, int64_t n, int32_t e,
                         void *stream, uint64_t *out_counts);
+/* ss_edit_distance_varlen: the same capped distance for pairs of per-pair
+ * length lengths[p] (both sequences) at word offset offsets[p] of `reads`
+ * and `refs` (SS_FMT_PACKED2, int64 word offsets, device arrays) and
+ * per-pair threshold E[p] <= 511; one warp per pair, the band spread over
+ * its lanes.  out_ed[p] = min(ED, E[p] + 1); a pair with E[p] > 511 gets -1
+ * and SS_ERR_UNSUPPORTED from the next ss_sync, a negative length or
+ * threshold -1 and SS_ERR_INVALID_ARG.  Asynchronous on `stream`.  Returns
+ * SS_OK, SS_ERR_INVALID_ARG or SS_ERR_CUDA. */
+int ss_edit_distance_varlen(ss_ctx *ctx, const void *reads, const void *refs,
+                            const int64_t *offsets, const int32_t *lengths,
+                            const int32_t *E, int64_t n, void *stream,
+                            int32_t *out_ed);
 
 /* ---- pairs of different lengths (Section 2.4) ------------------------------
  * Pair p: query (read) of read_len[p] bases at word read_off[p] of `reads`,

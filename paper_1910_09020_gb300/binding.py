@@ -40,6 +40,7 @@ EXPORTED = (
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
     "ss_filter_submaze", "ss_check_wait_timeout", "ss_filter_unequal",
+    "ss_edit_distance_varlen",
     "ss_server_create",
     "ss_server_submit", "ss_server_poll", "ss_server_wait", "ss_server_fetch",
     "ss_server_get_stats", "ss_server_reset_stats", "ss_server_destroy",
@@ -116,6 +117,7 @@ def load(build_if_needed: bool = True):
     lib.ss_filter_confusion.argtypes = [P, P, P, I64, I32, P, P]
     lib.ss_compact_accepted.argtypes = [P, P, I64, P, P, P]
     lib.ss_check_wait_timeout.argtypes = [P, I64, P]
+    lib.ss_edit_distance_varlen.argtypes = [P, P, P, P, P, P, I64, P, P]
     lib.ss_filter_unequal.argtypes = [P, P, P, P, P, P, P, P, I32, I64, P,
                                       P, P]
     lib.ss_filter_submaze.argtypes = [P, P, P, ctypes.c_int, I32, I32, I32,
@@ -436,6 +438,19 @@ class Filter:
                                     _ptr(out_q), _ptr(out_r))
         _check(rc, "ss_gather_pairs")
         return out_q, out_r
+
+    def edit_distance_varlen(self, reads, refs, offsets, lengths, E,
+                             stream=None):
+        """min(ED, E[p]+1) of packed pairs with per-pair word offsets,
+        lengths and thresholds (E <= 511); device int32[n]."""
+        import torch
+        n = lengths.shape[0]
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=lengths.device)
+        rc = load().ss_edit_distance_varlen(
+            self.ctx, _ptr(reads), _ptr(refs), _ptr(offsets), _ptr(lengths),
+            _ptr(E), n, _stream_handle(stream) or None, _ptr(out))
+        _check(rc, "ss_edit_distance_varlen")
+        return out[:n]
 
     def confusion(self, accept, ed, *, e: int, stream=None):
         """(true accepts, false accepts, false rejects, true rejects)."""

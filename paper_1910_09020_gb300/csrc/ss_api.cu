@@ -717,6 +717,26 @@ int ss_filter_confusion(ss_ctx *ctx, const uint8_t *accept,
     return SS_OK;
 }
 
+int ss_edit_distance_varlen(ss_ctx *ctx, const void *reads, const void *refs,
+                            const int64_t *offsets, const int32_t *lengths,
+                            const int32_t *E, int64_t n, void *stream,
+                            int32_t *out_ed)
+{
+    if (!ctx || n < 0)
+        return SS_ERR_INVALID_ARG;
+    if (n == 0)
+        return SS_OK;
+    if (!reads || !refs || !offsets || !lengths || !E || !out_ed)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SS_CUDA(ssk::launch_ed_var((const uint32_t *)reads,
+                               (const uint32_t *)refs, offsets, lengths, E,
+                               n, out_ed, ctx->d_status, ctx->sm_count,
+                               pick_stream(stream)));
+    ctx->counters.launches += 6;
+    return SS_OK;
+}
+
 int ss_filter_unequal(ss_ctx *ctx, const void *reads, const int64_t *read_off,
                       const int32_t *read_len, const void *refs,
                       const int64_t *ref_off, const int32_t *ref_len,

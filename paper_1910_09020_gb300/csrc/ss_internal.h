@@ -55,6 +55,12 @@ constexpr int kEdMaxE = 31;
 cudaError_t launch_ed_banded(int E, const uint32_t *reads,
                              const uint32_t *refs, int64_t n, int32_t m,
                              int32_t *ed, int sm_count, cudaStream_t st);
+// Warp per pair, any length, per-pair E <= kEdWarpMaxE.
+constexpr int kEdWarpMaxE = 511;
+cudaError_t launch_ed_var(const uint32_t *reads, const uint32_t *refs,
+                          const int64_t *off, const int32_t *len,
+                          const int32_t *E, int64_t n, int32_t *ed,
+                          int *status, int sm_count, cudaStream_t st);
 cudaError_t launch_confusion(const uint8_t *acc, const int32_t *ed,
                              int64_t n, int E, unsigned long long *counts,
                              int sm_count, cudaStream_t st);

@@ -97,4 +97,98 @@ SS_HD int ed_banded(const uint32_t *q, const uint32_t *r, int m, int w16)
     return D[E];  // j = i = m
 }
 
+// ---- large thresholds: one warp per pair -----------------------------------
+//
+// The same banded DP for E up to 511: the 2E+1 band cells of a row are
+// spread over the 32 lanes, C consecutive cells per lane, in registers.  The
+// in-row dependency D[i][j] = min(T[j], D[i][j-1] + 1), with T the best of
+// the diagonal and upper neighbours, is a prefix minimum: D[d] = d +
+// min_{d' <= d} (T[d'] - d'), computed per lane and then across the warp
+// with shuffles.  The reference bases of a lane's cells come from a 64-base
+// window of its bit planes, re-read every 32 rows.  Once every cell of a
+// row exceeds E, ED > E (every alignment passes through that row).
+template <int C>
+__device__ int ed_band_warp(const uint32_t *q, const uint32_t *r, int m,
+                            int E)
+{
+    const int lane = threadIdx.x & 31;
+    const int B = 2 * E + 1;
+    const int CAP = E + 1;
+    const int BIG = 1 << 30;
+    const int w16 = (m + 15) >> 4;
+    int P[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {  // row 0: D[0][j] = j
+        const int d = lane * C + c, j = d - E;
+        P[c] = (d < B && j >= 0 && j <= m) ? (j < CAP ? j : CAP) : CAP;
+    }
+    uint64_t wlo = 0, whi = 0;
+    int wstart = 0;
+    for (int i = 1; i <= m; ++i) {
+        const int b0 = i - E - 1 + lane * C;  // reference base of cell c = 0
+        if (((i - 1) & 31) == 0) {            // warp-uniform refill
+            wlo = plane_window(r, w16, m, b0, 0);
+            whi = plane_window(r, w16, m, b0, 1);
+            wstart = b0;
+        }
+        const int sh = b0 - wstart;           // 0..31
+        const uint32_t qw = ldg(q + ((i - 1) >> 4));
+        const uint64_t qlo = 0ull - (uint64_t)((qw >> ((i - 1) & 15)) & 1u);
+        const uint64_t qhi =
+            0ull - (uint64_t)((qw >> (16 + ((i - 1) & 15))) & 1u);
+        const uint64_t mm = ((wlo >> sh) ^ qlo) | ((whi >> sh) ^ qhi);
+        const int next0 = __shfl_down_sync(0xffffffffu, P[0], 1);
+        int PM[C];
+        int pm = BIG;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int d = lane * C + c, j = i + d - E;
+            int up = c + 1 < C ? P[c + 1] : (lane < 31 ? next0 : CAP);
+            if (d + 1 >= B)
+                up = CAP;
+            int t = P[c] + (int)((mm >> c) & 1ull);
+            t = t < up + 1 ? t : up + 1;
+            if (j == 0)
+                t = i;                        // D[i][0] = i
+            if (d >= B || j < 0 || j > m)
+                t = CAP;
+            const int u = t - d;
+            pm = pm < u ? pm : u;
+            PM[c] = pm;
+        }
+        // exclusive prefix minimum of the lanes' minima
+        int incl = pm;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off)
+                incl = incl < v ? incl : v;
+        }
+        int ex = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0)
+            ex = BIG;
+        int rowmin = CAP;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int d = lane * C + c, j = i + d - E;
+            int v = d + (ex < PM[c] ? ex : PM[c]);
+            v = v < CAP ? v : CAP;
+            if (d >= B || j < 0 || j > m)
+                v = CAP;
+            P[c] = v;
+            rowmin = rowmin < v ? rowmin : v;
+        }
+        if ((i & 7) == 0 &&
+            __reduce_min_sync(0xffffffffu, (unsigned)rowmin) >= (unsigned)CAP)
+            return CAP;
+    }
+    // cell d = E (j = i = m)
+    int out = CAP;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+        if (lane * C + c == E)
+            out = P[c];
+    return __shfl_sync(0xffffffffu, out, E / C);
+}
+
 }  // namespace ssk

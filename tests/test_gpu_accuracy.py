@@ -65,3 +65,65 @@ def test_no_false_rejects_full_size():
             assert ta + fa + fr + tr == n
             assert fr == 0, (E, fr)
             assert ta > 0 and tr > 0
+
+
+def _varlen_packed(F, seed, L, rate):
+    torch = torch_cuda()
+    reads, refs, off = synth.pairs_varlen(seed, 0, L, synth.rate_recipe(rate))
+    words = (L.astype(np.int64) + 15) // 16
+    woff = np.zeros(len(L) + 1, np.int64)
+    np.cumsum(words, out=woff[1:])
+    outs = []
+    for a in (reads, refs):
+        o = torch.zeros(int(woff[-1]) + 4, dtype=torch.int32, device="cuda")
+        F.pack(to_dev(a), offsets=to_dev(off[:-1]), lengths=to_dev(L),
+               out=o, out_offsets=to_dev(woff[:-1]))
+        outs.append(o)
+    return reads, refs, off, outs[0], outs[1], woff
+
+
+def test_warp_verifier_matches_oracle(F):
+    """The warp-per-pair verifier (E up to 511, every band width class)
+    against the oracle's Levenshtein DP, per-pair lengths and thresholds."""
+    rng = np.random.default_rng(41)
+    n = 600
+    L = synth.log_uniform(41, 0, n, 1, 1500)
+    E = np.minimum(rng.integers(0, 512, n),
+                   np.maximum(L // 3, rng.integers(0, 40, n))).astype(np.int32)
+    E[:6] = [0, 31, 32, 63, 64, 511]
+    for rate in (0.03, 0.2):
+        reads, refs, off, q, r, woff = _varlen_packed(F, 41, L, rate)
+        got = F.edit_distance_varlen(q, r, to_dev(woff[:-1]), to_dev(L),
+                                     to_dev(E))
+        F.sync()
+        got = got.cpu().numpy()
+        for p in range(n):
+            a = reads[off[p]:off[p + 1]].tobytes()
+            b = refs[off[p]:off[p + 1]].tobytes()
+            want = min(oracle.edit_distance(a, b), int(E[p]) + 1)
+            assert got[p] == want, (p, int(L[p]), int(E[p]), got[p], want)
+
+
+def test_warp_verifier_long_pairs(F):
+    L = np.array([2000, 5000, 3333], np.int32)
+    E = np.array([100, 250, 511], np.int32)
+    reads, refs, off, q, r, woff = _varlen_packed(F, 43, L, 0.04)
+    got = F.edit_distance_varlen(q, r, to_dev(woff[:-1]), to_dev(L),
+                                 to_dev(E)).cpu().numpy()
+    F.sync()
+    for p in range(3):
+        a = reads[off[p]:off[p + 1]].tobytes()
+        b = refs[off[p]:off[p + 1]].tobytes()
+        assert got[p] == min(oracle.edit_distance(a, b), int(E[p]) + 1)
+
+
+def test_warp_verifier_rejects_out_of_range(F):
+    L = np.array([100, 100, 100], np.int32)
+    reads, refs, off, q, r, woff = _varlen_packed(F, 44, L, 0.1)
+    got = F.edit_distance_varlen(q, r, to_dev(woff[:-1]), to_dev(L),
+                                 to_dev(np.array([5, 512, 3], np.int32)))
+    with pytest.raises(binding.SSError) as ei:
+        F.sync()
+    assert ei.value.code == binding.SS_ERR_UNSUPPORTED
+    g = got.cpu().numpy()
+    assert g[1] == -1 and g[0] >= 0 and g[2] >= 0
