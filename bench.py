@@ -676,7 +676,7 @@ def run_compaction(F, pq, pr, acc, n, E) -> dict:
     return out
 
 
-def run_serving(seconds: float) -> dict:
+def run_serving(seconds: float, slots: int = 2) -> dict:
     """Requests of 1..4096 pairs (log-uniform), lengths log-uniform
     100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
     Poisson process at 30 %, 60 % and 90 % of the measured capacity."""
@@ -698,7 +698,6 @@ def run_serving(seconds: float) -> dict:
             t.numpy()[:len(a)] = a
             pinned.append(t.numpy()[:len(a)])
         pool.append((pinned[0], pinned[1], L, E))
-    slots = 2
     out = {"workload": "requests of 1..4096 pairs (log-uniform), lengths "
                        "log-uniform 100..100000 bp, edit rate U[0,0.15], "
                        "E = 10 % of length, Poisson arrivals",
@@ -736,12 +735,13 @@ def run_serving(seconds: float) -> dict:
                 if delay > 0:
                     time.sleep(delay)
                 tickets.append(S.submit(*pool[pick[k]]))
+            # fetch each result as soon as it is done: results hold device
+            # memory (within the server's budget) until they are fetched
             for t in tickets:
                 S.wait(t)
+                S.fetch(t)
             span = time.perf_counter() - t0
             st = S.stats()
-            for t in tickets:
-                S.fetch(t)
             npairs = int(sum(len(pool[i][2]) for i in pick))
             loads.append({"offered_load": frac,
                           "offered_requests_per_s": rate,

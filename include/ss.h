@@ -309,7 +309,11 @@ int ss_filter_batch_noalloc(const void *reads, const void *refs,
  * them to the device, packs them and runs the bucketed filter with its
  * persistent grids sized to 1/slots of the SMs, so batches admitted while
  * others run execute beside them.  Results stay in device memory until
- * fetched.  A request whose bases are not all A/C/G/T fails alone
+ * fetched, and a batch's device memory counts against the budget until all
+ * of its requests are fetched: a client that waits for later requests
+ * before fetching earlier ones can fill the budget and stall admission, so
+ * fetch each result once it is done.  A request whose bases are not all
+ * A/C/G/T fails alone
  * (SS_ERR_INVALID_BASE; its bad pairs get obstacles = -1).
  *   ss_server_create   device, budget (0 = 8 GiB), slots 1..16.
  *   ss_server_submit   1 <= n <= 2^20; the host buffers must stay valid and

@@ -353,10 +353,22 @@ void scheduler(ss_server *s)
         }
         if (any_done)
             s->cv_done.notify_all();
-        // admission: fill free slots first-in first-out within the budget
+        // admission: fill free slots first-in first-out within the budget;
+        // a backlog is shared out over all free slots (by pairs), so a
+        // burst runs on every slot instead of queueing as one batch
+        int free_slots = 0;
+        for (const Slot &sl : s->slots)
+            free_slots += sl.running ? 0 : 1;
+        int64_t backlog = 0;
+        if (free_slots > 1)
+            for (const Request *r : s->pending)
+                backlog += r->n;
         for (int k = 0; k < s->nslots && !s->pending.empty(); ++k) {
             if (s->slots[k].running)
                 continue;
+            const int64_t share =
+                free_slots > 1 ? (backlog + free_slots - 1) / free_slots
+                               : s->max_batch_pairs;
             std::vector<Request *> take;
             size_t need = 0;
             int64_t pairs = 0;
@@ -364,7 +376,8 @@ void scheduler(ss_server *s)
                 Request *r = s->pending.front();
                 const bool first = take.empty();
                 if (!first && (s->in_use + need + r->footprint > s->budget ||
-                               pairs + r->n > s->max_batch_pairs))
+                               pairs + r->n > s->max_batch_pairs ||
+                               pairs >= share))
                     break;
                 if (first && s->in_use + r->footprint > s->budget)
                     break;  // wait for memory to free up
@@ -375,6 +388,8 @@ void scheduler(ss_server *s)
             }
             if (take.empty())
                 break;
+            backlog -= pairs;
+            free_slots -= 1;
             const int rc = launch_batch(s, k, take);
             if (rc != SS_OK) {
                 for (Request *r : take) {

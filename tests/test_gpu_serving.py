@@ -138,3 +138,30 @@ def test_admission_by_budget():
             rc, a, o, _ = S.fetch(t)
             oa, oo = oracle_of(r)
             assert (a == oa).all() and (o == oo).all()
+
+
+def test_unfetched_results_hold_the_budget():
+    """Results keep their device memory until fetched: with a budget that
+    fits one request, the second waits for the first to be fetched, then
+    runs (and matches the oracle)."""
+    L = np.full(1000, 1000, np.int32)
+    E = synth.thresholds(L, 5)
+    reqs = []
+    for i in range(2):
+        reads, refs, off = synth.pairs_varlen(900 + i, 0, L,
+                                              synth.rate_recipe(0.05))
+        reqs.append((reads, refs, L, E, off))
+    with binding.Server(0, hbm_budget_bytes=4 << 20, slots=2) as S:
+        t1 = S.submit(*reqs[0][:4])
+        t2 = S.submit(*reqs[1][:4])
+        assert S.wait(t1, timeout_s=60.0) == binding.SS_OK
+        assert S.wait(t2, timeout_s=0.5) == binding.SS_ERR_TIMEOUT
+        assert S.stats()["pending"] == 1
+        rc, a1, o1, _ = S.fetch(t1)
+        assert rc == binding.SS_OK
+        assert S.wait(t2, timeout_s=60.0) == binding.SS_OK
+        rc, a2, o2, _ = S.fetch(t2)
+        assert rc == binding.SS_OK
+    for req, a, o in ((reqs[0], a1, o1), (reqs[1], a2, o2)):
+        oa, oo = oracle_of(req)
+        assert (a == oa).all() and (o == oo).all()
