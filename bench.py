@@ -180,7 +180,7 @@ def measured_peaks() -> dict:
 # the source files each profiled kernel is compiled from: a change to any of
 # them makes its committed DRAM-traffic figure stale
 KERNEL_SOURCES = {
-    "k_rw_uniform": ["ss_device.cuh", "ss_internal.h", "ss_rw.cuh",
+    "k_rw_uniform": ["ss_device.cuh", "ss_rw_config.h", "ss_rw.cuh",
                      "ss_rw_launch.cuh", "ss_rw_e0.cu", "ss_rw_e1.cu",
                      "ss_rw_e2.cu", "ss_rw_e3.cu"],
     "k_pack_fixed": ["ss_device.cuh", "ss_pack.cuh", "ss_pack.cu"],
@@ -873,6 +873,8 @@ def run_ours(args):
 
     if rank != 0:
         F.close()
+        import torch.distributed as dist
+        dist.destroy_process_group()
         return 0
 
     # roofline of the dominant kernel: the filter launches of the sweep

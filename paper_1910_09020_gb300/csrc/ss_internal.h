@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <utility>
 
+#include "ss_rw_config.h"
+
 namespace ssk {
 
 struct RwUniformArgs;
@@ -11,11 +13,6 @@ struct RwLaunch;
 struct PairSet;
 struct BucketWs;
 struct TuneParams;
-
-// Largest E and m served by the thread-per-pair row-wise kernel (K3a).
-constexpr int kRwMaxE = 31;
-constexpr int kRwMaxM = 1024;
-constexpr int kRwThreads = 128;
 
 cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,
                               uint32_t *out, int *status, cudaStream_t st);

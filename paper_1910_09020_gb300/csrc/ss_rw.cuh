@@ -42,7 +42,7 @@
 #include <type_traits>
 
 #include "ss_device.cuh"
-#include "ss_internal.h"
+#include "ss_rw_config.h"
 
 namespace ssk {
 
