@@ -181,3 +181,20 @@ def test_unequal_lengths_match_oracle(emu):
                 continue
             want = oracle.filter_unequal(Q, R, E).obstacles
             assert got == want, (mq, mr, E, got, want)
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_cw_long_reads_match_oracle(emu, K):
+    """Column-wise routine on long reads at E = 10 % of the length: edge
+    and interior row words, survivors past K columns (low edit rates) and
+    both blocks of the 16-column phase."""
+    rng = np.random.default_rng(40 + K)
+    for i in range(6):
+        m = int(rng.integers(3000, 8000))
+        E = m // 10
+        rec = synth.rate_recipe(float(rng.choice([0.003, 0.02, 0.08, 0.15])))
+        Q, R = pairs(1500 + i, 1, m, rec)[0]
+        q, r = packed(Q), packed(R)
+        got = emu.emu_cw(P(q), P(r), m, E, K)
+        want = oracle.filter_pair(Q, R, E).obstacles
+        assert got == want, (m, E, K)
