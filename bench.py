@@ -69,8 +69,9 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the batched and served forms")
     ap.add_argument("--workload", default="all",
-                    choices=["all", "batched"],
-                    help="batched: only the persistent launch of the uneven "
+                    choices=["all", "batched", "long"],
+                    help="long: only the CTA-per-pair class (profiling); "
+                         "batched: only the persistent launch of the uneven "
                          "batch (for profiling)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window of each offered load")
@@ -1006,12 +1007,47 @@ def run_batched_only(args):
     return 0
 
 
+def run_long_only(args):
+    """The CTA-per-pair class alone (profiling aid): 608 pairs of 20 kbp,
+    edit rate 5 %, E = 10 % of the length (2000; 126 row words per pair,
+    four CTAs per SM), the shape of the served form's long pairs.  Two
+    filter passes without graph replay, so that a profiler sees every
+    launch; the busy k_cw_cta launch is the fifth of that kernel."""
+    import torch
+
+    from paper_1910_09020_gb300 import binding, synth
+    torch.cuda.set_device(0)
+    F = binding.Filter(0, workspace_bytes=1 << 30)
+    F.set_tuning(31, 8)
+    n, m = 608, 20000
+    L = np.full(n, m, np.int32)
+    E = synth.thresholds(L, 10)
+    pq, pr, dwo, dL, _, _ = _pack_varlen(F, L, synth.rate_recipe(0.05), 5)
+    dE = torch.from_numpy(E).cuda()
+    times = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        acc, obs = F.filter(pq, pr, offsets=dwo, lengths=dL, E=dE, sync=True,
+                            flags=binding.SS_FLAG_NO_GRAPH)
+        times.append(time.perf_counter() - t0)
+    o = obs.cpu().numpy()
+    print(json.dumps({"workload": f"{n} pairs x {m} bp, E = {int(E[0])}, "
+                                  "edit rate 5 %, CTA-per-pair class",
+                      "ms": [round(1e3 * t, 3) for t in times],
+                      "greedy_iterations": int(o.sum()),
+                      "accepted": int(acc.sum().item())}), flush=True)
+    F.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched_only(args)
+    if args.workload == "long":
+        return run_long_only(args)
     return run_ours(args)
 
 
