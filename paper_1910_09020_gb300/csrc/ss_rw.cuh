@@ -11,14 +11,15 @@
 // GB300 mapping: each thread holds, for the 32-column word k it is routing
 // through, the maze row words Z_s (one register each, built with one funnel
 // shift per bit plane and two logic ops: the maze is built lazily word by
-// word, as in the implicit maze of Section 2.4).  The longest run from
-// checkpoint c needs no per-row bit scan: with x_s = Z_s masked to columns
-// >= c, x_s | -x_s sets every bit at or above row s's first obstacle, so the
-// AND over rows has its lowest set bit at max_s(first obstacle) -- the end of
-// the longest escape segment -- found with one find-first per iteration.
-// When a run crosses into the next word, the rows that already met an
-// obstacle since c are kept in a bitmask and count as all-obstacle rows
-// until the next obstacle is found, so runs spanning words are exact.
+// word, as in the implicit maze of Section 2.4).  The longest run from the
+// checkpoint needs no per-row bit scan: per row, one or two integer ops
+// turn the row word into a mask whose AND (or OR) over rows has its lowest
+// (highest) set bit at the farthest first obstacle -- the end of the
+// longest escape segment -- found with one find-first per iteration
+// (rw_word_smear and rw_word_borrow below).  When a run crosses into the
+// next word, the rows that already met an obstacle since the checkpoint
+// are kept in a bitmask and count as blocked until the next obstacle is
+// found, so runs spanning words are exact.
 //
 // Three launch forms share rw_route():
 //  * k_rw_uniform<E>: the plain launch (uniform m and E, m <= 256).  Each
@@ -87,10 +88,188 @@ struct GlobalSeq {
     }
 };
 
+// Index of the highest set bit of x (x != 0).
+SS_HD int flo32(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return 31 - __clz((int)x);
+#else
+    return 31 - __builtin_clz(x);
+#endif
+}
+
+// Greedy routing inside one 32-column word (Section 2.4 steps 2-4) on its
+// maze row words Z (row r = diagonal r - EMAX), entered with the
+// checkpoint at or before the word start.  deadbits: rows that met an
+// obstacle since that checkpoint (runs continued from the previous word);
+// on return it holds them for the next word, or 0.  count and finished
+// advance as the greedy does.  Two forms, equal results:
+//
+// Smear-AND (E <= 4): with x_s = Z_s masked to columns >= c, x_s | -x_s
+// sets every bit at or above row s's first obstacle, so the AND over rows
+// has its lowest set bit at max_s(first obstacle): three operations per
+// row and iteration, a find-first per iteration.
+template <int NR, class RowBits>
+SS_HD void rw_word_smear(const uint32_t (&Z)[NR], RowBits &deadbits,
+                         int base, int m, int E, int &count, bool &finished,
+                         uint32_t neg1)
+{
+    uint32_t M = 0xffffffffu;  // columns >= checkpoint
+    for (;;) {
+        uint32_t A = 0xffffffffu;
+        if (deadbits) {
+            // runs continued from the previous word: rows that already
+            // met an obstacle since the checkpoint do not count
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t x =
+                    (Z[r] & M) |
+                    (0u - (uint32_t)((deadbits >> r) & (RowBits)1));
+                A &= x | (x * neg1);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t x = Z[r] & M;
+                A &= x | (x * neg1);
+            }
+        }
+        if (A == 0u) {
+            // a live row runs past the word end: remember the others
+            RowBits d = deadbits;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                d |= (RowBits)((Z[r] & M) != 0u) << r;
+            deadbits = d;
+            return;
+        }
+        deadbits = 0;  // an obstacle ends every run: fresh checkpoint
+        const int e = base + ffs32(A) - 1;  // end of the escape segment
+        if (e >= m) {                       // reached the destination
+            finished = true;
+            return;
+        }
+        ++count;                            // its obstacle
+        if (count > E) {                    // delay exceeds E: reject
+            finished = true;
+            return;
+        }
+        const int c = e + 1;                // new checkpoint
+        if (c >= base + 32)
+            return;
+        M = 0xffffffffu << (c - base);
+    }
+}
+
+// Row flags stacked by funnel shifts (row 0 arrived first, so it sits
+// highest: rows 0..31 at bits min(NR,32)-1-r of lo, rows 32.. at bits
+// NR-1-r of hi) -> a mask with bit r for row r.
+template <class RowBits, int NR>
+SS_HD RowBits rev_rows(uint32_t lo, uint32_t hi)
+{
+    constexpr int NLO = NR < 32 ? NR : 32;
+#ifdef __CUDA_ARCH__
+    RowBits out = (RowBits)(__brev(lo) >> (32 - NLO));
+    if constexpr (NR > 32)
+        out |= (RowBits)(__brev(hi) >> (64 - NR)) << 32;
+#else
+    RowBits out = 0;
+    for (int r = 0; r < NLO; ++r)
+        out |= (RowBits)((lo >> (NLO - 1 - r)) & 1u) << r;
+    if constexpr (NR > 32)
+        for (int r = 32; r < NR; ++r)
+            out |= (RowBits)((hi >> (NR - 1 - r)) & 1u) << r;
+#endif
+    return out;
+}
+
+// Borrow (E >= 5): Z_s - 2^cl borrows through the row's zeros from the
+// checkpoint bit cl up to its first obstacle p_s, so Z_s ^ (Z_s - 2^cl)
+// sets exactly bits cl..p_s, and the OR over rows has its highest set bit
+// at max_s p_s: two operations per row and iteration -- the subtraction a
+// multiply-add on the FMA pipe, the logic op on the ALU pipe -- and a
+// find-leading-one per iteration.  A row with no obstacle up to bit 31
+// borrows out and sets bits cl..31, like an obstacle at bit 31, so bit 31
+// of the OR sends the iteration to an exact per-row test.  The fixed cost
+// per iteration is higher than the smear-AND form's, which stays faster
+// up to nine rows.
+template <int NR, class RowBits>
+SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
+                          int base, int m, int E, int &count,
+                          bool &finished, uint32_t neg1)
+{
+    constexpr RowBits kAllRows = (RowBits)(((RowBits)1 << NR) - 1);
+    int cl = 0;  // checkpoint bit
+    for (;;) {
+        const uint32_t npc = (1u << cl) * neg1;  // -2^cl
+        // 1, re-derived every iteration: a multiplier the compiler can
+        // neither fold nor hoist, so z * one_i + npc stays one multiply-add
+        // per row (a hoisted z * 1 would cost a register per row and turn
+        // the subtraction into an ALU add)
+        const uint32_t one_i = (npc * neg1) >> cl;
+        uint32_t B = 0;
+        if (deadbits) {
+            // runs continued from the previous word (cl = 0): rows that
+            // already met an obstacle since the checkpoint read as blocked
+            // at bit 0
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t z =
+                    Z[r] | (uint32_t)((deadbits >> r) & (RowBits)1);
+                B |= z ^ (z * one_i + npc);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                B |= Z[r] ^ (Z[r] * one_i + npc);
+        }
+        int e;  // end of the escape segment
+        if (B >> 31) {
+            // a run reaches bit 31.  Row r met an obstacle in bits cl..31
+            // iff Z - 2^cl did not borrow out, i.e. iff bit 31 of
+            // ~(Z - 2^cl) | Z is set; funnel shifts stack those bits.
+            uint32_t d_lo = 0u, d_hi = 0u;  // rows 0..31, rows 32..
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t y = ~(Z[r] * one_i + npc) | Z[r];
+                if (r < 32)
+                    d_lo = funnel_l(y, d_lo, 1);
+                else
+                    d_hi = funnel_l(y, d_hi, 1);
+            }
+            const RowBits d = deadbits | rev_rows<RowBits, NR>(d_lo, d_hi);
+            if (d != kAllRows) {
+                deadbits = d;  // a live row runs past the word end
+                return;
+            }
+            e = base + 31;  // every run ends by bit 31, one exactly there
+        } else {
+            e = base + flo32(B);
+        }
+        deadbits = 0;  // an obstacle ends every run: fresh checkpoint
+        if (e >= m) {  // reached the destination
+            finished = true;
+            return;
+        }
+        ++count;          // its obstacle
+        if (count > E) {  // delay exceeds E: reject
+            finished = true;
+            return;
+        }
+        const int c = e + 1;  // new checkpoint
+        if (c >= base + 32)
+            return;
+        cl = c - base;
+    }
+}
+
+constexpr int kRwBorrowMinE = 5;  // rw_word_borrow from E' = 5 (11 rows)
+
 // Route one pair of length m with threshold E (E == EMAX when EXACT);
 // returns min(count, E+1).  Rows |s| > min(E, EMAX) are never built.
-// neg1 must hold 0xffffffff: negation is done as a multiply by it, which
-// issues on the FMA pipe and leaves the busier ALU pipe to the logic ops.
+// neg1 must hold 0xffffffff: the subtractions are multiply-adds by values
+// derived from it at run time, which issue on the FMA pipe and leave the
+// busier ALU pipe to the logic ops.
 template <int EMAX, bool EXACT, class Seq>
 SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
 {
@@ -145,51 +324,11 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
             Z[r] = z;
         }
         // Greedy routing inside word k (checkpoint c <= base on entry).
-        uint32_t M = 0xffffffffu;  // columns >= checkpoint
-        for (;;) {
-            uint32_t A = 0xffffffffu;
-            if (deadbits) {
-                // runs continued from the previous word: rows that already
-                // met an obstacle since the checkpoint do not count
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t x =
-                        (Z[r] & M) |
-                        (0u - (uint32_t)((deadbits >> r) & (RowBits)1));
-                    A &= x | (x * neg1);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t x = Z[r] & M;
-                    A &= x | (x * neg1);
-                }
-            }
-            if (A == 0u) {
-                // a live row runs past the word end: remember the others
-                RowBits d = deadbits;
-#pragma unroll
-                for (int r = 0; r < NR; ++r)
-                    d |= (RowBits)((Z[r] & M) != 0u) << r;
-                deadbits = d;
-                break;
-            }
-            deadbits = 0;  // an obstacle ends every run: fresh checkpoint
-            const int e = base + ffs32(A) - 1;  // end of the escape segment
-            if (e >= m) {                       // reached the destination
-                finished = true;
-                break;
-            }
-            ++count;                            // its obstacle
-            if (count > E) {                    // delay exceeds E: reject
-                finished = true;
-                break;
-            }
-            const int c = e + 1;                // new checkpoint
-            if (c >= base + 32)
-                break;
-            M = 0xffffffffu << (c - base);
-        }
+        if constexpr (EMAX >= kRwBorrowMinE)
+            rw_word_borrow<NR>(Z, deadbits, base, m, E, count, finished,
+                               neg1);
+        else
+            rw_word_smear<NR>(Z, deadbits, base, m, E, count, finished, neg1);
         // slide the Q window by one word
         qlo_p = qlo_c;
         qhi_p = qhi_c;
