@@ -105,10 +105,11 @@ SS_HD int flo32(uint32_t x)
 // on return it holds them for the next word, or 0.  count and finished
 // advance as the greedy does.  Two forms, equal results:
 //
-// Smear-AND (E <= 4): with x_s = Z_s masked to columns >= c, x_s | -x_s
-// sets every bit at or above row s's first obstacle, so the AND over rows
-// has its lowest set bit at max_s(first obstacle): three operations per
-// row and iteration, a find-first per iteration.
+// Smear-AND (plain kernel E <= 4, bucketed kernel): with x_s = Z_s masked to
+// columns >= c, x_s | -x_s sets every bit at or above row s's first
+// obstacle, so the AND over rows has its lowest set bit at max_s(first
+// obstacle): three operations per row and iteration, a find-first per
+// iteration.
 template <int NR, class RowBits>
 SS_HD void rw_word_smear(const uint32_t (&Z)[NR], RowBits &deadbits,
                          int base, int m, int E, int &count, bool &finished,
@@ -183,16 +184,16 @@ SS_HD RowBits rev_rows(uint32_t lo, uint32_t hi)
     return out;
 }
 
-// Borrow (E >= 5): Z_s - 2^cl borrows through the row's zeros from the
-// checkpoint bit cl up to its first obstacle p_s, so Z_s ^ (Z_s - 2^cl)
-// sets exactly bits cl..p_s, and the OR over rows has its highest set bit
-// at max_s p_s: two operations per row and iteration -- the subtraction a
-// multiply-add on the FMA pipe, the logic op on the ALU pipe -- and a
+// Borrow (plain kernel E >= 5): Z_s - 2^cl borrows through the row's zeros
+// from the checkpoint bit cl up to its first obstacle p_s, so Z_s ^ (Z_s -
+// 2^cl) sets exactly bits cl..p_s, and the OR over rows has its highest set
+// bit at max_s p_s: two operations per row and iteration -- the subtraction
+// a multiply-add on the FMA pipe, the logic op on the ALU pipe -- and a
 // find-leading-one per iteration.  A row with no obstacle up to bit 31
-// borrows out and sets bits cl..31, like an obstacle at bit 31, so bit 31
-// of the OR sends the iteration to an exact per-row test.  The fixed cost
-// per iteration is higher than the smear-AND form's, which stays faster
-// up to nine rows.
+// borrows out and sets bits cl..31, like an obstacle at bit 31, so bit 31 of
+// the OR sends the iteration to an exact per-row test.  The fixed cost per
+// iteration is higher than the smear-AND form's, which stays faster up to
+// nine rows.
 template <int NR, class RowBits>
 SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
                           int base, int m, int E, int &count,
@@ -263,7 +264,11 @@ SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
     }
 }
 
-constexpr int kRwBorrowMinE = 5;  // rw_word_borrow from E' = 5 (11 rows)
+// rw_word_borrow for the plain kernel's thresholds E >= 5 (11 rows or
+// more).  The bucketed kernel (E at run time, 2 EMAX + 1 rows) keeps the
+// smear-AND form: with the borrow form its two-length batches at E of
+// 7-10 % of the length ran 2 % slower.
+constexpr int kRwBorrowMinE = 5;
 
 // Route one pair of length m with threshold E (E == EMAX when EXACT);
 // returns min(count, E+1).  Rows |s| > min(E, EMAX) are never built.
@@ -324,7 +329,7 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
             Z[r] = z;
         }
         // Greedy routing inside word k (checkpoint c <= base on entry).
-        if constexpr (EMAX >= kRwBorrowMinE)
+        if constexpr (EXACT && EMAX >= kRwBorrowMinE)
             rw_word_borrow<NR>(Z, deadbits, base, m, E, count, finished,
                                neg1);
         else
