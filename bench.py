@@ -49,10 +49,17 @@ METRIC = "sequence pairs/sec (and Gbases/s) per GB300 vs roofline"
 FILTER_BYTES_PER_PAIR = 2 * ((M + 3) // 4) + 1 + 4
 # pack: both sequences read as ASCII, written at 2 bits per base
 PACK_BYTES_PER_PAIR = 2 * M + 2 * ((M + 3) // 4)
-# op model of the method per the lazy maze of Section 2.4: per evaluated
-# 32-column row word 7 logic/shift ops + 1 find-first; per iteration one
-# max per row plus 4 bookkeeping ops
+# op model of the method per the lazy maze of Section 2.4, in two
+# formulations of the same greedy; the roofline takes the cheaper one for
+# each threshold (the method's work is what its cheapest evaluation needs):
+# * row words: per evaluated 32-column row word 7 logic/shift ops + 1
+#   find-first; per iteration one max per row plus 4 bookkeeping ops;
+# * columns: per column walked, ceil((2E+1)/32) words holding its 2E+1
+#   rows, each 7 ops (2 funnel shifts of the query planes, 2 XORs with the
+#   broadcast reference base, 1 OR, 1 AND into the surviving rows, 1 for
+#   the broadcast); per iteration 4 bookkeeping ops; no find-first.
 K_WORD, K_RED, K_ITER = 7, 1, 4
+K_COL = 7
 
 
 def parse():
@@ -182,8 +189,8 @@ def measured_peaks() -> dict:
 # them makes its committed DRAM-traffic figure stale
 KERNEL_SOURCES = {
     "k_rw_uniform": ["ss_device.cuh", "ss_rw_config.h", "ss_rw.cuh",
-                     "ss_rw_launch.cuh", "ss_rw_e0.cu", "ss_rw_e1.cu",
-                     "ss_rw_e2.cu", "ss_rw_e3.cu"],
+                     "ss_rwc.cuh", "ss_rw_launch.cuh", "ss_rw_e0.cu",
+                     "ss_rw_e1.cu", "ss_rw_e2.cu", "ss_rw_e3.cu"],
     "k_pack_fixed": ["ss_device.cuh", "ss_pack.cuh", "ss_pack.cu"],
 }
 
@@ -218,7 +225,7 @@ def oracle_sample(n: int, first: int = 0):
 
 def time_oracle(reads, refs, threads: int = 0):
     """Oracle over every threshold of the sweep; returns (seconds, per-E
-    stats (cells, words, iterations) summed over pairs)."""
+    stats (cells, words, iterations, columns) summed over pairs)."""
     import oracle
     stats = {}
     t0 = time.perf_counter()
@@ -246,13 +253,27 @@ def cpu_baseline(target_s: float):
     }, stats, n
 
 
+def model_ops(E: int, words, iters, cols):
+    """ALU and find-first ops of the cheaper formulation (see K_COL), and
+    which one it is."""
+    rows = words * K_WORD + iters * (2 * E + 1) * K_RED + iters * K_ITER
+    by_col = cols * ((2 * E + 1 + 31) // 32) * K_COL + iters * K_ITER
+    if by_col < rows:
+        return by_col, 0, "columns"
+    return rows, words, "row words"
+
+
 def op_model(stats: dict, n: int) -> dict:
     """Per-pair algorithmic ALU and find-first ops of each threshold."""
     out = {}
-    for E, (cells, words, iters) in stats.items():
-        alu = (words * K_WORD + iters * (2 * E + 1) * K_RED + iters * K_ITER)
-        out[E] = {"alu_ops_per_pair": alu / n, "xu_ops_per_pair": words / n,
+    for E, (cells, words, iters, cols) in stats.items():
+        alu, xu, form = model_ops(E, words, iters, cols)
+        out[E] = {"alu_ops_per_pair": alu / n, "xu_ops_per_pair": xu / n,
+                  "model": form,
+                  "alu_ops_row_words_per_pair":
+                      model_ops(E, words, iters, 10**18)[0] / n,
                   "iterations_per_pair": iters / n,
+                  "columns_per_pair": cols / n,
                   "cells_per_pair": cells / n}
     return out
 
@@ -366,10 +387,12 @@ def _oracle_model(host, L, E, idx):
         so = np.zeros(len(sel) + 1, np.int64)
         np.cumsum(L[sel], out=so[1:])
         t0 = time.perf_counter()
-        _, _, (c, w, it) = oracle.filter_batch(sub_r, sub_f, L[sel],
-                                               E[sel], offsets=so,
-                                               with_stats=True)
+        _, _, (c, w, it, _) = oracle.filter_batch(sub_r, sub_f, L[sel],
+                                                  E[sel], offsets=so,
+                                                  with_stats=True)
         t += time.perf_counter() - t0
+        # the row-word formulation: the warp and CTA kernels evaluate 32
+        # rows per word op and stop each word early, below either model
         alu += w * K_WORD + it * (2 * int(e) + 1) * K_RED + it * K_ITER
         xu += w
         cells += c
@@ -900,7 +923,11 @@ def run_ours(args):
             t_alu = n * model[E]["alu_ops_per_pair"] / ipk["lop3"]
             t_xu = n * model[E]["xu_ops_per_pair"] / ipk["bfind"]
             d.update({"t_alu_ms": 1e3 * t_alu, "t_xu_ms": 1e3 * t_xu,
+                      "model": model[E]["model"],
                       "alu_ops_per_pair": model[E]["alu_ops_per_pair"],
+                      "alu_ops_row_words_per_pair":
+                          model[E]["alu_ops_row_words_per_pair"],
+                      "columns_per_pair": model[E]["columns_per_pair"],
                       "tops": n * model[E]["alu_ops_per_pair"] / (ms * 1e-3)
                       / 1e12})
             if max(t_alu, t_xu) > t_bound:
@@ -928,7 +955,9 @@ def run_ours(args):
         "bound": dom_bound, "achieved": achieved, "peak": peak, "unit": unit,
         "frac": roof_total / meas_total,
         "frac_note": "sum over the sweep of max(HBM, ALU, find-first) "
-                     "roofline time / measured time",
+                     "roofline time / measured time; the ALU term counts "
+                     "the cheaper of the row-word and column formulations "
+                     "of the greedy for each E (per_launch[].model)",
         "traffic": None if traffic is None else traffic * n,
         "algorithmic_bytes_per_launch": n * FILTER_BYTES_PER_PAIR,
         "peak_source": f"HBM {peaks['hbm_source']} ({peaks['hbm_gbs']} GB/s); "

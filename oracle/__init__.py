@@ -49,7 +49,7 @@ ERR_INVALID_BASE = -2
 
 class Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("words", ctypes.c_int64),
-                ("iterations", ctypes.c_int64)]
+                ("iterations", ctypes.c_int64), ("columns", ctypes.c_int64)]
 
 
 class Result(NamedTuple):
@@ -152,7 +152,7 @@ class Oracle:
             raise ValueError(f"oracle filter error {rc}")
         res = Result(bool(acc.value), int(obs.value))
         if with_stats:
-            return res, (st.cells, st.words, st.iterations)
+            return res, (st.cells, st.words, st.iterations, st.columns)
         return res
 
     def filter_submaze(self, Q, R, E: int, t: int, y: int) -> Result:
@@ -248,7 +248,8 @@ class Oracle:
             raise ValueError(f"oracle batch error {rc}")
         acc, obs = acc[:n], obs[:n]
         if with_stats:
-            return acc, obs, (st.cells, st.words, st.iterations)
+            return acc, obs, (st.cells, st.words, st.iterations,
+                              st.columns)
         return acc, obs
 
     def batch_status(self, reads, refs, m: int, E: int) -> int:

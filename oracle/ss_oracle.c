@@ -114,7 +114,7 @@ int sso_filter(const uint8_t *Q, const uint8_t *R, int64_t m, int64_t E,
     if (!valid_sequence(Q, m) || !valid_sequence(R, m))
         return SSO_ERR_INVALID_BASE;
 
-    sso_stats st = {0, 0, 0};
+    sso_stats st = {0, 0, 0, 0};
     /* Step (1): the maze is implicit; the first column is the first
      * checkpoint. */
     int64_t checkpoint = 1;
@@ -135,8 +135,11 @@ int sso_filter(const uint8_t *Q, const uint8_t *R, int64_t m, int64_t E,
         }
         /* The segment reaches the end of the row: the signal net has reached
          * the destination terminal, no obstacle follows it. */
-        if (checkpoint + longest > m)
+        if (checkpoint + longest > m) {
+            st.columns += m - checkpoint + 1;
             break;
+        }
+        st.columns += longest + 1;
         /* Otherwise the escape segment is the run plus the obstacle that
          * follows it (a lone obstacle when longest = 0). */
         count += 1;
@@ -329,6 +332,7 @@ static void *batch_worker(void *arg)
         jb->stats.cells += st.cells;
         jb->stats.words += st.words;
         jb->stats.iterations += st.iterations;
+        jb->stats.columns += st.columns;
     }
     return NULL;
 }
@@ -369,7 +373,7 @@ int sso_filter_batch(const uint8_t *reads, const uint8_t *refs,
         pthread_create(&tids[t], NULL, batch_worker, jb);
     }
     int status = SSO_OK;
-    sso_stats sum = {0, 0, 0};
+    sso_stats sum = {0, 0, 0, 0};
     for (int t = 0; t < threads; ++t) {
         pthread_join(tids[t], NULL);
         if (jobs[t].status != SSO_OK && status == SSO_OK)
@@ -377,6 +381,7 @@ int sso_filter_batch(const uint8_t *reads, const uint8_t *refs,
         sum.cells += jobs[t].stats.cells;
         sum.words += jobs[t].stats.words;
         sum.iterations += jobs[t].stats.iterations;
+        sum.columns += jobs[t].stats.columns;
     }
     if (stats_sum)
         *stats_sum = sum;

@@ -33,11 +33,15 @@ extern "C" {
  * 2.4 (from each checkpoint up to and including the first obstacle of every
  * row, or up to the row end); words: the same cells counted in 32-column
  * words per row and checkpoint (ceil(cells_in_row / 32)); iterations: number
- * of checkpoints visited (escape segments searched). */
+ * of checkpoints visited (escape segments searched); columns: maze columns
+ * those searches span (from each checkpoint through the column of the
+ * segment's obstacle, or to the row end) -- what a walk that evaluates all
+ * 2E+1 rows of one column at a time visits. */
 typedef struct sso_stats {
     int64_t cells;
     int64_t words;
     int64_t iterations;
+    int64_t columns;
 } sso_stats;
 
 /* Eq. 1: the chip maze entry Z[i, j] (1-based i, j).  Returns 0 or 1. */

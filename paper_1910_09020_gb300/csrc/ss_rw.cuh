@@ -44,6 +44,7 @@
 
 #include "ss_device.cuh"
 #include "ss_rw_config.h"
+#include "ss_rwc.cuh"
 
 namespace ssk {
 
@@ -491,6 +492,10 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// The plain kernel walks the greedy one column at a time (rw_route_cols)
+// from E = kRwColsMinE to 15, and row-wise (rw_route) otherwise.
+constexpr int kRwColsMinE = 6;
+
 constexpr int kRwMaxStages = 2;
 constexpr int kRwGroup = 8;                  // tiles per CTA
 constexpr int kRwPipeMaxW16 = 16;            // m <= 256
@@ -605,7 +610,11 @@ __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
         if (t < np) {
             const SmemSeqPad q{sQ + u * w16};
             const SmemSeqPad r{sR + u * w16};
-            const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
+            int cnt;
+            if constexpr (E >= kRwColsMinE && E <= 15)
+                cnt = rw_route_cols<E>(q, r, a.m);
+            else
+                cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
             a.acc[p0 + u] = (uint8_t)(cnt <= E);
             a.obs[p0 + u] = cnt;
         }

@@ -1,0 +1,188 @@
+// ss_rwc.cuh -- one thread per pair, the greedy walked one column at a time
+// with the 2E+1 maze rows as the bits of one word (E <= 15).
+//
+// Method (Section 2.4): from checkpoint c the longest escape segment ends
+// at p* = max over rows of the row's first obstacle at or after c.  Walking
+// the columns j = c, c+1, ... with S_j = the rows free of obstacles in
+// columns c..j (S_c-1 = all rows), p* is the first j with S_j = 0: the
+// column where the last surviving row meets its obstacle.  That obstacle is
+// counted and the walk restarts at p* + 1 with all rows; reaching the row
+// end with S non-empty ends the net with no count.  The walk stops once the
+// count exceeds E (only min(count, E+1) is reported).
+//
+// GB300 mapping: bit i of S is diagonal s = i - E.  Column j of the maze
+// (Eq. 1) is one word: the Q bit planes from bit j - E on (one funnel shift
+// per plane), compared with R[j] broadcast to every row (a byte permute of
+// a multiply-spread R word), and -- only in chunks where a row can leave
+// the query -- ANDed with the "Q base exists" plane (Eq. 1 case 4).  About
+// ten integer operations per column whatever E is, and every thread of a
+// warp executes the same column body, so a warp diverges only where its
+// pairs stop.  Cheaper than the row-wise routing (rw_route) once 2E+1 rows
+// are many: a random pair is rejected after a few columns per obstacle,
+// where row-wise routing rebuilds and scans all rows of each word.
+#pragma once
+#include <cstdint>
+
+#include "ss_device.cuh"
+
+namespace ssk {
+
+// Bits 0..3 of r moved to the sign bits of the four bytes (bit i to bit
+// 8i + 7).  The product's terms, bit i times 2^(7 + 7k) for k = 0..3, land
+// on sixteen distinct positions, so nothing carries.
+SS_HD uint32_t spread4(uint32_t r) { return (r & 0xfu) * 0x10204080u; }
+
+// All ones if the sign bit of byte I of t is set, else zero: the byte
+// permute's sign-replicating selector (selector nibble 8 + I), as an
+// immediate operand.  Only bytes of the first source are selected, so t
+// also serves as the second.
+template <int I>
+SS_HD uint32_t byte_sign(uint32_t t)
+{
+    static_assert(I >= 0 && I < 4, "byte index");
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %1, %2;"
+        : "=r"(d)
+        : "r"(t), "n"(0x8888 + 0x1111 * I));
+    return d;
+#else
+    return ((t >> (8 * I + 7)) & 1u) ? 0xffffffffu : 0u;
+#endif
+}
+
+// 32 bits of a plane from bit O of word C on (-32 < O < 32): the previous
+// word P supplies negative offsets, the next word N positive ones.
+template <int O>
+SS_HD uint32_t rwc_window(uint32_t P, uint32_t C, uint32_t N)
+{
+    if constexpr (O < 0)
+        return funnel_r(P, C, 32 + O);
+    else
+        return funnel_r(C, N, O);
+}
+
+// The Q planes around the 32-column word being walked: previous, current
+// and next words of the lo, hi and "base exists" planes.
+struct RwcQ {
+    uint32_t lo_p, lo_c, lo_n, hi_p, hi_c, hi_n, v_p, v_c, v_n;
+};
+
+// Columns D0 .. D0+7 of the word (all before the row end).  tl/th: R bits
+// of columns D0..D0+3 and D0+4..D0+7, spread by spread4.
+template <int E, bool EDGE, int D>
+SS_HD void rwc_column(uint32_t &S, int &count, const RwcQ &q, uint32_t tl,
+                      uint32_t th)
+{
+    constexpr uint32_t kAll = (1u << (2 * E + 1)) - 1u;
+    constexpr int O = D - E;  // Q bit of row 0 relative to the word
+    const uint32_t ql = rwc_window<O>(q.lo_p, q.lo_c, q.lo_n);
+    const uint32_t qh = rwc_window<O>(q.hi_p, q.hi_c, q.hi_n);
+    // one three-input logic op per plane: S & ~(Q plane ^ broadcast R bit)
+    S &= ~(ql ^ byte_sign<D & 3>(tl));
+    S &= ~(qh ^ byte_sign<D & 3>(th));
+    if (EDGE)
+        S &= rwc_window<O>(q.v_p, q.v_c, q.v_n);
+    // the last surviving row met its obstacle here: count it, restart
+    const bool z = S == 0u;
+    count += z;
+    S = z ? kAll : S;
+}
+
+template <int E, bool EDGE, int D0>
+SS_HD void rwc_chunk(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
+                     uint32_t rhi)
+{
+    const uint32_t l0 = spread4(rlo >> D0), h0 = spread4(rhi >> D0);
+    const uint32_t l1 = spread4(rlo >> (D0 + 4));
+    const uint32_t h1 = spread4(rhi >> (D0 + 4));
+    rwc_column<E, EDGE, D0 + 0>(S, count, q, l0, h0);
+    rwc_column<E, EDGE, D0 + 1>(S, count, q, l0, h0);
+    rwc_column<E, EDGE, D0 + 2>(S, count, q, l0, h0);
+    rwc_column<E, EDGE, D0 + 3>(S, count, q, l0, h0);
+    rwc_column<E, EDGE, D0 + 4>(S, count, q, l1, h1);
+    rwc_column<E, EDGE, D0 + 5>(S, count, q, l1, h1);
+    rwc_column<E, EDGE, D0 + 6>(S, count, q, l1, h1);
+    rwc_column<E, EDGE, D0 + 7>(S, count, q, l1, h1);
+}
+
+// One column at run-time offset d of the word (the row end's partial
+// chunk): the same arithmetic with run-time shifts, always with case 4.
+template <int E>
+SS_HD void rwc_column_rt(uint32_t &S, int &count, const RwcQ &q,
+                         uint32_t rlo, uint32_t rhi, int d)
+{
+    constexpr uint32_t kAll = (1u << (2 * E + 1)) - 1u;
+    const int o = d - E;
+    const bool neg = o < 0;
+    const uint32_t sh = (uint32_t)(neg ? 32 + o : o);
+    const uint32_t ql = neg ? funnel_r(q.lo_p, q.lo_c, sh)
+                            : funnel_r(q.lo_c, q.lo_n, sh);
+    const uint32_t qh = neg ? funnel_r(q.hi_p, q.hi_c, sh)
+                            : funnel_r(q.hi_c, q.hi_n, sh);
+    const uint32_t qv = neg ? funnel_r(q.v_p, q.v_c, sh)
+                            : funnel_r(q.v_c, q.v_n, sh);
+    const uint32_t bl = 0u - ((rlo >> d) & 1u);
+    const uint32_t bh = 0u - ((rhi >> d) & 1u);
+    S &= qv & ~((ql ^ bl) | (qh ^ bh));
+    const bool z = S == 0u;
+    count += z;
+    S = z ? kAll : S;
+}
+
+// Route one pair of length m with threshold E (1 <= E <= 15); returns
+// min(count, E+1), equal to rw_route's.
+template <int E, class Seq>
+SS_HD int rw_route_cols(const Seq &Qs, const Seq &Rs, int m)
+{
+    static_assert(E >= 1 && E <= 15, "2E+1 rows in one word");
+    constexpr uint32_t kAll = (1u << (2 * E + 1)) - 1u;
+    const int W32 = (m + 31) >> 5;
+    RwcQ q;
+    q.lo_p = q.hi_p = q.v_p = 0u;  // before the query: case 4
+    Qs.planes(0, q.lo_c, q.hi_c);
+    Qs.planes(1, q.lo_n, q.hi_n);
+    q.v_c = mask_below(m);
+    q.v_n = mask_below(m - 32);
+    uint32_t S = kAll;
+    int count = 0;
+    for (int k = 0; k < W32; ++k) {
+        const int base = k << 5;
+        uint32_t rlo, rhi;
+        Rs.planes(k, rlo, rhi);
+        // chunks of 8 columns; a chunk is an edge chunk when one of its
+        // rows reads a query index below 0 or at/after m
+#define SS_RWC_CHUNK(D0)                                                    \
+    {                                                                       \
+        const int c0 = base + (D0);                                         \
+        if (c0 + 8 > m) {                                                   \
+            for (int d = (D0); base + d < m; ++d)                           \
+                rwc_column_rt<E>(S, count, q, rlo, rhi, d);                 \
+            return count <= E ? count : E + 1;                              \
+        }                                                                   \
+        if (c0 < E || c0 + 7 + E >= m)                                      \
+            rwc_chunk<E, true, (D0)>(S, count, q, rlo, rhi);                \
+        else                                                                \
+            rwc_chunk<E, false, (D0)>(S, count, q, rlo, rhi);               \
+        if (count > E)                                                      \
+            return E + 1;                                                   \
+    }
+        SS_RWC_CHUNK(0)
+        SS_RWC_CHUNK(8)
+        SS_RWC_CHUNK(16)
+        SS_RWC_CHUNK(24)
+#undef SS_RWC_CHUNK
+        // slide the Q windows by one word
+        q.lo_p = q.lo_c;
+        q.hi_p = q.hi_c;
+        q.v_p = q.v_c;
+        q.lo_c = q.lo_n;
+        q.hi_c = q.hi_n;
+        q.v_c = q.v_n;
+        Qs.planes(k + 2, q.lo_n, q.hi_n);
+        q.v_n = mask_below(m - 32 * (k + 2));
+    }
+    return count <= E ? count : E + 1;
+}
+
+}  // namespace ssk

@@ -36,6 +36,7 @@ def load():
     lib = ctypes.CDLL(OUT)
     P = ctypes.c_void_p
     lib.emu_rw_exact.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
+    lib.emu_rw_cols.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
     lib.emu_rw_runtime.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int]
     lib.emu_cw.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]

@@ -8,6 +8,7 @@
 #include "ss_cw.cuh"
 #include "ss_pack.cuh"
 #include "ss_rw.cuh"
+#include "ss_rwc.cuh"
 #include "ss_submaze.cuh"
 #include "ss_unequal.cuh"
 #include "ss_verify.cuh"
@@ -30,6 +31,25 @@ int exact_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
 {
     int out = -100;
     ((E == Es ? (out = exact_one<Es>(q, r, m), 0) : 0), ...);
+    return out;
+}
+
+template <int E>
+int cols_one(const uint32_t *q, const uint32_t *r, int m)
+{
+    const int w16 = (m + 15) / 16;
+    if constexpr (E >= 1 && E <= 15)
+        return rw_route_cols<E>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m);
+    else
+        return -100;
+}
+
+template <int... Es>
+int cols_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
+                  std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    ((E == Es ? (out = cols_one<Es>(q, r, m), 0) : 0), ...);
     return out;
 }
 
@@ -141,6 +161,12 @@ int emu_ed(const uint32_t *q, const uint32_t *r, int m, int E)
 int emu_rw_exact(const uint32_t *q, const uint32_t *r, int m, int E)
 {
     return exact_dispatch(E, q, r, m, std::make_integer_sequence<int, 32>{});
+}
+
+// Column-at-a-time routine (E = 1..15).
+int emu_rw_cols(const uint32_t *q, const uint32_t *r, int m, int E)
+{
+    return cols_dispatch(E, q, r, m, std::make_integer_sequence<int, 16>{});
 }
 
 // Bucketed row-wise routine: runtime E <= EMAX (1, 3, 7, 15, 31).

@@ -45,6 +45,31 @@ def test_rw_exact_matches_oracle(emu, m):
             assert got == want, (m, E, Q, R)
 
 
+@pytest.mark.parametrize("m", [1, 2, 7, 8, 9, 15, 16, 17, 31, 32, 33, 40,
+                               64, 65, 100, 150, 250, 257])
+def test_rw_cols_matches_oracle(emu, m):
+    """Column-at-a-time routine: every E it supports, lengths around the
+    8-column chunks and 32-column words, edges on both sides."""
+    for Q, R in pairs(1700 + m, 40, m, synth.rate_recipe(0.12)):
+        q, r = packed(Q), packed(R)
+        for E in range(1, 16):
+            got = emu.emu_rw_cols(P(q), P(r), m, E)
+            want = oracle.filter_pair(Q, R, E).obstacles
+            assert got == want, (m, E, Q, R)
+
+
+def test_rw_cols_headline_recipe(emu):
+    """The headline workload's pairs (Poisson(3) edits or random) at the
+    sweep's thresholds."""
+    reads, refs = synth.pairs_fixed(5, 0, 400, 100, synth.SHORT_POISSON)
+    for i in range(400):
+        Q, R = reads[i].tobytes(), refs[i].tobytes()
+        q, r = packed(Q), packed(R)
+        for E in (2, 4, 5, 6, 8, 10, 15):
+            assert emu.emu_rw_cols(P(q), P(r), 100, E) == \
+                oracle.filter_pair(Q, R, E).obstacles, (i, E)
+
+
 @pytest.mark.parametrize("emax", [1, 3, 7, 15, 31])
 def test_rw_runtime_threshold_matches_oracle(emu, emax):
     rng = np.random.default_rng(emax)

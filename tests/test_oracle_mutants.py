@@ -36,9 +36,12 @@ MUTANTS = {
     "checkpoint_skip": ("checkpoint = checkpoint + longest + 1;",
                         "checkpoint = checkpoint + longest + 2;"),
     # an obstacle counted on reaching the destination
-    "count_at_end": ("if (checkpoint + longest > m)\n            break;",
+    "count_at_end": ("if (checkpoint + longest > m) {\n"
+                     "            st.columns += m - checkpoint + 1;\n"
+                     "            break;",
                      "if (checkpoint + longest > m) {\n"
-                     "            count += 1;\n            break;\n        }"),
+                     "            st.columns += m - checkpoint + 1;\n"
+                     "            count += 1;\n            break;"),
     # step (4) never stops (uncapped count reported)
     "no_early_stop": ("if (stop_above_E && count > E)",
                       "if (stop_above_E && 0)"),
