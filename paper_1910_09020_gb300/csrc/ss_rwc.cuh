@@ -89,45 +89,28 @@ SS_HD void rwc_column(uint32_t &S, int &count, const RwcQ &q, uint32_t tl,
     S = z ? kAll : S;
 }
 
-template <int E, bool EDGE, int D0>
+// Columns D0 .. D0+7 of the word; with TAIL, only the first `live` of
+// them (the row end's partial chunk: a uniform test before each column).
+template <int E, bool EDGE, int D0, bool TAIL = false>
 SS_HD void rwc_chunk(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
-                     uint32_t rhi)
+                     uint32_t rhi, int live = 8)
 {
     const uint32_t l0 = spread4(rlo >> D0), h0 = spread4(rhi >> D0);
     const uint32_t l1 = spread4(rlo >> (D0 + 4));
     const uint32_t h1 = spread4(rhi >> (D0 + 4));
-    rwc_column<E, EDGE, D0 + 0>(S, count, q, l0, h0);
-    rwc_column<E, EDGE, D0 + 1>(S, count, q, l0, h0);
-    rwc_column<E, EDGE, D0 + 2>(S, count, q, l0, h0);
-    rwc_column<E, EDGE, D0 + 3>(S, count, q, l0, h0);
-    rwc_column<E, EDGE, D0 + 4>(S, count, q, l1, h1);
-    rwc_column<E, EDGE, D0 + 5>(S, count, q, l1, h1);
-    rwc_column<E, EDGE, D0 + 6>(S, count, q, l1, h1);
-    rwc_column<E, EDGE, D0 + 7>(S, count, q, l1, h1);
-}
-
-// One column at run-time offset d of the word (the row end's partial
-// chunk): the same arithmetic with run-time shifts, always with case 4.
-template <int E>
-SS_HD void rwc_column_rt(uint32_t &S, int &count, const RwcQ &q,
-                         uint32_t rlo, uint32_t rhi, int d)
-{
-    constexpr uint32_t kAll = (1u << (2 * E + 1)) - 1u;
-    const int o = d - E;
-    const bool neg = o < 0;
-    const uint32_t sh = (uint32_t)(neg ? 32 + o : o);
-    const uint32_t ql = neg ? funnel_r(q.lo_p, q.lo_c, sh)
-                            : funnel_r(q.lo_c, q.lo_n, sh);
-    const uint32_t qh = neg ? funnel_r(q.hi_p, q.hi_c, sh)
-                            : funnel_r(q.hi_c, q.hi_n, sh);
-    const uint32_t qv = neg ? funnel_r(q.v_p, q.v_c, sh)
-                            : funnel_r(q.v_c, q.v_n, sh);
-    const uint32_t bl = 0u - ((rlo >> d) & 1u);
-    const uint32_t bh = 0u - ((rhi >> d) & 1u);
-    S &= qv & ~((ql ^ bl) | (qh ^ bh));
-    const bool z = S == 0u;
-    count += z;
-    S = z ? kAll : S;
+#define SS_RWC_COL(I, L, H)                                                 \
+    if (TAIL && (I) >= live)                                                \
+        return;                                                             \
+    rwc_column<E, EDGE, D0 + (I)>(S, count, q, L, H);
+    SS_RWC_COL(0, l0, h0)
+    SS_RWC_COL(1, l0, h0)
+    SS_RWC_COL(2, l0, h0)
+    SS_RWC_COL(3, l0, h0)
+    SS_RWC_COL(4, l1, h1)
+    SS_RWC_COL(5, l1, h1)
+    SS_RWC_COL(6, l1, h1)
+    SS_RWC_COL(7, l1, h1)
+#undef SS_RWC_COL
 }
 
 // Route one pair of length m with threshold E (1 <= E <= 15); returns
@@ -156,8 +139,7 @@ SS_HD int rw_route_cols(const Seq &Qs, const Seq &Rs, int m)
     {                                                                       \
         const int c0 = base + (D0);                                         \
         if (c0 + 8 > m) {                                                   \
-            for (int d = (D0); base + d < m; ++d)                           \
-                rwc_column_rt<E>(S, count, q, rlo, rhi, d);                 \
+            rwc_chunk<E, true, (D0), true>(S, count, q, rlo, rhi, m - c0);  \
             return count <= E ? count : E + 1;                              \
         }                                                                   \
         if (c0 < E || c0 + 7 + E >= m)                                      \
