@@ -26,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -195,11 +196,21 @@ KERNEL_SOURCES = {
 }
 
 
+def code_of(text: str) -> str:
+    """C/CUDA source without comments and blank space: what compiles."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(kernel: str) -> str:
+    """Hash of the code (comments and layout ignored) a profiled kernel is
+    compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_09020_gb300", "csrc")
     for name in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        with open(os.path.join(csrc, name)) as f:
+            h.update(code_of(f.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -881,16 +892,20 @@ def run_ours(args):
         # the device path and the host path must agree
         same = (torch.equal(hacc, acc.cpu()) and torch.equal(hobs, obs.cpu()))
         e2e["matches_device_path"] = bool(same)
-        # the host link's own rate: one pinned host -> device copy of the
-        # same input bytes (the e2e path cannot beat bytes / this rate)
-        a, b = _ev(), _ev()
-        torch.cuda.synchronize()
-        a.record()
-        dq.copy_(hq, non_blocking=True)
-        dr.copy_(hr, non_blocking=True)
-        b.record()
-        torch.cuda.synchronize()
-        h2d_gbs = 2 * n * M / (a.elapsed_time(b) * 1e-3) / 1e9
+        # the host link's own rate: pinned host -> device copies of the
+        # same input bytes, the best of three (the e2e path cannot beat
+        # bytes / this rate)
+        best_ms = float("inf")
+        for _ in range(3):
+            a, b = _ev(), _ev()
+            torch.cuda.synchronize()
+            a.record()
+            dq.copy_(hq, non_blocking=True)
+            dr.copy_(hr, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            best_ms = min(best_ms, a.elapsed_time(b))
+        h2d_gbs = 2 * n * M / (best_ms * 1e-3) / 1e9
         e2e["h2d_copy_gbs"] = h2d_gbs
         e2e["copy_bound_pairs_per_s"] = (
             world * pairs_per_step / (2 * n * M / (h2d_gbs * 1e9)))

@@ -185,16 +185,16 @@ SS_HD RowBits rev_rows(uint32_t lo, uint32_t hi)
     return out;
 }
 
-// Borrow (plain kernel E >= 5): Z_s - 2^cl borrows through the row's zeros
-// from the checkpoint bit cl up to its first obstacle p_s, so Z_s ^ (Z_s -
-// 2^cl) sets exactly bits cl..p_s, and the OR over rows has its highest set
-// bit at max_s p_s: two operations per row and iteration -- the subtraction
-// a multiply-add on the FMA pipe, the logic op on the ALU pipe -- and a
-// find-leading-one per iteration.  A row with no obstacle up to bit 31
-// borrows out and sets bits cl..31, like an obstacle at bit 31, so bit 31 of
-// the OR sends the iteration to an exact per-row test.  The fixed cost per
-// iteration is higher than the smear-AND form's, which stays faster up to
-// nine rows.
+// Borrow (plain kernel E = 5 and E >= 16): Z_s - 2^cl borrows through the
+// row's zeros from the checkpoint bit cl up to its first obstacle p_s, so
+// Z_s ^ (Z_s - 2^cl) sets exactly bits cl..p_s, and the OR over rows has its
+// highest set bit at max_s p_s: two operations per row and iteration -- the
+// subtraction a multiply-add on the FMA pipe, the logic op on the ALU pipe
+// -- and a find-leading-one per iteration.  A row with no obstacle up to bit
+// 31 borrows out and sets bits cl..31, like an obstacle at bit 31, so bit 31
+// of the OR sends the iteration to an exact per-row test.  The fixed cost
+// per iteration is higher than the smear-AND form's, which stays faster up
+// to nine rows.
 template <int NR, class RowBits>
 SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
                           int base, int m, int E, int &count,
@@ -265,10 +265,11 @@ SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
     }
 }
 
-// rw_word_borrow for the plain kernel's thresholds E >= 5 (11 rows or
-// more).  The bucketed kernel (E at run time, 2 EMAX + 1 rows) keeps the
-// smear-AND form: with the borrow form its two-length batches at E of
-// 7-10 % of the length ran 2 % slower.
+// rw_word_borrow for the plain kernel's row-wise thresholds E >= 5 (11
+// rows or more; E = 6..15 walk columns instead, see kRwColsMinE).  The
+// bucketed kernel (E at run time, 2 EMAX + 1 rows) keeps the smear-AND
+// form: with the borrow form its two-length batches at E of 7-10 % of the
+// length ran 2 % slower.
 constexpr int kRwBorrowMinE = 5;
 
 // Route one pair of length m with threshold E (E == EMAX when EXACT);
