@@ -130,7 +130,7 @@ def test_uniform_parity_all_E(F, m):
     n = 777 if m <= 256 else 260
     for name, rec in recipes().items():
         reads, refs = synth.pairs_fixed(7 + m, 0, n, m, rec)
-        for E in list(range(0, 12)) + [15, 16, 20, 25, 31]:
+        for E in list(range(0, 17)) + [20, 25, 31]:
             acc, obs = gpu_filter_fixed(F, reads, refs, E)
             oacc, oobs = oracle_fixed(reads, refs, E)
             assert_same(acc, obs, oacc, oobs, f"m={m} E={E} {name}")
