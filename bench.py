@@ -385,7 +385,7 @@ def _pack_varlen(F, L, recipe, seed):
 
 
 def _oracle_model(host, L, E, idx):
-    """Oracle time and the op model (survey's row-word model) on a sample
+    """Oracle time and the op model (the row-word formulation) on a sample
     of pairs, by threshold group.  Returns (seconds, alu ops, xu ops,
     cells)."""
     import oracle
