@@ -385,9 +385,9 @@ def _pack_varlen(F, L, recipe, seed):
 
 
 def _oracle_model(host, L, E, idx):
-    """Oracle time and the op model (the row-word formulation) on a sample
-    of pairs, by threshold group.  Returns (seconds, alu ops, xu ops,
-    cells)."""
+    """Oracle time and the op model (per threshold group, the cheaper of
+    the row-word and column formulations) on a sample of pairs.  Returns
+    (seconds, alu ops, xu ops, cells)."""
     import oracle
     reads, refs, off = host
     t = alu = xu = cells = 0.0
@@ -398,14 +398,13 @@ def _oracle_model(host, L, E, idx):
         so = np.zeros(len(sel) + 1, np.int64)
         np.cumsum(L[sel], out=so[1:])
         t0 = time.perf_counter()
-        _, _, (c, w, it, _) = oracle.filter_batch(sub_r, sub_f, L[sel],
-                                                  E[sel], offsets=so,
-                                                  with_stats=True)
+        _, _, (c, w, it, col) = oracle.filter_batch(sub_r, sub_f, L[sel],
+                                                    E[sel], offsets=so,
+                                                    with_stats=True)
         t += time.perf_counter() - t0
-        # the row-word formulation: the warp and CTA kernels evaluate 32
-        # rows per word op and stop each word early, below either model
-        alu += w * K_WORD + it * (2 * int(e) + 1) * K_RED + it * K_ITER
-        xu += w
+        a_, x_, _ = model_ops(int(e), w, it, col)  # the cheaper form
+        alu += a_
+        xu += x_
         cells += c
     return t, alu, xu, cells
 
@@ -502,9 +501,10 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
     roof["bound"] = ("hbm" if t_bound == roof["t_hbm_ms"] else
                      "alu" if t_bound == roof.get("t_alu_ms") else "xu")
     roof["frac"] = t_bound / t_p
-    roof["note"] = ("ALU term: the row-word op model of the lazy maze; the "
-                    "warp/CTA kernels evaluate 32 rows per word op, so they "
-                    "can run faster than that model")
+    roof["note"] = ("ALU term: per threshold group the cheaper of the "
+                    "row-word and column op models of the lazy maze; the "
+                    "warp/CTA kernels evaluate each 32-row word only until "
+                    "its rows die, so they can run below either model")
     out["roofline"] = roof
     del pq, pr
     return out
