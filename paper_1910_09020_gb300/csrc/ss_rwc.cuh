@@ -22,6 +22,7 @@
 // where row-wise routing rebuilds and scans all rows of each word.
 #pragma once
 #include <cstdint>
+#include <utility>
 
 #include "ss_device.cuh"
 
@@ -89,8 +90,21 @@ SS_HD void rwc_column(uint32_t &S, int &count, const RwcQ &q, uint32_t tl,
     S = z ? kAll : S;
 }
 
-// Columns D0 .. D0+7 of the word; with TAIL, only the first `live` of
-// them (the row end's partial chunk: a uniform test before each column).
+// Columns D0+I of the word for I in the sequence; with TAIL, only those
+// with I < live (the row end's partial chunk: a uniform test per column).
+template <int E, bool EDGE, int D0, bool TAIL, int... I>
+SS_HD void rwc_columns(uint32_t &S, int &count, const RwcQ &q, uint32_t l0,
+                       uint32_t h0, uint32_t l1, uint32_t h1, int live,
+                       std::integer_sequence<int, I...>)
+{
+    ((!TAIL || I < live
+          ? rwc_column<E, EDGE, D0 + I>(S, count, q, I < 4 ? l0 : l1,
+                                        I < 4 ? h0 : h1)
+          : void()),
+     ...);
+}
+
+// Columns D0 .. D0+7 of the word (the first `live` of them with TAIL).
 template <int E, bool EDGE, int D0, bool TAIL = false>
 SS_HD void rwc_chunk(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
                      uint32_t rhi, int live = 8)
@@ -98,19 +112,27 @@ SS_HD void rwc_chunk(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
     const uint32_t l0 = spread4(rlo >> D0), h0 = spread4(rhi >> D0);
     const uint32_t l1 = spread4(rlo >> (D0 + 4));
     const uint32_t h1 = spread4(rhi >> (D0 + 4));
-#define SS_RWC_COL(I, L, H)                                                 \
-    if (TAIL && (I) >= live)                                                \
-        return;                                                             \
-    rwc_column<E, EDGE, D0 + (I)>(S, count, q, L, H);
-    SS_RWC_COL(0, l0, h0)
-    SS_RWC_COL(1, l0, h0)
-    SS_RWC_COL(2, l0, h0)
-    SS_RWC_COL(3, l0, h0)
-    SS_RWC_COL(4, l1, h1)
-    SS_RWC_COL(5, l1, h1)
-    SS_RWC_COL(6, l1, h1)
-    SS_RWC_COL(7, l1, h1)
-#undef SS_RWC_COL
+    rwc_columns<E, EDGE, D0, TAIL>(S, count, q, l0, h0, l1, h1, live,
+                                   std::make_integer_sequence<int, 8>{});
+}
+
+// Chunk D0 of the word at column base: the walk's result if it ends here
+// (the row end, or the count past E), else -1.  A chunk is an edge chunk
+// when one of its rows reads a query index below 0 or at/after m.
+template <int E, int D0>
+SS_HD int rwc_chunk_at(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
+                       uint32_t rhi, int base, int m)
+{
+    const int c0 = base + D0;
+    if (c0 + 8 > m) {
+        rwc_chunk<E, true, D0, true>(S, count, q, rlo, rhi, m - c0);
+        return count <= E ? count : E + 1;
+    }
+    if (c0 < E || c0 + 7 + E >= m)
+        rwc_chunk<E, true, D0>(S, count, q, rlo, rhi);
+    else
+        rwc_chunk<E, false, D0>(S, count, q, rlo, rhi);
+    return count > E ? E + 1 : -1;
 }
 
 // Route one pair of length m with threshold E (1 <= E <= 15); returns
@@ -133,27 +155,12 @@ SS_HD int rw_route_cols(const Seq &Qs, const Seq &Rs, int m)
         const int base = k << 5;
         uint32_t rlo, rhi;
         Rs.planes(k, rlo, rhi);
-        // chunks of 8 columns; a chunk is an edge chunk when one of its
-        // rows reads a query index below 0 or at/after m
-#define SS_RWC_CHUNK(D0)                                                    \
-    {                                                                       \
-        const int c0 = base + (D0);                                         \
-        if (c0 + 8 > m) {                                                   \
-            rwc_chunk<E, true, (D0), true>(S, count, q, rlo, rhi, m - c0);  \
-            return count <= E ? count : E + 1;                              \
-        }                                                                   \
-        if (c0 < E || c0 + 7 + E >= m)                                      \
-            rwc_chunk<E, true, (D0)>(S, count, q, rlo, rhi);                \
-        else                                                                \
-            rwc_chunk<E, false, (D0)>(S, count, q, rlo, rhi);               \
-        if (count > E)                                                      \
-            return E + 1;                                                   \
-    }
-        SS_RWC_CHUNK(0)
-        SS_RWC_CHUNK(8)
-        SS_RWC_CHUNK(16)
-        SS_RWC_CHUNK(24)
-#undef SS_RWC_CHUNK
+        int res;
+        if ((res = rwc_chunk_at<E, 0>(S, count, q, rlo, rhi, base, m)) >= 0 ||
+            (res = rwc_chunk_at<E, 8>(S, count, q, rlo, rhi, base, m)) >= 0 ||
+            (res = rwc_chunk_at<E, 16>(S, count, q, rlo, rhi, base, m)) >= 0 ||
+            (res = rwc_chunk_at<E, 24>(S, count, q, rlo, rhi, base, m)) >= 0)
+            return res;
         // slide the Q windows by one word
         q.lo_p = q.lo_c;
         q.hi_p = q.hi_c;
