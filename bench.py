@@ -264,11 +264,21 @@ def cpu_baseline(target_s: float):
     }, stats, n
 
 
+def row_word_ops(E: int, words, iters):
+    """ALU ops of the row-word formulation (and `words` find-first ops)."""
+    return words * K_WORD + iters * (2 * E + 1) * K_RED + iters * K_ITER
+
+
+def column_ops(E: int, iters, cols):
+    """ALU ops of the column formulation (no find-first)."""
+    return cols * ((2 * E + 1 + 31) // 32) * K_COL + iters * K_ITER
+
+
 def model_ops(E: int, words, iters, cols):
     """ALU and find-first ops of the cheaper formulation (see K_COL), and
     which one it is."""
-    rows = words * K_WORD + iters * (2 * E + 1) * K_RED + iters * K_ITER
-    by_col = cols * ((2 * E + 1 + 31) // 32) * K_COL + iters * K_ITER
+    rows = row_word_ops(E, words, iters)
+    by_col = column_ops(E, iters, cols)
     if by_col < rows:
         return by_col, 0, "columns"
     return rows, words, "row words"
@@ -282,7 +292,7 @@ def op_model(stats: dict, n: int) -> dict:
         out[E] = {"alu_ops_per_pair": alu / n, "xu_ops_per_pair": xu / n,
                   "model": form,
                   "alu_ops_row_words_per_pair":
-                      model_ops(E, words, iters, 10**18)[0] / n,
+                      row_word_ops(E, words, iters) / n,
                   "iterations_per_pair": iters / n,
                   "columns_per_pair": cols / n,
                   "cells_per_pair": cells / n}

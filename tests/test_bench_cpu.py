@@ -33,8 +33,10 @@ def test_op_model_takes_the_cheaper_formulation():
     assert form == "columns" and xu == 0
     assert ops == 66 * bench.K_COL + 9 * bench.K_ITER
     # more than 32 rows take several words per column
-    ops, _, _ = bench.model_ops(40, words=10**9, iters=2, cols=10)
-    assert ops == 10 * 3 * bench.K_COL + 2 * bench.K_ITER
+    assert bench.column_ops(40, iters=2, cols=10) == \
+        10 * 3 * bench.K_COL + 2 * bench.K_ITER
+    ops, _, form = bench.model_ops(40, words=10**9, iters=2, cols=10)
+    assert form == "columns" and ops == bench.column_ops(40, 2, 10)
 
 
 def test_op_model_on_oracle_counters():
