@@ -25,8 +25,14 @@ __global__ void __launch_bounds__(128) k_submaze(const SubmazeArgs a)
          p += (int64_t)gridDim.x * blockDim.x) {
         const GlobalSeq q{a.reads + p * a.w16, a.w16};
         const GlobalSeq r{a.refs + p * a.w16, a.w16};
-        const int cnt =
-            submaze_route<EMAX>(q, r, a.m, a.E, a.t, a.y, a.neg1);
+        // the column walk from EMAX = 7 (it walks at least one 8-column
+        // chunk, which row-wise routing of up to 7 rows undercuts); the
+        // row-wise form for 63 rows
+        int cnt;
+        if constexpr (EMAX >= 7 && EMAX <= 15)
+            cnt = submaze_route_cols<EMAX>(q, r, a.m, a.E, a.t, a.y);
+        else
+            cnt = submaze_route<EMAX>(q, r, a.m, a.E, a.t, a.y, a.neg1);
         a.acc[p] = (uint8_t)(cnt <= a.E);
         a.obs[p] = cnt;
     }
@@ -42,8 +48,8 @@ cudaError_t launch_submaze(const uint32_t *reads, const uint32_t *refs,
     SubmazeArgs a{reads, refs, n, m, E, t, y, (m + 15) / 16, 0xffffffffu,
                   acc, obs};
     const int64_t want = (n + 127) / 128;
-    const int grid = (int)(want < (int64_t)sm_count * 16 ? want
-                                                         : (int64_t)sm_count * 16);
+    const int64_t cap = (int64_t)sm_count * 16;
+    const int grid = (int)(want < cap ? want : cap);
     const int Ee = E < m - 1 ? E : (m > 0 ? m - 1 : 0);
     if (Ee <= 3)
         k_submaze<3><<<grid, 128, 0, st>>>(a);

@@ -50,5 +50,9 @@ def load():
                                 ctypes.c_int]
     lib.emu_submaze.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int]
+    lib.emu_submaze_rows.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int]
+    lib.emu_submaze_cols.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int]
     _lib = lib
     return lib

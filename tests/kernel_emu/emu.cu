@@ -145,6 +145,41 @@ int emu_submaze(const uint32_t *q, const uint32_t *r, int m, int E, int t,
     if (Ee <= 3)
         return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
     if (Ee <= 7)
+        return submaze_route_cols<7>(Q, R, m, E, t, y);
+    if (Ee <= 15)
+        return submaze_route_cols<15>(Q, R, m, E, t, y);
+    return submaze_route<31>(Q, R, m, E, t, y, 0xffffffffu);
+}
+
+// The column-walk sub-maze routine at every class it supports (-2 above).
+int emu_submaze_cols(const uint32_t *q, const uint32_t *r, int m, int E, int t,
+                     int y)
+{
+    const int w16 = (m + 15) / 16;
+    const GlobalSeq Q{q, w16}, R{r, w16};
+    const int Ee = eff_threshold(m, E);
+    if (Ee <= 1)
+        return submaze_route_cols<1>(Q, R, m, E, t, y);
+    if (Ee <= 3)
+        return submaze_route_cols<3>(Q, R, m, E, t, y);
+    if (Ee <= 7)
+        return submaze_route_cols<7>(Q, R, m, E, t, y);
+    if (Ee <= 15)
+        return submaze_route_cols<15>(Q, R, m, E, t, y);
+    return -2;
+}
+
+// The row-wise sub-maze routine at every class (the kernel uses it for
+// EMAX = 3 and 31).
+int emu_submaze_rows(const uint32_t *q, const uint32_t *r, int m, int E, int t,
+                     int y)
+{
+    const int w16 = (m + 15) / 16;
+    const GlobalSeq Q{q, w16}, R{r, w16};
+    const int Ee = eff_threshold(m, E);
+    if (Ee <= 3)
+        return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
+    if (Ee <= 7)
         return submaze_route<7>(Q, R, m, E, t, y, 0xffffffffu);
     if (Ee <= 15)
         return submaze_route<15>(Q, R, m, E, t, y, 0xffffffffu);

@@ -137,16 +137,23 @@ def test_banded_edit_distance_matches_oracle(emu, m):
 
 @pytest.mark.parametrize("t", [1, 3, 8, 31, 32, 33, 77, 1000])
 def test_submaze_matches_oracle(emu, t):
+    """The kernel's choice and both sub-maze routines (the column walk at
+    every class up to E' = 15, the row-wise one at every class) against
+    the oracle."""
     rng = np.random.default_rng(t)
     for i in range(40):
         m = int(rng.integers(1, 180))
         Q, R = pairs(800 + i, 1, m, synth.rate_recipe(0.12))[0]
         q, r = packed(Q), packed(R)
-        for E in (0, 2, 5, 15, 31):
+        for E in (0, 1, 2, 5, 9, 15, 20, 31):
             for y in (1, 3, 1000):
-                got = emu.emu_submaze(P(q), P(r), m, E, t, y)
                 want = oracle.filter_submaze(Q, R, E, t, y).obstacles
+                got = emu.emu_submaze(P(q), P(r), m, E, t, y)
                 assert got == want, (m, E, t, y)
+                got = emu.emu_submaze_rows(P(q), P(r), m, E, t, y)
+                assert got == want, ("rows", m, E, t, y)
+                got = emu.emu_submaze_cols(P(q), P(r), m, E, t, y)
+                assert got in (want, -2), ("cols", m, E, t, y)
 
 
 CODE = {c: i for i, c in enumerate(b"ACGT")}
