@@ -66,7 +66,12 @@ __global__ void __launch_bounds__(128) k_rw_unequal(const UnequalArgs a)
             continue;
         const GlobalSeq q{a.reads + a.read_off[p], (mQ + 15) >> 4};
         const GlobalSeq r{a.refs + a.ref_off[p], (mR + 15) >> 4};
-        const int cnt = rw_route2<EMAX>(q, mQ, r, mR, E, 0xffffffffu);
+        // the column walk from 15 rows; row-wise below and for 63 rows
+        int cnt;
+        if constexpr (EMAX >= 7 && EMAX <= 15)
+            cnt = rw_route2_cols<EMAX>(q, mQ, r, mR, E);
+        else
+            cnt = rw_route2<EMAX>(q, mQ, r, mR, E, 0xffffffffu);
         a.acc[p] = (uint8_t)(cnt <= E);
         a.obs[p] = cnt;
     }

@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "ss_device.cuh"
+#include "ss_rwc.cuh"
 
 namespace ssk {
 
@@ -119,6 +120,117 @@ SS_HD int rw_route2(const Seq &Qs, int mQ, const Seq &Rs, int mR, int E,
         Qs.planes(k + 2, qlo_n, qhi_n);
     }
     return count;
+}
+
+// rw_route2 walked one column at a time (EMAX <= 15), as rw_route_cols
+// walks the equal-length greedy: the 2 EMAX + 1 rows in one word, the
+// pair's own 2E + 1 of them set in kAll, one column per reference base.
+// In a chunk where a row reads a query index outside 0..mQ-1, a cell is an
+// obstacle iff (in range and mismatched) or (out of range and the lengths
+// are equal): one three-input op with the per-pair mask fe (all ones when
+// the ends are free), so the warp's threads need not agree on it.
+template <int EMAX, bool EDGE, int D>
+SS_HD void uqc_column(uint32_t &S, int &count, const RwcQ &q, uint32_t tl,
+                      uint32_t th, uint32_t kAll, uint32_t fe)
+{
+    constexpr int O = D - EMAX;  // Q bit of row 0 relative to the word
+    const uint32_t xl =
+        rwc_window<O>(q.lo_p, q.lo_c, q.lo_n) ^ byte_sign<D & 3>(tl);
+    const uint32_t xh =
+        rwc_window<O>(q.hi_p, q.hi_c, q.hi_n) ^ byte_sign<D & 3>(th);
+    if (EDGE) {
+        const uint32_t qv = rwc_window<O>(q.v_p, q.v_c, q.v_n);
+        const uint32_t mis = xl | xh;
+        S &= ~((qv & mis) | (~qv & ~fe));
+    } else {
+        S &= ~xl;
+        S &= ~xh;
+    }
+    const bool z = S == 0u;  // the last free row met its obstacle here
+    count += z;
+    S = z ? kAll : S;
+}
+
+template <int EMAX, bool EDGE, int D0, bool TAIL, int... I>
+SS_HD void uqc_columns(uint32_t &S, int &count, const RwcQ &q, uint32_t l0,
+                       uint32_t h0, uint32_t l1, uint32_t h1, uint32_t kAll,
+                       uint32_t fe, int live, std::integer_sequence<int, I...>)
+{
+    ((!TAIL || I < live
+          ? uqc_column<EMAX, EDGE, D0 + I>(S, count, q, I < 4 ? l0 : l1,
+                                           I < 4 ? h0 : h1, kAll, fe)
+          : void()),
+     ...);
+}
+
+// Chunk D0 (8 columns) of the word at column base: the result if the walk
+// ends here (the reference's end, or the count past E), else -1.
+template <int EMAX, int D0>
+SS_HD int uqc_chunk_at(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
+                       uint32_t rhi, uint32_t kAll, uint32_t fe, int base,
+                       int mQ, int mR, int Er, int E)
+{
+    const int c0 = base + D0;
+    const uint32_t l0 = spread4(rlo >> D0), h0 = spread4(rhi >> D0);
+    const uint32_t l1 = spread4(rlo >> (D0 + 4));
+    const uint32_t h1 = spread4(rhi >> (D0 + 4));
+    const auto cols = std::make_integer_sequence<int, 8>{};
+    if (c0 + 8 > mR) {  // the reference's end
+        uqc_columns<EMAX, true, D0, true>(S, count, q, l0, h0, l1, h1, kAll,
+                                          fe, mR - c0, cols);
+        return count <= E ? count : E + 1;
+    }
+    if (c0 < Er || c0 + 7 + Er >= mQ)
+        uqc_columns<EMAX, true, D0, false>(S, count, q, l0, h0, l1, h1, kAll,
+                                           fe, 8, cols);
+    else
+        uqc_columns<EMAX, false, D0, false>(S, count, q, l0, h0, l1, h1,
+                                            kAll, fe, 8, cols);
+    return count > E ? E + 1 : -1;
+}
+
+// rw_route2's result, walked one column at a time (EMAX <= 15).
+template <int EMAX, class Seq>
+SS_HD int rw_route2_cols(const Seq &Qs, int mQ, const Seq &Rs, int mR,
+                         int E)
+{
+    static_assert(EMAX >= 1 && EMAX <= 15, "2 EMAX + 1 rows in one word");
+    const int Er = E < EMAX ? E : EMAX;  // rows past EMAX read no base
+    const uint32_t kAll = ((2u << (2 * Er)) - 1u) << (EMAX - Er);
+    const uint32_t fe = mQ != mR ? 0xffffffffu : 0u;
+    const int W32 = (mR + 31) >> 5;
+    RwcQ q;
+    q.lo_p = q.hi_p = q.v_p = 0u;  // before the query
+    Qs.planes(0, q.lo_c, q.hi_c);
+    Qs.planes(1, q.lo_n, q.hi_n);
+    q.v_c = mask_below(mQ);
+    q.v_n = mask_below(mQ - 32);
+    uint32_t S = kAll;
+    int count = 0;
+    for (int k = 0; k < W32; ++k) {
+        const int base = k << 5;
+        uint32_t rlo, rhi;
+        Rs.planes(k, rlo, rhi);
+        int res;
+        if ((res = uqc_chunk_at<EMAX, 0>(S, count, q, rlo, rhi, kAll, fe,
+                                         base, mQ, mR, Er, E)) >= 0 ||
+            (res = uqc_chunk_at<EMAX, 8>(S, count, q, rlo, rhi, kAll, fe,
+                                         base, mQ, mR, Er, E)) >= 0 ||
+            (res = uqc_chunk_at<EMAX, 16>(S, count, q, rlo, rhi, kAll, fe,
+                                          base, mQ, mR, Er, E)) >= 0 ||
+            (res = uqc_chunk_at<EMAX, 24>(S, count, q, rlo, rhi, kAll, fe,
+                                          base, mQ, mR, Er, E)) >= 0)
+            return res;
+        q.lo_p = q.lo_c;
+        q.hi_p = q.hi_c;
+        q.v_p = q.v_c;
+        q.lo_c = q.lo_n;
+        q.hi_c = q.hi_n;
+        q.v_c = q.v_n;
+        Qs.planes(k + 2, q.lo_n, q.hi_n);
+        q.v_n = mask_below(mQ - 32 * (k + 2));
+    }
+    return count <= E ? count : E + 1;
 }
 
 }  // namespace ssk

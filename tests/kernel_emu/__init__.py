@@ -48,6 +48,8 @@ def load():
     lib.emu_pack_window.restype = ctypes.c_uint32
     lib.emu_unequal.argtypes = [P, ctypes.c_int, P, ctypes.c_int,
                                 ctypes.c_int]
+    lib.emu_unequal_form.argtypes = [P, ctypes.c_int, P, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int]
     lib.emu_submaze.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int]
     lib.emu_submaze_rows.argtypes = [P, P, ctypes.c_int, ctypes.c_int,

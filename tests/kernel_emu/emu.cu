@@ -127,6 +127,37 @@ int emu_unequal(const uint32_t *q, int mQ, const uint32_t *r, int mR, int E)
     if (rows <= 3)
         return rw_route2<3>(Q, mQ, R, mR, E, 0xffffffffu);
     if (rows <= 7)
+        return rw_route2_cols<7>(Q, mQ, R, mR, E);
+    if (rows <= 15)
+        return rw_route2_cols<15>(Q, mQ, R, mR, E);
+    if (rows <= 31)
+        return rw_route2<31>(Q, mQ, R, mR, E, 0xffffffffu);
+    return -2;
+}
+
+// Both unequal-length routines at every class they support (form 0:
+// row-wise, 1: column walk; -2 past the class table or the form's rows).
+int emu_unequal_form(const uint32_t *q, int mQ, const uint32_t *r, int mR,
+                     int E, int form)
+{
+    const GlobalSeq Q{q, (mQ + 15) / 16}, R{r, (mR + 15) / 16};
+    const int rows = unequal_rows(mQ, mR, E);
+    if (rows < 0)
+        return 0;
+    if (form == 1) {
+        if (rows <= 1)
+            return rw_route2_cols<1>(Q, mQ, R, mR, E);
+        if (rows <= 3)
+            return rw_route2_cols<3>(Q, mQ, R, mR, E);
+        if (rows <= 7)
+            return rw_route2_cols<7>(Q, mQ, R, mR, E);
+        if (rows <= 15)
+            return rw_route2_cols<15>(Q, mQ, R, mR, E);
+        return -2;
+    }
+    if (rows <= 3)
+        return rw_route2<3>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 7)
         return rw_route2<7>(Q, mQ, R, mR, E, 0xffffffffu);
     if (rows <= 15)
         return rw_route2<15>(Q, mQ, R, mR, E, 0xffffffffu);

@@ -207,12 +207,13 @@ def test_unequal_lengths_match_oracle(emu):
         Q = Q[:mq]
         R = R[:mr]
         q, r = packed(Q), packed(R)
-        for E in (0, 1, 3, 7, 12, 31):
-            got = emu.emu_unequal(P(q), mq, P(r), mr, E)
-            if got == -2:
-                continue
+        for E in (0, 1, 2, 3, 5, 7, 9, 12, 15, 20, 31):
             want = oracle.filter_unequal(Q, R, E).obstacles
-            assert got == want, (mq, mr, E, got, want)
+            got = emu.emu_unequal(P(q), mq, P(r), mr, E)
+            assert got in (want, -2), (mq, mr, E, got, want)
+            for form in (0, 1):  # row-wise and column walk, every class
+                got = emu.emu_unequal_form(P(q), mq, P(r), mr, E, form)
+                assert got in (want, -2), (form, mq, mr, E, got, want)
 
 
 @pytest.mark.parametrize("K", [4, 8, 16])
