@@ -18,8 +18,12 @@
 // ten integer operations per column whatever E is, and every thread of a
 // warp executes the same column body, so a warp diverges only where its
 // pairs stop.  Cheaper than the row-wise routing (rw_route) once 2E+1 rows
-// are many: a random pair is rejected after a few columns per obstacle,
-// where row-wise routing rebuilds and scans all rows of each word.
+// are many and many pairs are dissimilar: a random pair is rejected after
+// a few columns per obstacle, where row-wise routing rebuilds and scans all
+// rows of each word (for a long, similar pair the row-wise form, 32
+// columns per op, stays cheaper).  The same walk, with the pair's rows
+// masked inside a wider word, serves the sub-maze mode (ss_submaze.cuh) and
+// pairs of different lengths (ss_unequal.cuh).
 #pragma once
 #include <cstdint>
 #include <utility>
@@ -69,8 +73,8 @@ struct RwcQ {
     uint32_t lo_p, lo_c, lo_n, hi_p, hi_c, hi_n, v_p, v_c, v_n;
 };
 
-// Columns D0 .. D0+7 of the word (all before the row end).  tl/th: R bits
-// of columns D0..D0+3 and D0+4..D0+7, spread by spread4.
+// Column D of the word (before the row end); tl/th: the R bits of D's
+// quad of columns, spread by spread4.
 template <int E, bool EDGE, int D>
 SS_HD void rwc_column(uint32_t &S, int &count, const RwcQ &q, uint32_t tl,
                       uint32_t th)
