@@ -246,8 +246,10 @@ int ss_filter_unequal(ss_ctx *ctx, const void *reads, const int64_t *read_off,
  * notes that this can only underestimate the exact count (more false
  * accepts, never a false reject); t >= m with y > e gives the exact filter.
  * Fixed-stride SS_FMT_PACKED2 pairs of length m; min(e, m-1) <= 31 (else
- * SS_ERR_UNSUPPORTED); t, y >= 1.  Returns SS_OK, SS_ERR_INVALID_ARG,
- * SS_ERR_UNSUPPORTED or SS_ERR_CUDA. */
+ * SS_ERR_UNSUPPORTED); t, y >= 1.  For m <= 256 the pairs are staged by
+ * bulk copies whose bounded waits, should one give up, latch SS_ERR_TIMEOUT
+ * for the next ss_sync.  Asynchronous on `stream`.  Returns SS_OK,
+ * SS_ERR_INVALID_ARG, SS_ERR_UNSUPPORTED or SS_ERR_CUDA. */
 int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
                       int format, int32_t m, int32_t e, int32_t t, int32_t y,
                       int64_t n, void *stream, uint8_t *out_accept,

@@ -283,25 +283,9 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
     const int64_t ntiles = (n + kRwThreads - 1) / kRwThreads;
     if (w16 <= kRwPipeMaxW16) {
         L.pipe = true;
-        RwPipeArgs &a = L.pa;
-        a.reads = reads;
-        a.refs = refs;
-        a.n = n;
-        a.ntiles = ntiles;
-        a.m = m;
-        a.w16 = w16;
-        a.stages = rw_pipe_stages(w16);
-        a.group = kRwGroup;
-        a.bulk = ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15) == 0;
-        a.neg1 = 0xffffffffu;
-        a.acc = acc;
-        a.obs = obs;
-        a.status = status;
-        L.smem = rw_pipe_smem(w16);
-        const int64_t groups = (ntiles + a.group - 1) / a.group;
-        if (groups > 0x7fffffff)
+        if (!rw_pipe_config(reads, refs, n, m, acc, obs, status, L.pa,
+                            L.grid, L.smem))
             return cudaErrorInvalidValue;
-        L.grid = (unsigned)groups;
     } else {
         L.pipe = false;
         RwUniformArgs &a = L.sa;
@@ -785,8 +769,8 @@ int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
     }
     SS_CUDA(ssk::launch_submaze((const uint32_t *)reads,
                                 (const uint32_t *)refs, n, m, e, t, y,
-                                out_accept, out_obstacles, ctx->sm_count,
-                                st));
+                                out_accept, out_obstacles, ctx->d_status,
+                                ctx->sm_count, st));
     ctx->counters.launches += 1;
     return SS_OK;
 }

@@ -66,7 +66,7 @@ cudaError_t launch_confusion(const uint8_t *acc, const int32_t *ed,
 cudaError_t launch_submaze(const uint32_t *reads, const uint32_t *refs,
                            int64_t n, int32_t m, int32_t E, int32_t t,
                            int32_t y, uint8_t *acc, int32_t *obs,
-                           int sm_count, cudaStream_t st);
+                           int *status, int sm_count, cudaStream_t st);
 
 // Pairs of different lengths (ss_unequal.cu).
 cudaError_t launch_unequal(const uint32_t *reads, const int64_t *read_off,

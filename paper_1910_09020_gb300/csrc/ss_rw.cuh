@@ -529,11 +529,44 @@ struct RwPipeArgs {
     int *status;
 };
 
-// Plain launch: uniform m <= 256 and E; CTA b routes tiles group * b ..
-// group * b + group - 1 of kRwThreads pairs each, from pair-major
-// shared-memory stages filled by bulk copies.
-template <int E>
-__global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
+// Arguments, grid and dynamic shared memory of a pipelined launch over n
+// pairs of length m (w16 <= kRwPipeMaxW16); false if the grid would exceed
+// 2^31 - 1 CTAs.
+inline bool rw_pipe_config(const uint32_t *reads, const uint32_t *refs,
+                           int64_t n, int32_t m, uint8_t *acc, int32_t *obs,
+                           int *status, RwPipeArgs &a, unsigned &grid,
+                           size_t &smem)
+{
+    const int w16 = (m + 15) / 16 > 1 ? (m + 15) / 16 : 1;
+    a.reads = reads;
+    a.refs = refs;
+    a.n = n;
+    a.ntiles = (n + kRwThreads - 1) / kRwThreads;
+    a.m = m;
+    a.w16 = w16;
+    a.stages = rw_pipe_stages(w16);
+    a.group = kRwGroup;
+    a.bulk = ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15) == 0;
+    a.neg1 = 0xffffffffu;
+    a.acc = acc;
+    a.obs = obs;
+    a.status = status;
+    smem = rw_pipe_smem(w16);
+    const int64_t groups = (a.ntiles + a.group - 1) / a.group;
+    grid = (unsigned)groups;
+    return groups <= 0x7fffffff;
+}
+
+// The pipelined tile loop of the uniform launches (m <= 256): CTA b takes
+// tiles group * b .. group * b + group - 1 of kRwThreads pairs each into
+// pair-major shared-memory stages filled by bulk copies, orders each tile by
+// the predicted cost (SORT), and routes pair u of the tile with
+// route(Q, R) -> min(count, E+1) over its staged words.  Reads past the
+// pair land in the stage (Q is followed by the tile's R words); R may be
+// read up to kRwPadWords words past.  Results go to the pair's own index.
+template <bool SORT, class Route>
+__device__ __forceinline__ void rw_pipe_run(const RwPipeArgs &a, int E,
+                                            Route route)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ __align__(8) uint64_t full[kRwMaxStages];
@@ -606,25 +639,34 @@ __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
             __syncthreads();
         }
         int u = t;
-        if (E >= 2)
+        if (SORT)
             u = rw_sort_tile(sQ, sR, w16, 1, w16, np, s_cnt, s_perm);
         if (t < np) {
-            const SmemSeqPad q{sQ + u * w16};
-            const SmemSeqPad r{sR + u * w16};
-            int cnt;
-            if constexpr (E >= kRwColsMinE && E <= 15)
-                cnt = rw_route_cols<E>(q, r, a.m);
-            else
-                cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
+            const int cnt =
+                route(SmemSeqPad{sQ + u * w16}, SmemSeqPad{sR + u * w16});
             a.acc[p0 + u] = (uint8_t)(cnt <= E);
             a.obs[p0 + u] = cnt;
         }
-        if (E >= 2 && t < 32)
+        if (SORT && t < 32)
             s_cnt[t] = 0;
         __syncthreads();  // stage s and the sort buffers are free again
         if (t == 0 && by_copy(tile_of(j + S)))
             issue(s, tile_of(j + S));
     }
+}
+
+// Plain launch: uniform m <= 256 and E, the exact greedy; the cost sort
+// from E = 2 (below, nearly every pair routes in one or two steps).
+template <int E>
+__global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
+{
+    rw_pipe_run<(E >= 2)>(a, E, [&](const SmemSeqPad &q,
+                                    const SmemSeqPad &r) {
+        if constexpr (E >= kRwColsMinE && E <= 15)
+            return rw_route_cols<E>(q, r, a.m);
+        else
+            return rw_route<E, true>(q, r, a.m, E, a.neg1);
+    });
 }
 
 }  // namespace ssk

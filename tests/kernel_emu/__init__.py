@@ -37,6 +37,7 @@ def load():
     P = ctypes.c_void_p
     lib.emu_rw_exact.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
     lib.emu_rw_cols.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
+    lib.emu_rw_staged.argtypes = [P, P] + [ctypes.c_int] * 3
     lib.emu_rw_runtime.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int]
     lib.emu_cw.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -56,5 +57,6 @@ def load():
                                      ctypes.c_int, ctypes.c_int]
     lib.emu_submaze_cols.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int]
+    lib.emu_submaze_staged.argtypes = [P, P] + [ctypes.c_int] * 5
     _lib = lib
     return lib

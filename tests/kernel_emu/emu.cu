@@ -17,39 +17,47 @@ using namespace ssk;
 
 namespace {
 
+// staged: the pair's words read as the pipelined kernel reads them from
+// its stage (SmemSeqPad: whatever follows the pair is read as is).
 template <int E>
-int exact_one(const uint32_t *q, const uint32_t *r, int m)
+int exact_one(const uint32_t *q, const uint32_t *r, int m, bool staged)
 {
     const int w16 = (m + 15) / 16;
+    if (staged)
+        return rw_route<E, true>(SmemSeqPad{q}, SmemSeqPad{r}, m, E,
+                                 0xffffffffu);
     return rw_route<E, true>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E,
                              0xffffffffu);
 }
 
 template <int... Es>
 int exact_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
-                   std::integer_sequence<int, Es...>)
+                   bool staged, std::integer_sequence<int, Es...>)
 {
     int out = -100;
-    ((E == Es ? (out = exact_one<Es>(q, r, m), 0) : 0), ...);
+    ((E == Es ? (out = exact_one<Es>(q, r, m, staged), 0) : 0), ...);
     return out;
 }
 
 template <int E>
-int cols_one(const uint32_t *q, const uint32_t *r, int m)
+int cols_one(const uint32_t *q, const uint32_t *r, int m, bool staged)
 {
     const int w16 = (m + 15) / 16;
-    if constexpr (E >= 1 && E <= 15)
+    if constexpr (E >= 1 && E <= 15) {
+        if (staged)
+            return rw_route_cols<E>(SmemSeqPad{q}, SmemSeqPad{r}, m);
         return rw_route_cols<E>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m);
-    else
+    } else {
         return -100;
+    }
 }
 
 template <int... Es>
 int cols_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
-                  std::integer_sequence<int, Es...>)
+                  bool staged, std::integer_sequence<int, Es...>)
 {
     int out = -100;
-    ((E == Es ? (out = cols_one<Es>(q, r, m), 0) : 0), ...);
+    ((E == Es ? (out = cols_one<Es>(q, r, m, staged), 0) : 0), ...);
     return out;
 }
 
@@ -92,6 +100,43 @@ int ed_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
     const int w16 = (m + 15) / 16;
     ((E == Es ? (out = ed_banded<Es>(q, r, m, w16), 0) : 0), ...);
     return out;
+}
+
+// Sub-maze approximate mode: t-column sub-mazes, at most y obstacles each.
+// form 0: the kernels' choice per class; 1: the row-wise routine at every
+// class; 2: the column walk at every class it supports (-2 above).
+template <class Seq>
+int submaze_form(const Seq &Q, const Seq &R, int m, int E, int t, int y,
+                 int form)
+{
+    const int Ee = eff_threshold(m, E);
+    if (form == 0) {
+        if (Ee <= 3)
+            return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
+        if (Ee <= 7)
+            return submaze_route_cols<7>(Q, R, m, E, t, y);
+        if (Ee <= 15)
+            return submaze_route_cols<15>(Q, R, m, E, t, y);
+        return submaze_route<31>(Q, R, m, E, t, y, 0xffffffffu);
+    }
+    if (form == 1) {
+        if (Ee <= 3)
+            return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
+        if (Ee <= 7)
+            return submaze_route<7>(Q, R, m, E, t, y, 0xffffffffu);
+        if (Ee <= 15)
+            return submaze_route<15>(Q, R, m, E, t, y, 0xffffffffu);
+        return submaze_route<31>(Q, R, m, E, t, y, 0xffffffffu);
+    }
+    if (Ee <= 1)
+        return submaze_route_cols<1>(Q, R, m, E, t, y);
+    if (Ee <= 3)
+        return submaze_route_cols<3>(Q, R, m, E, t, y);
+    if (Ee <= 7)
+        return submaze_route_cols<7>(Q, R, m, E, t, y);
+    if (Ee <= 15)
+        return submaze_route_cols<15>(Q, R, m, E, t, y);
+    return -2;
 }
 
 }  // namespace
@@ -166,55 +211,33 @@ int emu_unequal_form(const uint32_t *q, int mQ, const uint32_t *r, int mR,
     return -2;
 }
 
-// Sub-maze approximate mode: t-column sub-mazes, at most y obstacles each.
 int emu_submaze(const uint32_t *q, const uint32_t *r, int m, int E, int t,
                 int y)
 {
     const int w16 = (m + 15) / 16;
-    const GlobalSeq Q{q, w16}, R{r, w16};
-    const int Ee = eff_threshold(m, E);
-    if (Ee <= 3)
-        return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
-    if (Ee <= 7)
-        return submaze_route_cols<7>(Q, R, m, E, t, y);
-    if (Ee <= 15)
-        return submaze_route_cols<15>(Q, R, m, E, t, y);
-    return submaze_route<31>(Q, R, m, E, t, y, 0xffffffffu);
+    return submaze_form(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E, t, y, 0);
 }
 
-// The column-walk sub-maze routine at every class it supports (-2 above).
-int emu_submaze_cols(const uint32_t *q, const uint32_t *r, int m, int E, int t,
-                     int y)
-{
-    const int w16 = (m + 15) / 16;
-    const GlobalSeq Q{q, w16}, R{r, w16};
-    const int Ee = eff_threshold(m, E);
-    if (Ee <= 1)
-        return submaze_route_cols<1>(Q, R, m, E, t, y);
-    if (Ee <= 3)
-        return submaze_route_cols<3>(Q, R, m, E, t, y);
-    if (Ee <= 7)
-        return submaze_route_cols<7>(Q, R, m, E, t, y);
-    if (Ee <= 15)
-        return submaze_route_cols<15>(Q, R, m, E, t, y);
-    return -2;
-}
-
-// The row-wise sub-maze routine at every class (the kernel uses it for
-// EMAX = 3 and 31).
 int emu_submaze_rows(const uint32_t *q, const uint32_t *r, int m, int E, int t,
                      int y)
 {
     const int w16 = (m + 15) / 16;
-    const GlobalSeq Q{q, w16}, R{r, w16};
-    const int Ee = eff_threshold(m, E);
-    if (Ee <= 3)
-        return submaze_route<3>(Q, R, m, E, t, y, 0xffffffffu);
-    if (Ee <= 7)
-        return submaze_route<7>(Q, R, m, E, t, y, 0xffffffffu);
-    if (Ee <= 15)
-        return submaze_route<15>(Q, R, m, E, t, y, 0xffffffffu);
-    return submaze_route<31>(Q, R, m, E, t, y, 0xffffffffu);
+    return submaze_form(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E, t, y, 1);
+}
+
+int emu_submaze_cols(const uint32_t *q, const uint32_t *r, int m, int E, int t,
+                     int y)
+{
+    const int w16 = (m + 15) / 16;
+    return submaze_form(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m, E, t, y, 2);
+}
+
+// The same over staged words as the pipelined kernels read them: whatever
+// follows the pair's words (another pair, the R plane) is read as is.
+int emu_submaze_staged(const uint32_t *q, const uint32_t *r, int m, int E,
+                       int t, int y, int form)
+{
+    return submaze_form(SmemSeqPad{q}, SmemSeqPad{r}, m, E, t, y, form);
 }
 
 // Banded edit distance of the accuracy harness: min(ED, E+1), E <= 31.
@@ -226,13 +249,26 @@ int emu_ed(const uint32_t *q, const uint32_t *r, int m, int E)
 // Plain-kernel routine with compile-time E (0..31).
 int emu_rw_exact(const uint32_t *q, const uint32_t *r, int m, int E)
 {
-    return exact_dispatch(E, q, r, m, std::make_integer_sequence<int, 32>{});
+    return exact_dispatch(E, q, r, m, false,
+                          std::make_integer_sequence<int, 32>{});
 }
 
 // Column-at-a-time routine (E = 1..15).
 int emu_rw_cols(const uint32_t *q, const uint32_t *r, int m, int E)
 {
-    return cols_dispatch(E, q, r, m, std::make_integer_sequence<int, 16>{});
+    return cols_dispatch(E, q, r, m, false,
+                         std::make_integer_sequence<int, 16>{});
+}
+
+// Both, over staged words (cols: the column walk, else row-wise).
+int emu_rw_staged(const uint32_t *q, const uint32_t *r, int m, int E,
+                  int cols)
+{
+    if (cols)
+        return cols_dispatch(E, q, r, m, true,
+                             std::make_integer_sequence<int, 16>{});
+    return exact_dispatch(E, q, r, m, true,
+                          std::make_integer_sequence<int, 32>{});
 }
 
 // Bucketed row-wise routine: runtime E <= EMAX (1, 3, 7, 15, 31).

@@ -47,7 +47,7 @@ def test_submaze_matches_oracle(F, m, t, y):
     n = 1500
     reads, refs = synth.pairs_fixed(310 + m + t, 0, n, m,
                                     synth.rate_recipe(0.1))
-    for E in (0, 3, 9, 31):
+    for E in (0, 3, 5, 9, 31):
         acc, obs = run(F, reads, refs, E, t, y)
         oacc, oobs = oracle_submaze(reads, refs, E, t, y)
         assert_same(acc, obs, oacc, oobs, f"submaze m={m} E={E} t={t} y={y}")
@@ -72,6 +72,28 @@ def test_submaze_never_exceeds_exact_and_full_span_is_exact(F):
         oacc, oobs = oracle_submaze(reads[idx], refs[idx], E, 8, 3)
         assert_same(sacc.cpu().numpy()[idx], so[idx], oacc, oobs,
                     f"full-size sample E={E}")
+
+
+def test_submaze_unaligned_packed_input(F):
+    """Packed input not 16-byte aligned: the staged launch loads its tiles
+    without bulk copies."""
+    torch = torch_cuda()
+    n, m = 20_000, 100
+    reads, refs = synth.pairs_fixed(67, 0, n, m, synth.SHORT_POISSON)
+    w16 = binding.ss_packed_words(m)
+    q = F.pack(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack(to_dev(refs.reshape(-1)), m=m, n=n)
+    qb = torch.zeros(n * w16 + 4, dtype=torch.int32, device="cuda")
+    rb = torch.zeros(n * w16 + 4, dtype=torch.int32, device="cuda")
+    qb[1:1 + n * w16] = q
+    rb[3:3 + n * w16] = r
+    for E in (2, 6, 10):
+        acc, obs = F.filter_submaze(qb[1:1 + n * w16], rb[3:3 + n * w16],
+                                    m=m, e=E, t=8, y=3, n=n)
+        F.sync()
+        oacc, oobs = oracle_submaze(reads, refs, E, 8, 3)
+        assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                    f"unaligned E={E}")
 
 
 def test_submaze_edges(F):

@@ -156,6 +156,39 @@ def test_submaze_matches_oracle(emu, t):
                 assert got in (want, -2), ("cols", m, E, t, y)
 
 
+@pytest.mark.parametrize("m", [1, 7, 16, 17, 31, 32, 33, 63, 64, 65, 100,
+                               127, 128, 150, 200, 256])
+def test_staged_reads_ignore_what_follows(emu, m):
+    """The pipelined kernels route a pair in place in its shared-memory
+    stage, where the words after it are the next pair's (or the tile's R
+    words): the plain and sub-maze routines must give the oracle's result
+    whatever those words hold."""
+    rng = np.random.default_rng(m)
+    w16 = (m + 15) // 16
+
+    def staged(seq):
+        junk = rng.integers(0, 2**32, 8, dtype=np.uint64).astype(np.uint32)
+        return np.concatenate([oracle.pack_reference(seq)[:w16], junk])
+
+    for Q, R in pairs(2100 + m, 10, m, synth.rate_recipe(0.12)):
+        q, r = staged(Q), staged(R)
+        for E in range(32):
+            want = oracle.filter_pair(Q, R, E).obstacles
+            assert emu.emu_rw_staged(P(q), P(r), m, E, 0) == want, (m, E)
+            if 1 <= E <= 15:
+                got = emu.emu_rw_staged(P(q), P(r), m, E, 1)
+                assert got == want, ("cols", m, E)
+        for E in (0, 2, 5, 9, 15, 31):
+            for t in (5, 8, 32):
+                for y in (1, 3):
+                    want = oracle.filter_submaze(Q, R, E, t, y).obstacles
+                    for form in (0, 1, 2):
+                        got = emu.emu_submaze_staged(P(q), P(r), m, E, t, y,
+                                                     form)
+                        assert got == want or (form == 2 and got == -2), (
+                            m, E, t, y, form)
+
+
 CODE = {c: i for i, c in enumerate(b"ACGT")}
 CODE.update({c: i for i, c in enumerate(b"acgt")})
 
