@@ -60,14 +60,22 @@ __global__ void __launch_bounds__(kPackThreads, 8)
                  int *status)
 {
     __shared__ uint32_t code[kPackChunks];
+    __shared__ int64_t s_pair[2];
     const int64_t total = n * (int64_t)w16;
     const int64_t g0 = (int64_t)blockIdx.x * kPackWords;
     if (g0 >= total)
         return;
     const int64_t g1 = min(g0 + (int64_t)kPackWords, total);  // exclusive
-    const int64_t pa = g0 / w16;
+    // the pairs of the first and last word: two 64-bit divisions, done by
+    // one thread (each costs a warp tens of instructions)
+    if (threadIdx.x == 0) {
+        s_pair[0] = g0 / w16;
+        s_pair[1] = (g1 - 1) / w16;
+    }
+    __syncthreads();
+    const int64_t pa = s_pair[0];
     const int wa = (int)(g0 - pa * w16);
-    const int64_t pb = (g1 - 1) / w16;
+    const int64_t pb = s_pair[1];
     const int wb = (int)(g1 - 1 - pb * w16);
     const int64_t b0 = pa * m + 16 * (int64_t)wa;      // first byte
     const int64_t b1 = pb * m + min(16 * (wb + 1), m);  // end byte

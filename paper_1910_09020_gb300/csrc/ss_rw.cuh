@@ -24,7 +24,7 @@
 // Three launch forms share rw_route():
 //  * k_rw_uniform<E>: the plain launch (uniform m and E, m <= 256).  Each
 //    CTA routes a group of kRwGroup consecutive tiles of 128 pairs; a ring
-//    of 2-3 shared-memory stages is filled by bulk asynchronous copies (one
+//    of two shared-memory stages is filled by bulk asynchronous copies (one
 //    per sequence per tile, completing on an mbarrier), so the next tiles'
 //    HBM reads are in flight while the current tile is routed.  Groups, not
 //    a persistent grid: the block scheduler hands out groups as SMs free
@@ -497,19 +497,20 @@ __global__ void __launch_bounds__(128)
 // from E = kRwColsMinE to 15, and row-wise (rw_route) otherwise.
 constexpr int kRwColsMinE = 6;
 
-constexpr int kRwMaxStages = 2;
 constexpr int kRwGroup = 8;                  // tiles per CTA
 constexpr int kRwPipeMaxW16 = 16;            // m <= 256
 constexpr uint64_t kRwWaitNs = 2000000000ull;  // 2 s per stage wait
 
-// Stages and dynamic shared memory of the pipelined kernel for w16 words.
-// Two stages: a third adds shared memory (fewer resident CTAs) and measured
-// no faster; more tiles per CTA than 8 unbalance the CTAs' routing cost.
-SS_HD int rw_pipe_stages(int) { return 2; }
+// Shared-memory stages of the pipelined kernel, a compile-time constant so
+// that a tile's stage and barrier phase are bit operations.  Two stages: a
+// third adds shared memory (fewer resident CTAs) and measured no faster;
+// more tiles per CTA than 8 unbalance the CTAs' routing cost.
+constexpr int kRwStages = 2;
 constexpr int kRwPadWords = 4;  // read past the last pair of the ring
+// Dynamic shared memory of the pipelined kernel for w16 words per sequence.
 SS_HD size_t rw_pipe_smem(int w16)
 {
-    return ((size_t)rw_pipe_stages(w16) * 2u * kRwThreads * (size_t)w16 +
+    return ((size_t)kRwStages * 2u * kRwThreads * (size_t)w16 +
             kRwPadWords) * 4u;
 }
 
@@ -520,7 +521,6 @@ struct RwPipeArgs {
     int64_t ntiles;         // ceil(n / kRwThreads)
     int32_t m;
     int32_t w16;
-    int32_t stages;         // 1..kRwMaxStages
     int32_t bulk;           // inputs 16-byte aligned: full tiles bulk-copied
     int32_t group;          // tiles per CTA
     uint32_t neg1;          // 0xffffffff (see rw_route)
@@ -544,7 +544,6 @@ inline bool rw_pipe_config(const uint32_t *reads, const uint32_t *refs,
     a.ntiles = (n + kRwThreads - 1) / kRwThreads;
     a.m = m;
     a.w16 = w16;
-    a.stages = rw_pipe_stages(w16);
     a.group = kRwGroup;
     a.bulk = ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15) == 0;
     a.neg1 = 0xffffffffu;
@@ -569,12 +568,12 @@ __device__ __forceinline__ void rw_pipe_run(const RwPipeArgs &a, int E,
                                             Route route)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ __align__(8) uint64_t full[kRwMaxStages];
+    __shared__ __align__(8) uint64_t full[kRwStages];
     __shared__ int s_cnt[32];
     __shared__ uint8_t s_perm[kRwThreads];
     const int t = threadIdx.x;
     const int w16 = a.w16;
-    const int S = a.stages;
+    constexpr int S = kRwStages;
     const uint32_t tile_words = (uint32_t)kRwThreads * (uint32_t)w16;
     const uint32_t tile_bytes = tile_words * 4u;
     // tile j < group of this CTA is global tile group * blockIdx.x + j; it
@@ -605,26 +604,26 @@ __device__ __forceinline__ void rw_pipe_run(const RwPipeArgs &a, int E,
         for (int j = 0; j < S; ++j)
             if (by_copy(tile_of(j)))
                 issue(j, tile_of(j));
-    for (int64_t j = 0;; ++j) {
+    for (int j = 0;; ++j) {
         const int64_t tile = tile_of(j);
         if (tile >= a.ntiles)
             break;
-        const int s = (int)(j % S);
+        const int s = (int)((uint32_t)j % S);
         uint32_t *sQ = smem + (size_t)s * 2u * tile_words;
         uint32_t *sR = sQ + tile_words;
         const int64_t p0 = tile * kRwThreads;
         const int np = (int)min((int64_t)kRwThreads, a.n - p0);
         if (by_copy(tile)) {
             const bool ok = mbar_wait_bounded(
-                &full[s], (uint32_t)((j / S) & 1), kRwWaitNs);
+                &full[s], ((uint32_t)j / S) & 1u, kRwWaitNs);
             if (__syncthreads_or(!ok)) {
                 if (t == 0) {
                     atomicOr(a.status, kStatusTimeout);
                     // drain the copies still in flight into this CTA
-                    for (int64_t k = j; k < j + S; ++k)
+                    for (int k = j; k < j + S; ++k)
                         if (by_copy(tile_of(k)))
-                            mbar_wait_bounded(&full[k % S],
-                                              (uint32_t)((k / S) & 1),
+                            mbar_wait_bounded(&full[(uint32_t)k % S],
+                                              ((uint32_t)k / S) & 1u,
                                               kRwWaitNs);
                 }
                 return;
