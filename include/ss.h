@@ -22,7 +22,9 @@
  * kernels (a non-ACGT byte, a negative per-pair length or threshold) are
  * latched in the context and returned by ss_sync().
  *
- * Threading: a context may be used by one host thread at a time.
+ * Threading: a context may be used by one host thread at a time; contexts
+ * (and servers) may be created and used from several host threads at once,
+ * on one device or several.
  */
 #ifndef SS_H
 #define SS_H

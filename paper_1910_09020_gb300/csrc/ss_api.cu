@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -254,12 +255,26 @@ ssk::PairSet make_pairs(const void *reads, const void *refs,
 namespace ssk {
 
 namespace {
-bool g_rw_ready = false;
+// Set once per device by rw_init (under bucket_init's lock).
+std::atomic<bool> g_rw_ready[kMaxDevices];
+
+bool rw_ready_here()
+{
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return d >= 0 && d < kMaxDevices &&
+           g_rw_ready[d].load(std::memory_order_acquire);
+}
 }  // namespace
 
-cudaError_t rw_init()
+cudaError_t rw_init(int device)
 {
-    if (g_rw_ready)
+    if (device < 0 || device >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    if (g_rw_ready[device].load(std::memory_order_acquire))
         return cudaSuccess;
     cudaError_t e;
     if ((e = rw_init_e0()) != cudaSuccess ||
@@ -267,7 +282,7 @@ cudaError_t rw_init()
         (e = rw_init_e2()) != cudaSuccess ||
         (e = rw_init_e3()) != cudaSuccess)
         return e;
-    g_rw_ready = true;
+    g_rw_ready[device].store(true, std::memory_order_release);
     return cudaSuccess;
 }
 
@@ -276,7 +291,7 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
                               uint8_t *acc, int32_t *obs, int *status,
                               cudaStream_t st)
 {
-    if (!g_rw_ready || E < 0 || E > kRwMaxE)
+    if (E < 0 || E > kRwMaxE || !rw_ready_here())
         return cudaErrorInvalidValue;
     RwLaunch L{};
     const int w16 = std::max((m + 15) / 16, 1);
@@ -376,7 +391,7 @@ int ss_create(ss_ctx **out, int device, size_t workspace_bytes)
         return SS_ERR_CUDA;
     }
     ctx->sm_count = prop.multiProcessorCount;
-    if (ssk::bucket_init(ctx->sm_count) != cudaSuccess) {
+    if (ssk::bucket_init() != cudaSuccess) {
         (void)cudaGetLastError();
         ss_destroy(ctx);
         return SS_ERR_CUDA;

@@ -11,7 +11,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #include "ss_bucket.cuh"
 #include "ss_cw.cuh"
@@ -215,20 +217,38 @@ int occupancy_per_sm(KernelT kernel, int threads, size_t smem)
     return per_sm;
 }
 
-// Resident CTAs per SM of every persistent kernel, computed once (outside
-// any stream capture); a launch over `sm_share` SMs uses per_sm * sm_share
-// CTAs, so several bucketed passes can share the GPU side by side.
+// Resident CTAs per SM of every persistent kernel, computed once per device
+// (outside any stream capture) together with the kernels' shared-memory
+// attributes, which are per device; a launch over `sm_share` SMs uses
+// per_sm * sm_share CTAs, so several bucketed passes can share the GPU side
+// by side.  Written once under g_init_mu before `ready` is released; read
+// only by threads that saw it set.
 struct LaunchCfg {
     int rw[kRwClasses];
     int cw[3][kClasses];  // [subgrid 4/8/16][class]
-    bool ready = false;
+    std::atomic<bool> ready{false};
 };
-LaunchCfg g_cfg;
+LaunchCfg g_cfg[kMaxDevices];
+std::mutex g_init_mu;
+
+// The current device's configuration, or nullptr before bucket_init.
+const LaunchCfg *launch_cfg()
+{
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (d < 0 || d >= kMaxDevices ||
+        !g_cfg[d].ready.load(std::memory_order_acquire))
+        return nullptr;
+    return &g_cfg[d];
+}
 
 int kidx(int k) { return k == 4 ? 0 : k == 16 ? 2 : 1; }
 
 template <int K>
-cudaError_t init_cw(int sm_count)
+cudaError_t init_cw(LaunchCfg &cfg)
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_cw_warp<K>,
@@ -241,26 +261,27 @@ cudaError_t init_cw(int sm_count)
     for (int c = 0; c < kCwwClasses; ++c) {
         const int cls = kRwClasses + c;
         const size_t smem = (size_t)4 * cw_class_slice_words(cls) * 4;
-        g_cfg.cw[kidx(K)][cls] = occupancy_per_sm(k_cw_warp<K>, 128, smem);
+        cfg.cw[kidx(K)][cls] = occupancy_per_sm(k_cw_warp<K>, 128, smem);
     }
     for (int w = 0; w < kCwcWidths; ++w)
         for (int b = 0; b < kCwcMbounds; ++b) {
             const int cls = cwc_class(w, b);
             const size_t smem = (size_t)cw_class_slice_words(cls) * 4;
-            g_cfg.cw[kidx(K)][cls] =
+            cfg.cw[kidx(K)][cls] =
                 occupancy_per_sm(k_cw_cta<K>, cwc_width(w), smem);
         }
     return cudaSuccess;
 }
 
 template <int K>
-cudaError_t launch_cw_classes(CwArgs a, int sm_share, cudaStream_t st)
+cudaError_t launch_cw_classes(const LaunchCfg &cfg, CwArgs a, int sm_share,
+                              cudaStream_t st)
 {
     for (int c = 0; c < kCwwClasses; ++c) {
         a.cls = kRwClasses + c;
         a.slice_words = cw_class_slice_words(a.cls);
         const size_t smem = (size_t)4 * a.slice_words * 4;
-        k_cw_warp<K><<<g_cfg.cw[kidx(K)][a.cls] * sm_share, 128, smem, st>>>(
+        k_cw_warp<K><<<cfg.cw[kidx(K)][a.cls] * sm_share, 128, smem, st>>>(
             a);
     }
     for (int w = 0; w < kCwcWidths; ++w)
@@ -268,7 +289,7 @@ cudaError_t launch_cw_classes(CwArgs a, int sm_share, cudaStream_t st)
             a.cls = cwc_class(w, b);
             a.slice_words = cw_class_slice_words(a.cls);
             const size_t smem = (size_t)a.slice_words * 4;
-            k_cw_cta<K><<<g_cfg.cw[kidx(K)][a.cls] * sm_share, cwc_width(w),
+            k_cw_cta<K><<<cfg.cw[kidx(K)][a.cls] * sm_share, cwc_width(w),
                           smem, st>>>(a);
         }
     return cudaGetLastError();
@@ -276,23 +297,30 @@ cudaError_t launch_cw_classes(CwArgs a, int sm_share, cudaStream_t st)
 
 }  // namespace
 
-cudaError_t bucket_init(int sm_count)
+cudaError_t bucket_init()
 {
-    if (g_cfg.ready)
-        return cudaSuccess;
-    cudaError_t e = rw_init();
+    int d = -1;
+    cudaError_t e = cudaGetDevice(&d);
     if (e != cudaSuccess)
         return e;
-    g_cfg.rw[0] = occupancy_per_sm(k_rw_bucket<1>, 128, 0);
-    g_cfg.rw[1] = occupancy_per_sm(k_rw_bucket<3>, 128, 0);
-    g_cfg.rw[2] = occupancy_per_sm(k_rw_bucket<7>, 128, 0);
-    g_cfg.rw[3] = occupancy_per_sm(k_rw_bucket<15>, 128, 0);
-    g_cfg.rw[4] = occupancy_per_sm(k_rw_bucket<31>, 128, 0);
-    if ((e = init_cw<4>(sm_count)) != cudaSuccess ||
-        (e = init_cw<8>(sm_count)) != cudaSuccess ||
-        (e = init_cw<16>(sm_count)) != cudaSuccess)
+    if (d < 0 || d >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_init_mu);
+    LaunchCfg &cfg = g_cfg[d];
+    if (cfg.ready.load(std::memory_order_relaxed))
+        return cudaSuccess;
+    if ((e = rw_init(d)) != cudaSuccess)
         return e;
-    g_cfg.ready = true;
+    cfg.rw[0] = occupancy_per_sm(k_rw_bucket<1>, 128, 0);
+    cfg.rw[1] = occupancy_per_sm(k_rw_bucket<3>, 128, 0);
+    cfg.rw[2] = occupancy_per_sm(k_rw_bucket<7>, 128, 0);
+    cfg.rw[3] = occupancy_per_sm(k_rw_bucket<15>, 128, 0);
+    cfg.rw[4] = occupancy_per_sm(k_rw_bucket<31>, 128, 0);
+    if ((e = init_cw<4>(cfg)) != cudaSuccess ||
+        (e = init_cw<8>(cfg)) != cudaSuccess ||
+        (e = init_cw<16>(cfg)) != cudaSuccess)
+        return e;
+    cfg.ready.store(true, std::memory_order_release);
     return cudaSuccess;
 }
 
@@ -320,26 +348,27 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
     if ((e = cudaEventRecord(fork, st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess)
         return e;
-    if (!g_cfg.ready)
+    const LaunchCfg *cfg = launch_cfg();
+    if (!cfg)
         return cudaErrorNotReady;
     const int sh = sm_count;  // persistent grids span this many SMs
     CwArgs a{ps, ws, 0, 0};
     a.cls = 0;
-    k_rw_bucket<1><<<g_cfg.rw[0] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<1><<<cfg->rw[0] * sh, 128, 0, st>>>(a);
     a.cls = 1;
-    k_rw_bucket<3><<<g_cfg.rw[1] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<3><<<cfg->rw[1] * sh, 128, 0, st>>>(a);
     a.cls = 2;
-    k_rw_bucket<7><<<g_cfg.rw[2] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<7><<<cfg->rw[2] * sh, 128, 0, st>>>(a);
     a.cls = 3;
-    k_rw_bucket<15><<<g_cfg.rw[3] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<15><<<cfg->rw[3] * sh, 128, 0, st>>>(a);
     a.cls = 4;
-    k_rw_bucket<31><<<g_cfg.rw[4] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<31><<<cfg->rw[4] * sh, 128, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     switch (tp.cw_subgrid) {
-    case 4: e = launch_cw_classes<4>(a, sh, side); break;
-    case 16: e = launch_cw_classes<16>(a, sh, side); break;
-    default: e = launch_cw_classes<8>(a, sh, side); break;
+    case 4: e = launch_cw_classes<4>(*cfg, a, sh, side); break;
+    case 16: e = launch_cw_classes<16>(*cfg, a, sh, side); break;
+    default: e = launch_cw_classes<8>(*cfg, a, sh, side); break;
     }
     if (e != cudaSuccess)
         return e;
@@ -358,7 +387,8 @@ cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
 {
     if (ps.n <= 0)
         return cudaSuccess;
-    if (!g_cfg.ready)
+    const LaunchCfg *cfg = launch_cfg();
+    if (!cfg)
         return cudaErrorNotReady;
     cudaError_t e;
     const TuneParams tp;
@@ -378,18 +408,18 @@ cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
     const int sh = sm_count;
     CwArgs a{ps, ws, 0, 0};
     a.cls = 0;
-    k_rw_bucket<1><<<g_cfg.rw[0] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<1><<<cfg->rw[0] * sh, 128, 0, st>>>(a);
     a.cls = 1;
-    k_rw_bucket<3><<<g_cfg.rw[1] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<3><<<cfg->rw[1] * sh, 128, 0, st>>>(a);
     a.cls = 2;
-    k_rw_bucket<7><<<g_cfg.rw[2] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<7><<<cfg->rw[2] * sh, 128, 0, st>>>(a);
     a.cls = 3;
-    k_rw_bucket<15><<<g_cfg.rw[3] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<15><<<cfg->rw[3] * sh, 128, 0, st>>>(a);
     a.cls = 4;
-    k_rw_bucket<31><<<g_cfg.rw[4] * sh, 128, 0, st>>>(a);
+    k_rw_bucket<31><<<cfg->rw[4] * sh, 128, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    return launch_cw_classes<8>(a, sh, st);
+    return launch_cw_classes<8>(*cfg, a, sh, st);
 }
 
 }  // namespace ssk

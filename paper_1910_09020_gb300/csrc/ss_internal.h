@@ -28,9 +28,11 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
                               const uint32_t *refs, int64_t n, int32_t m,
                               uint8_t *acc, int32_t *obs, int *status,
                               cudaStream_t st);
-// Kernel attributes of the plain launches (once per process,
-// before any capture; called by bucket_init).
-cudaError_t rw_init();
+// Devices the one-time set-up below keeps state for (ids 0..63).
+constexpr int kMaxDevices = 64;
+// Kernel attributes of the plain launches on device `device` (the current
+// one; before any capture; called by bucket_init under its lock).
+cudaError_t rw_init(int device);
 
 // K2 + K4: bucketed persistent form of a mixed batch.
 size_t bucket_ws_bytes(int64_t n);
@@ -38,9 +40,10 @@ BucketWs bucket_ws_at(void *base, int64_t n);
 int cw_class_slice_words(int cls);
 cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
                                        int *status, cudaStream_t st);
-// Kernel attributes and persistent grid sizes (once per process, called by
-// ss_create before any capture).
-cudaError_t bucket_init(int sm_count);
+// Kernel attributes and persistent grid sizes of the current device, once
+// per device (called by ss_create, ss_server_start and the allocation-free
+// entry before any capture; safe to call from several host threads).
+cudaError_t bucket_init();
 cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
                             const TuneParams &tp, int *status, int sm_count,
                             cudaStream_t st, cudaStream_t side,

@@ -33,7 +33,7 @@ constexpr size_t kStatusOffset = kScratchBytes - 256;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
+using ssk::kMaxDevices;
 struct DeviceSetup {
     bool ready = false;
     void *scratch = nullptr;
@@ -60,10 +60,7 @@ int scratch_of_current_device(void **out)
             (void)cudaGetLastError();
             return SS_ERR_CUDA;
         }
-        int sm_count = 0;
-        if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount,
-                                   dev) != cudaSuccess ||
-            ssk::bucket_init(sm_count) != cudaSuccess) {
+        if (ssk::bucket_init() != cudaSuccess) {
             (void)cudaGetLastError();
             return SS_ERR_CUDA;
         }

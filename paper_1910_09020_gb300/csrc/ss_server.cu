@@ -443,7 +443,7 @@ int ss_server_create(ss_server **out, int device, size_t hbm_budget_bytes,
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     (void)cudaGetLastError();
-    if (ssk::bucket_init(s->sm_count) != cudaSuccess) {
+    if (ssk::bucket_init() != cudaSuccess) {
         delete s;
         return SS_ERR_CUDA;
     }
