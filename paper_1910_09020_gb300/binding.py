@@ -244,6 +244,45 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+def _dptr(t, device: int, what: str, nbytes: int = 0) -> int:
+    """Address of a contiguous CUDA tensor on `device` holding at least
+    `nbytes` (0 for None).  The C ABI takes plain device pointers and cannot
+    check them: a host tensor, another device's tensor or a short buffer
+    would be read or written out of bounds by the kernels."""
+    if t is None:
+        return 0
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: expected a CUDA tensor on cuda:{device}")
+    if t.device.index != device:
+        raise ValueError(f"{what}: tensor on cuda:{t.device.index}, "
+                         f"context on cuda:{device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError(f"{what}: {have} bytes, the call needs {nbytes}")
+    return int(t.data_ptr())
+
+
+def _hptr(t, what: str, nbytes: int = 0) -> int:
+    """Address of a contiguous host tensor holding at least `nbytes`."""
+    if getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: expected a host (CPU) tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: tensor must be contiguous")
+    have = t.numel() * t.element_size()
+    if have < nbytes:
+        raise ValueError(f"{what}: {have} bytes, the call needs {nbytes}")
+    return int(t.data_ptr())
+
+
+def _seq_bytes(fmt: int, n: int, m: int) -> int:
+    """Bytes of n fixed-stride sequences of m bases in format fmt."""
+    if n <= 0 or m <= 0:
+        return 0
+    return n * m if fmt == SS_FMT_ASCII else n * 4 * ss_packed_words(m)
+
+
 def _stream_handle(stream) -> int:
     import torch
     if stream is None:
@@ -286,8 +325,17 @@ class Filter:
                                   device=ascii.device)
         else:
             n = lengths.shape[0]
-        rc = ss_pack(self.ctx, _ptr(ascii), _ptr(offsets), _ptr(lengths), m,
-                     n, _ptr(out), _ptr(out_offsets), _stream_handle(stream))
+        d = self.device
+        fixed = offsets is None
+        rc = ss_pack(self.ctx,
+                     _dptr(ascii, d, "ascii",
+                           _seq_bytes(SS_FMT_ASCII, n, m) if fixed else 0),
+                     _dptr(offsets, d, "offsets", 8 * n),
+                     _dptr(lengths, d, "lengths", 4 * n), m, n,
+                     _dptr(out, d, "out",
+                           _seq_bytes(SS_FMT_PACKED2, n, m) if fixed else 0),
+                     _dptr(out_offsets, d, "out_offsets", 8 * n),
+                     _stream_handle(stream))
         _check(rc, "ss_pack")
         return out
 
@@ -304,10 +352,16 @@ class Filter:
             out_accept = torch.empty(n, dtype=torch.uint8, device=dev)
         if out_obstacles is None:
             out_obstacles = torch.empty(n, dtype=torch.int32, device=dev)
-        rc = ss_filter_batch(self.ctx, _ptr(reads), _ptr(refs), fmt,
-                             _ptr(offsets), _ptr(lengths), m, _ptr(E), e, n,
-                             flags, _stream_handle(stream), _ptr(out_accept),
-                             _ptr(out_obstacles))
+        d = self.device
+        seq = _seq_bytes(fmt, n, m) if offsets is None else 0
+        rc = ss_filter_batch(self.ctx, _dptr(reads, d, "reads", seq),
+                             _dptr(refs, d, "refs", seq), fmt,
+                             _dptr(offsets, d, "offsets", 8 * n),
+                             _dptr(lengths, d, "lengths", 4 * n), m,
+                             _dptr(E, d, "E", 4 * n), e, n, flags,
+                             _stream_handle(stream),
+                             _dptr(out_accept, d, "out_accept", n),
+                             _dptr(out_obstacles, d, "out_obstacles", 4 * n))
         _check(rc, "ss_filter_batch")
         if sync:
             self.sync(stream)
@@ -328,9 +382,13 @@ class Filter:
         if out_obstacles is None:
             out_obstacles = torch.empty((len(es), n), dtype=torch.int32,
                                         pin_memory=True)
-        rc = ss_filter_host(self.ctx, _ptr(reads), _ptr(refs), fmt, m,
-                            ctypes.addressof(e_arr), len(es), n,
-                            _ptr(out_accept), _ptr(out_obstacles))
+        seq = _seq_bytes(fmt, n, m)
+        k = len(es)
+        rc = ss_filter_host(self.ctx, _hptr(reads, "reads", seq),
+                            _hptr(refs, "refs", seq), fmt, m,
+                            ctypes.addressof(e_arr), k, n,
+                            _hptr(out_accept, "out_accept", k * n),
+                            _hptr(out_obstacles, "out_obstacles", 4 * k * n))
         _check(rc, "ss_filter_host")
         if isinstance(e, int):
             return out_accept[0], out_obstacles[0]
@@ -349,10 +407,17 @@ class Filter:
         if out_obstacles is None:
             out_obstacles = torch.empty(n, dtype=torch.int32,
                                         device=reads.device)
-        ms = ss_autotune(self.ctx, _ptr(reads), _ptr(refs), _ptr(offsets),
-                         _ptr(lengths), m, _ptr(E), e, n,
-                         _stream_handle(stream), _ptr(out_accept),
-                         _ptr(out_obstacles), reps)
+        d = self.device
+        seq = _seq_bytes(SS_FMT_PACKED2, n, m) if offsets is None else 0
+        ms = ss_autotune(self.ctx, _dptr(reads, d, "reads", seq),
+                         _dptr(refs, d, "refs", seq),
+                         _dptr(offsets, d, "offsets", 8 * n),
+                         _dptr(lengths, d, "lengths", 4 * n), m,
+                         _dptr(E, d, "E", 4 * n), e, n,
+                         _stream_handle(stream),
+                         _dptr(out_accept, d, "out_accept", n),
+                         _dptr(out_obstacles, d, "out_obstacles", 4 * n),
+                         reps)
         rmax, k = ss_get_tuning(self.ctx)
         return rmax, k, ms
 
@@ -366,9 +431,13 @@ class Filter:
         n = reads.shape[0] if n is None else n
         if out is None:
             out = torch.empty(n, dtype=torch.int32, device=reads.device)
+        d = self.device
+        seq = _seq_bytes(SS_FMT_PACKED2, n, m)
         rc = load().ss_edit_distance_banded(
-            self.ctx, _ptr(reads) or None, _ptr(refs) or None, SS_FMT_PACKED2,
-            m, e, n, _stream_handle(stream) or None, _ptr(out) or None)
+            self.ctx, _dptr(reads, d, "reads", seq) or None,
+            _dptr(refs, d, "refs", seq) or None, SS_FMT_PACKED2, m, e, n,
+            _stream_handle(stream) or None,
+            _dptr(out, d, "out", 4 * n) or None)
         _check(rc, "ss_edit_distance_banded")
         return out
 
@@ -380,7 +449,10 @@ class Filter:
         n = reads.shape[0] if n is None else n
         acc = torch.empty(max(n, 1), dtype=torch.uint8, device=reads.device)
         obs = torch.empty(max(n, 1), dtype=torch.int32, device=reads.device)
-        rc = load().ss_filter_submaze(self.ctx, _ptr(reads), _ptr(refs),
+        d = self.device
+        seq = _seq_bytes(SS_FMT_PACKED2, n, m)
+        rc = load().ss_filter_submaze(self.ctx, _dptr(reads, d, "reads", seq),
+                                      _dptr(refs, d, "refs", seq),
                                       SS_FMT_PACKED2, m, e, t, y, n,
                                       _stream_handle(stream) or None,
                                       _ptr(acc), _ptr(obs))
@@ -396,10 +468,14 @@ class Filter:
         dev = read_len.device
         acc = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
         obs = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        d = self.device
         rc = load().ss_filter_unequal(
-            self.ctx, _ptr(reads), _ptr(read_off), _ptr(read_len), _ptr(refs),
-            _ptr(ref_off), _ptr(ref_len), _ptr(E), e, n,
-            _stream_handle(stream) or None, _ptr(acc), _ptr(obs))
+            self.ctx, _dptr(reads, d, "reads"),
+            _dptr(read_off, d, "read_off", 8 * n),
+            _dptr(read_len, d, "read_len", 4 * n), _dptr(refs, d, "refs"),
+            _dptr(ref_off, d, "ref_off", 8 * n),
+            _dptr(ref_len, d, "ref_len", 4 * n), _dptr(E, d, "E", 4 * n), e,
+            n, _stream_handle(stream) or None, _ptr(acc), _ptr(obs))
         _check(rc, "ss_filter_unequal")
         return acc[:n], obs[:n]
 
@@ -417,7 +493,9 @@ class Filter:
         n = accept.shape[0]
         idx = torch.empty(max(n, 1), dtype=torch.int64, device=accept.device)
         cnt = torch.empty(1, dtype=torch.int64, device=accept.device)
-        rc = load().ss_compact_accepted(self.ctx, _ptr(accept) or None, n,
+        rc = load().ss_compact_accepted(self.ctx,
+                                        _dptr(accept, self.device, "accept")
+                                        or None, n,
                                         _stream_handle(stream) or None,
                                         _ptr(idx), _ptr(cnt))
         _check(rc, "ss_compact_accepted")
@@ -432,8 +510,11 @@ class Filter:
         out_q = torch.zeros(max(n * w16, 1), dtype=torch.int32,
                             device=reads.device)
         out_r = torch.zeros_like(out_q)
-        rc = load().ss_gather_pairs(self.ctx, _ptr(reads), _ptr(refs), m,
-                                    _ptr(index), _ptr(count), n,
+        d = self.device
+        rc = load().ss_gather_pairs(self.ctx, _dptr(reads, d, "reads"),
+                                    _dptr(refs, d, "refs"), m,
+                                    _dptr(index, d, "index"),
+                                    _dptr(count, d, "count", 8), n,
                                     _stream_handle(stream) or None,
                                     _ptr(out_q), _ptr(out_r))
         _check(rc, "ss_gather_pairs")
@@ -446,9 +527,12 @@ class Filter:
         import torch
         n = lengths.shape[0]
         out = torch.empty(max(n, 1), dtype=torch.int32, device=lengths.device)
+        d = self.device
         rc = load().ss_edit_distance_varlen(
-            self.ctx, _ptr(reads), _ptr(refs), _ptr(offsets), _ptr(lengths),
-            _ptr(E), n, _stream_handle(stream) or None, _ptr(out))
+            self.ctx, _dptr(reads, d, "reads"), _dptr(refs, d, "refs"),
+            _dptr(offsets, d, "offsets", 8 * n),
+            _dptr(lengths, d, "lengths", 4 * n), _dptr(E, d, "E", 4 * n), n,
+            _stream_handle(stream) or None, _ptr(out))
         _check(rc, "ss_edit_distance_varlen")
         return out[:n]
 
@@ -456,9 +540,11 @@ class Filter:
         """(true accepts, false accepts, false rejects, true rejects)."""
         import torch
         counts = torch.zeros(4, dtype=torch.int64, device=accept.device)
+        n = accept.shape[0]
+        d = self.device
         rc = load().ss_filter_confusion(
-            self.ctx, _ptr(accept), _ptr(ed), accept.shape[0], e,
-            _stream_handle(stream) or None, _ptr(counts))
+            self.ctx, _dptr(accept, d, "accept", n), _dptr(ed, d, "ed", 4 * n),
+            n, e, _stream_handle(stream) or None, _ptr(counts))
         _check(rc, "ss_filter_confusion")
         return tuple(int(x) for x in counts.cpu().tolist())
 

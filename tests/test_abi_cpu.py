@@ -83,3 +83,24 @@ def test_wait_self_test_rejects_null_context():
     lib = binding.load()
     assert lib.ss_check_wait_timeout(None, 50_000_000, None) == \
         binding.SS_ERR_INVALID_ARG
+
+
+def test_binding_rejects_host_short_or_strided_buffers():
+    """The C ABI takes plain pointers and cannot check them, so the binding
+    refuses what the kernels would read or write out of bounds: a host
+    tensor where a device one is due (and the reverse), a strided view, or
+    fewer bytes than the call's shape needs."""
+    torch = pytest.importorskip("torch")
+    h = torch.zeros(64, dtype=torch.uint8)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        binding._dptr(h, 0, "reads")
+    assert binding._dptr(None, 0, "E") == 0
+    assert binding._hptr(h, "reads", 64) == h.data_ptr()
+    with pytest.raises(ValueError, match="needs 65"):
+        binding._hptr(h, "reads", 65)
+    with pytest.raises(ValueError, match="contiguous"):
+        binding._hptr(h.view(8, 8).t(), "reads")
+    assert binding._seq_bytes(binding.SS_FMT_ASCII, 3, 100) == 300
+    assert binding._seq_bytes(binding.SS_FMT_PACKED2, 3, 100) == 3 * 7 * 4
+    assert binding._seq_bytes(binding.SS_FMT_PACKED2, 0, 100) == 0
+    assert binding._seq_bytes(binding.SS_FMT_ASCII, 5, 0) == 0

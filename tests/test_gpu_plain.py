@@ -208,6 +208,31 @@ def test_empty_and_zero_length(F):
     assert acc.cpu().tolist() == [1] * 8 and obs.cpu().tolist() == [0] * 8
 
 
+def test_binding_refuses_buffers_the_kernels_would_overrun(F):
+    """A host tensor, a short buffer or a strided view never reaches a
+    kernel: the binding raises before the call."""
+    torch = torch_cuda()
+    n, m = 1000, 100
+    w16 = binding.ss_packed_words(m)
+    q = torch.zeros(n * w16, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        F.filter(q.cpu(), q, m=m, e=3, n=n)
+    with pytest.raises(ValueError, match="needs"):
+        F.filter(q[:-1], q, m=m, e=3, n=n)
+    with pytest.raises(ValueError, match="contiguous"):
+        F.filter(q.view(n, w16).t(), q, m=m, e=3, n=n)
+    with pytest.raises(ValueError, match="needs"):
+        F.filter(q, q, m=m, e=3, n=n,
+                 out_accept=torch.empty(n - 1, dtype=torch.uint8,
+                                        device="cuda"))
+    with pytest.raises(ValueError, match="needs"):
+        F.filter_submaze(q, q[: w16 * (n - 1)], m=m, e=3, t=8, y=3, n=n)
+    with pytest.raises(ValueError, match="host"):
+        F.filter_host(q, q, m=m, e=3, n=n, fmt=FMT_PACKED2)
+    acc, obs = F.filter(q, q, m=m, e=3, n=n, sync=True)  # still usable
+    assert acc.all()
+
+
 def test_invalid_base_through_filter(F):
     reads, refs = synth.pairs_fixed(4, 0, 300, 100, synth.SHORT_POISSON)
     refs[299, 99] = ord("x")

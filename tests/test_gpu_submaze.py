@@ -100,12 +100,14 @@ def test_submaze_edges(F):
     torch = torch_cuda()
     empty = torch.zeros(4, dtype=torch.int32, device="cuda")
     acc, obs = F.filter_submaze(empty, empty, m=100, e=3, t=8, y=3, n=0)
+    one = torch.zeros(binding.ss_packed_words(100), dtype=torch.int32,
+                      device="cuda")  # one pair of 100 bp
     assert acc.numel() == 0
     reads, refs = synth.pairs_fixed(5, 0, 10, 1, synth.rate_recipe(0.5))
     acc, obs = run(F, reads, refs, 0, 1, 1)
     oacc, oobs = oracle_submaze(reads, refs, 0, 1, 1)
     assert_same(acc, obs, oacc, oobs, "m=1")
     with pytest.raises(binding.SSError):
-        F.filter_submaze(empty, empty, m=100, e=40, t=8, y=3, n=1)
+        F.filter_submaze(one, one, m=100, e=40, t=8, y=3, n=1)
     with pytest.raises(binding.SSError):
-        F.filter_submaze(empty, empty, m=100, e=3, t=0, y=3, n=1)
+        F.filter_submaze(one, one, m=100, e=3, t=0, y=3, n=1)
