@@ -597,6 +597,13 @@ class Server:
         refs = np.ascontiguousarray(refs, dtype=np.uint8)
         lengths = np.ascontiguousarray(lengths, dtype=np.int32)
         E = np.ascontiguousarray(E, dtype=np.int32)
+        # the library copies sum(lengths) bytes of each from host memory
+        need = int(np.clip(lengths, 0, None).sum(dtype=np.int64))
+        if reads.size < need or refs.size < need:
+            raise ValueError(f"reads/refs hold {reads.size}/{refs.size} "
+                             f"bytes, the lengths need {need}")
+        if E.size < lengths.size:
+            raise ValueError(f"{E.size} thresholds for {lengths.size} pairs")
         t = ctypes.c_uint64()
         rc = load().ss_server_submit(
             self.h, reads.ctypes.data if reads.size else None,

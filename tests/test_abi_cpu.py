@@ -104,3 +104,18 @@ def test_binding_rejects_host_short_or_strided_buffers():
     assert binding._seq_bytes(binding.SS_FMT_PACKED2, 3, 100) == 3 * 7 * 4
     assert binding._seq_bytes(binding.SS_FMT_PACKED2, 0, 100) == 0
     assert binding._seq_bytes(binding.SS_FMT_ASCII, 5, 0) == 0
+
+
+def test_server_submit_checks_request_sizes():
+    """A request's reads and refs must hold sum(lengths) bytes each (the
+    library copies that much from host memory) and one threshold per pair;
+    checked before the library is called (no server needed)."""
+    np = pytest.importorskip("numpy")
+    S = object.__new__(binding.Server)  # no device: the checks come first
+    S.h, S._keep = 0, {}
+    with pytest.raises(ValueError, match="need 200"):
+        S.submit(np.zeros(100, np.uint8), np.zeros(200, np.uint8),
+                 [100, 100], [1, 1])
+    with pytest.raises(ValueError, match="thresholds"):
+        S.submit(np.zeros(200, np.uint8), np.zeros(200, np.uint8),
+                 [100, 100], [1])
