@@ -110,32 +110,32 @@ SS_HD int flo32(uint32_t x)
 // columns >= c, x_s | -x_s sets every bit at or above row s's first
 // obstacle, so the AND over rows has its lowest set bit at max_s(first
 // obstacle): three operations per row and iteration, a find-first per
-// iteration.
+// iteration.  The word is entered at its first column (a checkpoint of the
+// previous word is at most its end), so the first search needs no column
+// mask, two operations per row; only it can carry blocked rows (a found
+// obstacle clears them), so the later ones need no check for them.
 template <int NR, class RowBits>
 SS_HD void rw_word_smear(const uint32_t (&Z)[NR], RowBits &deadbits,
                          int base, int m, int E, int &count, bool &finished,
                          uint32_t neg1)
 {
+    uint32_t A = 0xffffffffu;
+    if (deadbits) {
+        // runs continued from the previous word: rows that already met an
+        // obstacle since the checkpoint do not count
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const uint32_t x =
+                Z[r] | (0u - (uint32_t)((deadbits >> r) & (RowBits)1));
+            A &= x | (x * neg1);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            A &= Z[r] | (Z[r] * neg1);
+    }
     uint32_t M = 0xffffffffu;  // columns >= checkpoint
     for (;;) {
-        uint32_t A = 0xffffffffu;
-        if (deadbits) {
-            // runs continued from the previous word: rows that already
-            // met an obstacle since the checkpoint do not count
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t x =
-                    (Z[r] & M) |
-                    (0u - (uint32_t)((deadbits >> r) & (RowBits)1));
-                A &= x | (x * neg1);
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t x = Z[r] & M;
-                A &= x | (x * neg1);
-            }
-        }
         if (A == 0u) {
             // a live row runs past the word end: remember the others
             RowBits d = deadbits;
@@ -160,6 +160,12 @@ SS_HD void rw_word_smear(const uint32_t (&Z)[NR], RowBits &deadbits,
         if (c >= base + 32)
             return;
         M = 0xffffffffu << (c - base);
+        A = 0xffffffffu;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const uint32_t x = Z[r] & M;
+            A &= x | (x * neg1);
+        }
     }
 }
 
