@@ -39,7 +39,7 @@ def pairs(seed, n, m, recipe):
 def test_rw_exact_matches_oracle(emu, m):
     for Q, R in pairs(60 + m, 60, m, synth.rate_recipe(0.15)):
         q, r = packed(Q), packed(R)
-        for E in (0, 1, 2, 5, 10, 17, 31):
+        for E in (0, 1, 2, 3, 4, 5, 10, 17, 31):
             got = emu.emu_rw_exact(P(q), P(r), m, E)
             want = oracle.filter_pair(Q, R, E).obstacles
             assert got == want, (m, E, Q, R)
