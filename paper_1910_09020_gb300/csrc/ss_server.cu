@@ -95,6 +95,9 @@ struct ss_server {
     size_t budget = 0;
     size_t in_use = 0;
     std::vector<Slot> slots;
+    // reads of results and status words: a non-blocking stream, so a read
+    // waits for nothing the caller has queued on the legacy default stream
+    cudaStream_t copy_st = nullptr;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> pending;
@@ -112,6 +115,17 @@ struct ss_server {
 };
 
 namespace {
+
+// Device -> host read on the server's copy stream (the batch it reads from
+// has completed).
+cudaError_t read_back(ss_server *s, void *dst, const void *src, size_t bytes)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost,
+                                    s->copy_st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s->copy_st);
+    return e;
+}
 
 // Device bytes a request needs while it runs (inputs, packed words,
 // per-pair metadata, bucket permutation, results).
@@ -321,16 +335,22 @@ void scheduler(ss_server *s)
             if (!b || !b->done.load(std::memory_order_acquire))
                 continue;
             int dev_status = 0;
-            cudaMemcpy(&dev_status, b->status, sizeof(int),
-                       cudaMemcpyDeviceToHost);
+            int st = SS_OK;
+            if (read_back(s, &dev_status, b->status, sizeof(int)) !=
+                cudaSuccess) {
+                (void)cudaGetLastError();
+                st = SS_ERR_CUDA;
+            }
             // a bad base fails its own request only
             if (dev_status & ssk::kStatusInvalidBase) {
                 b->host_bad.resize((size_t)b->n);
-                cudaMemcpy(b->host_bad.data(), b->bad, (size_t)b->n,
-                           cudaMemcpyDeviceToHost);
+                if (read_back(s, b->host_bad.data(), b->bad, (size_t)b->n) !=
+                    cudaSuccess) {
+                    (void)cudaGetLastError();
+                    st = SS_ERR_CUDA;
+                }
             }
-            int st = SS_OK;
-            if (dev_status & ssk::kStatusUnsupported)
+            if (st == SS_OK && (dev_status & ssk::kStatusUnsupported))
                 st = SS_ERR_UNSUPPORTED;
             for (Request *r : b->reqs) {
                 r->state = kDone;
@@ -443,8 +463,11 @@ int ss_server_create(ss_server **out, int device, size_t hbm_budget_bytes,
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     (void)cudaGetLastError();
-    if (ssk::bucket_init() != cudaSuccess) {
-        delete s;
+    if (ssk::bucket_init() != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) !=
+            cudaSuccess) {
+        (void)cudaGetLastError();
+        ss_server_destroy(s);
         return SS_ERR_CUDA;
     }
     s->slots.resize(slots);
@@ -502,6 +525,8 @@ int ss_server_destroy(ss_server *s)
         if (sl.join)
             cudaEventDestroy(sl.join);
     }
+    if (s->copy_st)
+        cudaStreamDestroy(s->copy_st);
     delete s;
     return SS_OK;
 }
@@ -592,11 +617,10 @@ int ss_server_fetch(ss_server *s, uint64_t ticket, uint8_t *out_accept,
     int rc = r->status;
     if (r->batch && r->batch->dev) {
         cudaSetDevice(s->device);
-        if (cudaMemcpy(out_accept, r->batch->acc + r->first, (size_t)r->n,
-                       cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(out_obstacles, r->batch->obs + r->first,
-                       (size_t)r->n * 4, cudaMemcpyDeviceToHost) !=
-                cudaSuccess) {
+        if (read_back(s, out_accept, r->batch->acc + r->first,
+                      (size_t)r->n) != cudaSuccess ||
+            read_back(s, out_obstacles, r->batch->obs + r->first,
+                      (size_t)r->n * 4) != cudaSuccess) {
             (void)cudaGetLastError();
             rc = SS_ERR_CUDA;
         }
