@@ -644,11 +644,15 @@ int ss_sync(ss_ctx *ctx, void *stream)
     SS_CUDA(cudaStreamSynchronize(st));
     SS_CUDA(cudaStreamSynchronize(ctx->stream));
     SS_CUDA(cudaStreamSynchronize(ctx->side));
+    // read and clear the status word on the context's own (non-blocking)
+    // stream, the clear complete before any later launch can latch again
     int flags = 0;
-    SS_CUDA(cudaMemcpy(&flags, ctx->d_status, sizeof(int),
-                       cudaMemcpyDeviceToHost));
+    SS_CUDA(cudaMemcpyAsync(&flags, ctx->d_status, sizeof(int),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    SS_CUDA(cudaStreamSynchronize(ctx->stream));
     if (flags) {
-        SS_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        SS_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
+        SS_CUDA(cudaStreamSynchronize(ctx->stream));
         if (flags & ssk::kStatusInvalidBase)
             return SS_ERR_INVALID_BASE;
         if (flags & ssk::kStatusInvalidArg)
