@@ -328,11 +328,15 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u8", "data": "synthetic",
-        "config": config_dict(args.gpus, n_override=n),
+        # the workload this arm stands in for (the GPU arm's config); the
+        # bounded sample actually timed is stated in cpu_baseline.sample
+        "config": config_dict(args.gpus, n_override=args.pairs),
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores,
                          "kind": "oracle",
-                         "sample": f"{n} pairs x {len(SWEEP)} thresholds "
-                                   f"per step"},
+                         "sample": f"step s (warm-up first) times pairs "
+                                   f"s*{n} .. (s+1)*{n}-1 of the workload "
+                                   f"x {len(SWEEP)} thresholds, {cores} "
+                                   f"host threads"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

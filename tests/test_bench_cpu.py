@@ -50,3 +50,23 @@ def test_op_model_on_oracle_counters():
     for E in bench.SWEEP:
         assert model[E]["alu_ops_per_pair"] <= \
             model[E]["alu_ops_row_words_per_pair"] + 1e-9
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line on the GPU arm's config, metric and unit, with the sample it
+    timed described in cpu_baseline."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, bench.__file__, "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "pairs/s"
+    assert line["higher_is_better"] is True
+    assert line["config"] == bench.config_dict(1)
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
