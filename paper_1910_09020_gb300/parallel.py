@@ -39,7 +39,10 @@ def gather_results(acc: np.ndarray, obs: np.ndarray, bounds, group=None):
     """Gather every rank's (accept, obstacles) to rank 0 in batch order.
     Returns the full arrays on rank 0 and None elsewhere.  Uses the
     process group's backend with CPU tensors (gloo) -- a one-off gather at
-    the end, not a step of the filter."""
+    the end, not a step of the filter.  A rank that has left makes the
+    others' gather raise at once; one that stays up without joining makes
+    it raise after the process group's timeout (set it at
+    init_process_group)."""
     import torch
     import torch.distributed as dist
     rank = dist.get_rank(group)

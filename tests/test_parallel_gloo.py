@@ -74,3 +74,48 @@ def test_two_ranks_gloo_gather_equals_single_process(tmp_path):
     reads, refs, off, L, E = _batch()
     acc, obs = oracle.filter_batch(reads, refs, L, E, offsets=off)
     assert (got["acc"] == acc).all() and (got["obs"] == obs).all()
+
+
+def _worker_lost_rank(rank, world, port, out_path, mode):
+    import datetime
+    import time
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    try:
+        if rank == 1:
+            # leaves between steps (exits), or stays up without ever
+            # joining the gather (stalls past the group's timeout)
+            if mode == "stalls":
+                time.sleep(8)
+            return
+        bounds = [(0, 5), (5, 10)]
+        t0 = time.time()
+        try:
+            parallel.gather_results(np.ones(5, np.uint8),
+                                    np.zeros(5, np.int32), bounds)
+            outcome = "completed"
+        except Exception as e:  # the failure the test expects
+            outcome = type(e).__name__
+        np.savez(out_path, outcome=outcome, seconds=time.time() - t0)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(180)
+@pytest.mark.parametrize("mode", ["exits", "stalls"])
+def test_lost_rank_ends_the_gather_with_an_error(tmp_path, mode):
+    """Failure detection on the host: a rank that leaves between steps, or
+    never joins the gather, makes the survivor's gather fail -- at once, or
+    within the process group's 5 s timeout -- instead of hanging."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "lost.npz")
+    mp.spawn(_worker_lost_rank, args=(2, _free_port(), out, mode), nprocs=2,
+             join=True)
+    got = np.load(out)
+    assert str(got["outcome"]) != "completed"
+    assert float(got["seconds"]) < 30
