@@ -14,7 +14,9 @@ thresholds) per second with the inputs resident in HBM; the inputs (6 GB
 ASCII + 1.7 GB packed) are far larger than L2, so no flush is needed.
 ``e2e`` runs the same sweep through ``ss_filter_host`` from pinned host
 buffers (copies inside the timed region).  ``cpu_baseline`` times the CPU
-oracle on a bounded sample on the host cores.
+oracle on the host cores over every pair of the workload at every
+threshold, and ``parity`` compares its decisions with the GPU's, pair by
+pair.
 
 ``--impl reference`` times the CPU oracle alone on the same workload (the
 reference arm).  Under torchrun each rank filters its own 30M pairs (weak
@@ -73,7 +75,6 @@ def parse():
                     help="pairs per GPU (default: the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the batched and served forms")
     ap.add_argument("--workload", default="all",
@@ -247,21 +248,39 @@ def time_oracle(reads, refs, threads: int = 0):
     return time.perf_counter() - t0, stats
 
 
-def cpu_baseline(target_s: float):
+def cpu_oracle_full(reads, refs, acc, obs):
+    """The oracle over EVERY pair of the workload at every threshold of the
+    sweep (about 9 s on 16 host cores at 30M pairs): its time is the CPU
+    baseline, its counters feed the op model, and its decisions are compared
+    element by element with the GPU's (acc, obs: host arrays [E, n]).
+    Returns (cpu_baseline, per-E stats, parity)."""
     import oracle
     cores = oracle.default_threads()
-    probe_n = 20000
-    r, f = oracle_sample(probe_n)
-    dt, _ = time_oracle(r, f)
-    n = int(min(N_PAIRS, max(probe_n, probe_n * target_s / max(dt, 1e-6))))
-    r, f = oracle_sample(n)
-    dt, stats = time_oracle(r, f)
-    value = n * len(SWEEP) / dt
-    return {
-        "value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-        "sample": f"first {n} pairs of the workload x {len(SWEEP)} thresholds "
-                  f"({dt:.1f} s, {cores} host threads)",
-    }, stats, n
+    n = reads.shape[0]
+    stats = {}
+    t_all = 0.0
+    mismatches = 0
+    first_bad = None
+    for t, E in enumerate(SWEEP):
+        t0 = time.perf_counter()
+        oa, oo, st = oracle.filter_batch(reads, refs, M, E, with_stats=True)
+        t_all += time.perf_counter() - t0
+        stats[E] = st
+        bad = np.flatnonzero((oa != acc[t]) | (oo != obs[t]))
+        mismatches += int(len(bad))
+        if len(bad) and first_bad is None:
+            first_bad = {"E": E, "pair": int(bad[0]),
+                         "gpu": [int(acc[t][bad[0]]), int(obs[t][bad[0]])],
+                         "oracle": [int(oa[bad[0]]), int(oo[bad[0]])]}
+    cpu = {"value": n * len(SWEEP) / t_all, "unit": "pairs/s",
+           "cores": cores, "kind": "oracle",
+           "sample": f"every pair of the workload ({n}) x {len(SWEEP)} "
+                     f"thresholds ({t_all:.1f} s, {cores} host threads)"}
+    parity = {"pairs_checked": n, "decisions_checked": n * len(SWEEP),
+              "mismatches": mismatches, "first_mismatch": first_bad,
+              "against": "CPU oracle (Eq. 1, Section 2.4 steps 1-5), "
+                         "accept flag and obstacle count of every pair"}
+    return cpu, stats, parity
 
 
 def row_word_ops(E: int, words, iters):
@@ -339,6 +358,11 @@ def run_reference(args):
                                    f"host threads"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+        # what one timed step holds: ms_per_step is the time of this many
+        # pairs (a slice of the config's pairs_per_gpu), not of the config
+        "sample_pairs_per_step": n,
+        "sample_decisions_per_step": n * len(SWEEP),
+        "ms_per_config_step": 1e3 * t / len(times) * (args.pairs / n),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -939,9 +963,12 @@ def run_ours(args):
     ipk = measure_int_peaks(local)
     cpu = None
     model = None
+    parity = None
     if not args.no_cpu and world == 1:
-        cpu, stats, sample_n = cpu_baseline(args.cpu_seconds)
-        model = op_model(stats, sample_n)
+        cpu, stats, parity = cpu_oracle_full(
+            hq.numpy().reshape(n, M), hr.numpy().reshape(n, M),
+            acc.cpu().numpy(), obs.cpu().numpy())
+        model = op_model(stats, n)
     hbm = peaks["hbm_gbs"] * 1e9
     per_launch = []
     roof_total = meas_total = 0.0
@@ -1040,7 +1067,7 @@ def run_ours(args):
         "data": "synthetic", "config": config_dict(world, n),
         "clocks": clk, "e2e": e2e,
         "gpu_launches": (2 + len(SWEEP)) * args.steps,
-        "roofline": roofline, "cpu_baseline": cpu,
+        "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
         "breakdown": {"pack_ms": pack_ms, "filter_ms": filter_ms,
                       "pack_gbs": n * PACK_BYTES_PER_PAIR / (pack_ms * 1e-3)
                       / 1e9, "generate_s": gen_s},

@@ -142,8 +142,10 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
 
 /* Wait for all work on `stream` (NULL = default stream) and for the
  * context's internal streams, and return the first
- * device-side error latched since the previous ss_sync (then clear it), or
- * SS_OK. */
+ * device-side error latched since the previous ss_sync, or SS_OK.  The
+ * status word is read and cleared in one atomic exchange: an error latched
+ * meanwhile by a launch still running on some other stream is not lost but
+ * returned by a later ss_sync. */
 int ss_sync(ss_ctx *ctx, void *stream);
 
 /* Self-test of the device-side failure path (not in the paper): launch one
@@ -293,8 +295,10 @@ int ss_gather_pairs(ss_ctx *ctx, const void *reads, const void *refs,
  *   - All calls share the one array and it keeps the last call's contents:
  *     calls that overlap on the GPU (other streams or host threads) race.
  *     Order them on one stream or synchronise between them.
- *   - There is no ss_sync for it: a pair with a negative length or
- *     threshold, or one too long to stage, gets obstacles = -1 (accept 0).
+ *   - There is no ss_sync for it and no status is reported: a pair with a
+ *     negative length or threshold, or one longer than 131072 bases (too
+ *     long to stage), gets obstacles = -1 and accept = 0; the kernels'
+ *     status flags go to a word of the scratch array that nothing reads.
  * Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM or SS_ERR_CUDA. */
 #define SS_NOALLOC_MAX_PAIRS 1048576
 int ss_filter_batch_noalloc(const void *reads, const void *refs,

@@ -46,7 +46,8 @@ struct ss_ctx {
     cudaStream_t side = nullptr;     // column-wise classes (forked)
     cudaStream_t hstream[2] = {nullptr, nullptr};  // ss_filter_host pipeline
     cudaEvent_t fork = nullptr, join = nullptr;
-    int *d_status = nullptr;         // latched device errors
+    int *d_status = nullptr;         // [0] latched device errors, [1] the
+                                     // value ss_sync last took from [0]
     size_t budget = 0;
     void *ws = nullptr;              // workspace: one growable device block
     size_t ws_bytes = 0;
@@ -243,7 +244,7 @@ ssk::PairSet make_pairs(const void *reads, const void *refs,
     ps.Es = E;
     ps.m = m;
     ps.e = e;
-    ps.stride = (m + 15) / 16;
+    ps.stride = ((int64_t)m + 15) / 16;
     ps.n = n;
     ps.acc = acc;
     ps.obs = obs;
@@ -384,8 +385,8 @@ int ss_create(ss_ctx **out, int device, size_t workspace_bytes)
             cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) !=
             cudaSuccess ||
-        cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
-        cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_status, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
         (void)cudaGetLastError();
         ss_destroy(ctx);
         return SS_ERR_CUDA;
@@ -644,15 +645,16 @@ int ss_sync(ss_ctx *ctx, void *stream)
     SS_CUDA(cudaStreamSynchronize(st));
     SS_CUDA(cudaStreamSynchronize(ctx->stream));
     SS_CUDA(cudaStreamSynchronize(ctx->side));
-    // read and clear the status word on the context's own (non-blocking)
-    // stream, the clear complete before any later launch can latch again
+    // take the status word (read and clear in one atomic exchange) on the
+    // context's own non-blocking stream: a flag latched by a launch on any
+    // other stream is either taken here or kept for the next ss_sync
     int flags = 0;
-    SS_CUDA(cudaMemcpyAsync(&flags, ctx->d_status, sizeof(int),
+    SS_CUDA(ssk::launch_status_take(ctx->d_status, ctx->d_status + 1,
+                                    ctx->stream));
+    SS_CUDA(cudaMemcpyAsync(&flags, ctx->d_status + 1, sizeof(int),
                             cudaMemcpyDeviceToHost, ctx->stream));
     SS_CUDA(cudaStreamSynchronize(ctx->stream));
     if (flags) {
-        SS_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
-        SS_CUDA(cudaStreamSynchronize(ctx->stream));
         if (flags & ssk::kStatusInvalidBase)
             return SS_ERR_INVALID_BASE;
         if (flags & ssk::kStatusInvalidArg)

@@ -79,6 +79,10 @@ cudaError_t launch_unequal(const uint32_t *reads, const int64_t *read_off,
                            uint8_t *acc, int32_t *obs, int *status,
                            int sm_count, cudaStream_t st);
 
+// Read and clear the status word in one atomic exchange; the old value
+// lands in *taken (ss_selftest.cu).
+cudaError_t launch_status_take(int *status, int *taken, cudaStream_t st);
+
 // Bounded-wait self-test (ss_selftest.cu).
 cudaError_t launch_wait_timeout(uint64_t limit_ns, int *status,
                                 cudaStream_t st);

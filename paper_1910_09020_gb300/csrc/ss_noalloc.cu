@@ -27,7 +27,10 @@
 namespace {
 
 // Bucket workspace for SS_NOALLOC_MAX_PAIRS pairs (4 B of permutation per
-// pair plus the class tables) and a status word at the end.
+// pair plus the class tables) and, at the end, the word the kernels latch
+// their status flags into.  This entry point reports no status (bad pairs
+// are marked by obstacles = -1 instead), so that word is a sink nothing
+// reads and needs no clearing.
 constexpr size_t kScratchBytes = (size_t)4 * SS_NOALLOC_MAX_PAIRS + 64 * 1024;
 constexpr size_t kStatusOffset = kScratchBytes - 256;
 
@@ -100,10 +103,6 @@ extern "C" int ss_filter_batch_noalloc(const void *reads, const void *refs,
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
     int *status = (int *)((char *)scratch + kStatusOffset);
-    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return SS_ERR_CUDA;
-    }
     ssk::PairSet ps;
     ps.reads = (const uint32_t *)reads;
     ps.refs = (const uint32_t *)refs;
@@ -112,7 +111,7 @@ extern "C" int ss_filter_batch_noalloc(const void *reads, const void *refs,
     ps.Es = E;
     ps.m = m;
     ps.e = e;
-    ps.stride = (m + 15) / 16;
+    ps.stride = ((int64_t)m + 15) / 16;
     ps.n = n;
     ps.acc = out_accept;
     ps.obs = out_obstacles;

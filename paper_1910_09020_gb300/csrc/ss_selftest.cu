@@ -1,4 +1,9 @@
-// ss_selftest.cu -- the device-side bounded wait, made to run out.
+// ss_selftest.cu -- the context's status word, and the device-side bounded
+// wait made to run out.
+//
+// k_status_take reads and clears the latched status word in one atomic
+// exchange, so a flag that another stream's kernel latches at any moment is
+// either taken by this read or left for the next one, never lost.
 //
 // One CTA initialises an mbarrier that nothing ever completes and waits on
 // it with the same bounded wait the filter kernels use for their bulk
@@ -13,6 +18,17 @@
 #include "ss_internal.h"
 
 namespace ssk {
+
+__global__ void k_status_take(int *status, int *taken)
+{
+    *taken = atomicExch(status, 0);
+}
+
+cudaError_t launch_status_take(int *status, int *taken, cudaStream_t st)
+{
+    k_status_take<<<1, 1, 0, st>>>(status, taken);
+    return cudaGetLastError();
+}
 
 __global__ void k_wait_timeout(uint64_t limit_ns, int *status)
 {

@@ -1,10 +1,14 @@
 """Parity at the benchmark's full sizes, in the launch configurations
-bench.py times, on sampled outputs the oracle computes one by one:
+bench.py times:
 
-* 30M x 100 bp, E = 0, 2, ..., 10, plain launches (the headline sweep);
-* 10M x 250 bp + 10M x 150 bp at E = 0 %, 5 %, 10 %, plain and persistent;
-* the uneven 2M-pair batch (64..10000 bp, E = 5 %), one bucketed graph;
-* full-shape served requests (up to 4096 pairs, 100..100000 bp, E = 10 %).
+* 30M x 100 bp, E = 0, 2, ..., 10, plain launches (the headline sweep):
+  every pair at every threshold against the oracle;
+* 10M x 250 bp + 10M x 150 bp at every E from 0 % to 10 % of the length,
+  plain and persistent: every pair of both forms against the oracle;
+* the uneven 2M-pair batch (64..10000 bp, E = 5 %), one bucketed graph:
+  every pair up to 2 kbp and a seeded 2 % sample of the longer ones;
+* full-shape served requests (up to 4096 pairs, 100..100000 bp, E = 10 %):
+  every pair up to 2 kbp and a seeded 2 % sample of the longer ones.
 """
 import numpy as np
 import pytest
@@ -23,14 +27,37 @@ def _torch():
     return torch
 
 
-def _check_sample(acc, obs, idx, reads, refs, m, E, what):
-    oa, oo = oracle.filter_batch(reads[idx], refs[idx], m, E)
-    ga, go = acc[idx], obs[idx]
-    bad = np.nonzero((ga != oa) | (go != oo))[0]
-    assert len(bad) == 0, (what, idx[bad[:5]], ga[bad[:5]], oa[bad[:5]])
+def _check_all(acc, obs, reads, refs, m, E, what):
+    """Every pair of a fixed-length batch against the oracle."""
+    oa, oo = oracle.filter_batch(reads, refs, m, E)
+    bad = np.nonzero((acc != oa) | (obs != oo))[0]
+    assert len(bad) == 0, (what, len(bad), bad[:5], acc[bad[:5]],
+                           oa[bad[:5]], obs[bad[:5]], oo[bad[:5]])
 
 
-def test_headline_sweep_30M_sampled():
+def _check_varlen(acc, obs, idx, reads, refs, off, L, E, what):
+    """Pairs idx of a concatenated batch against the oracle."""
+    sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in idx])
+    sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in idx])
+    so = np.zeros(len(idx) + 1, np.int64)
+    np.cumsum(L[idx], out=so[1:])
+    oa, oo = oracle.filter_batch(sub_r, sub_f, L[idx], E[idx], offsets=so)
+    bad = np.nonzero((acc[idx] != oa) | (obs[idx] != oo))[0]
+    assert len(bad) == 0, (what, len(bad), idx[bad[:5]])
+
+
+def _short_and_sampled(L, seed, limit=2000, frac=0.02, at_least=0):
+    """Every pair of length <= limit plus a seeded sample (frac of them,
+    at least `at_least`) of the longer ones."""
+    short = np.flatnonzero(L <= limit)
+    long_ = np.flatnonzero(L > limit)
+    k = min(len(long_), max(int(round(frac * len(long_))), at_least))
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(long_, k, replace=False) if k else long_[:0]
+    return np.sort(np.concatenate([short, pick])), len(short), k
+
+
+def test_headline_sweep_30M_every_pair():
     torch = _torch()
     n, m = 30_000_000, 100
     hq = torch.empty(n * m, dtype=torch.uint8, pin_memory=True)
@@ -38,27 +65,21 @@ def test_headline_sweep_30M_sampled():
     synth.pairs_fixed(SEED + 2, 0, n, m, synth.SHORT_POISSON,
                       out=(hq.numpy(), hr.numpy()))
     reads, refs = hq.numpy().reshape(n, m), hr.numpy().reshape(n, m)
-    rng = np.random.default_rng(1)
-    idx = np.unique(np.concatenate([rng.integers(0, n, 20000),
-                                    np.arange(0, 300), np.arange(n - 300, n)]))
     with binding.Filter(0) as F:
         q = F.pack(hq.cuda(), m=m, n=n)
         r = F.pack(hr.cuda(), m=m, n=n)
         for E in (0, 2, 4, 6, 8, 10):
             acc, obs = F.filter(q, r, m=m, e=E, n=n, sync=True)
-            _check_sample(acc.cpu().numpy(), obs.cpu().numpy(), idx, reads,
-                          refs, m, E, f"sweep E={E}")
+            _check_all(acc.cpu().numpy(), obs.cpu().numpy(), reads, refs, m,
+                       E, f"sweep E={E}")
 
 
-def test_two_lengths_20M_sampled_both_forms():
+def test_two_lengths_20M_every_pair_both_forms():
     torch = _torch()
     n3 = 10_000_000
     rec = synth.rate_recipe(0.12)
     r250 = synth.pairs_fixed(SEED + 3, 0, n3, 250, rec)
     r150 = synth.pairs_fixed(SEED + 3, n3, n3, 150, rec)
-    rng = np.random.default_rng(2)
-    i250 = np.unique(rng.integers(0, n3, 6000))
-    i150 = np.unique(rng.integers(0, n3, 6000))
     with binding.Filter(0, workspace_bytes=2 << 30) as F:
         bufs = []
         for (rd, rf), m in ((r250, 250), (r150, 150)):
@@ -73,7 +94,7 @@ def test_two_lengths_20M_sampled_both_forms():
                          ).cuda()
         lens = torch.cat([torch.full((n3,), 250, dtype=torch.int32),
                           torch.full((n3,), 150, dtype=torch.int32)]).cuda()
-        for pct in (0, 5, 10):
+        for pct in range(0, 11):
             e250, e150 = 250 * pct // 100, 150 * pct // 100
             a1, o1 = F.filter(bufs[0][0], bufs[0][1], m=250, e=e250, n=n3,
                               sync=True)
@@ -83,15 +104,20 @@ def test_two_lengths_20M_sampled_both_forms():
                             torch.full((n3,), e150, dtype=torch.int32)]).cuda()
             ab, ob = F.filter(allq, allr, offsets=offs, lengths=lens, E=Es,
                               sync=True)
-            assert torch.equal(torch.cat([a1, a2]), ab)
-            assert torch.equal(torch.cat([o1, o2]), ob)
-            _check_sample(a1.cpu().numpy(), o1.cpu().numpy(), i250, r250[0],
-                          r250[1], 250, e250, f"250 bp {pct}%")
-            _check_sample(a2.cpu().numpy(), o2.cpu().numpy(), i150, r150[0],
-                          r150[1], 150, e150, f"150 bp {pct}%")
+            # the persistent form against the oracle (every pair); the
+            # plain form equal to it
+            ab, ob = ab.cpu().numpy(), ob.cpu().numpy()
+            _check_all(ab[:n3], ob[:n3], r250[0], r250[1], 250, e250,
+                       f"250 bp {pct}% persistent")
+            _check_all(ab[n3:], ob[n3:], r150[0], r150[1], 150, e150,
+                       f"150 bp {pct}% persistent")
+            assert (a1.cpu().numpy() == ab[:n3]).all(), f"250 bp {pct}%"
+            assert (o1.cpu().numpy() == ob[:n3]).all(), f"250 bp {pct}%"
+            assert (a2.cpu().numpy() == ab[n3:]).all(), f"150 bp {pct}%"
+            assert (o2.cpu().numpy() == ob[n3:]).all(), f"150 bp {pct}%"
 
 
-def test_uneven_2M_batch_sampled():
+def test_uneven_2M_batch_short_pairs_all_long_sampled():
     torch = _torch()
     n = 2_000_000
     L = np.sort(synth.log_uniform(SEED + 4, 0, n, 64, 10000)).astype(np.int32)
@@ -116,18 +142,12 @@ def test_uneven_2M_batch_sampled():
         acc, obs = F.filter(pq, pr, offsets=dwo, lengths=dL,
                             E=torch.from_numpy(E).cuda(), sync=True)
         acc, obs = acc.cpu().numpy(), obs.cpu().numpy()
-    rng = np.random.default_rng(3)
-    idx = np.unique(np.concatenate([rng.integers(0, n, 2500),
-                                    np.arange(n - 50, n)]))
-    sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in idx])
-    sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in idx])
-    so = np.zeros(len(idx) + 1, np.int64)
-    np.cumsum(L[idx], out=so[1:])
-    oa, oo = oracle.filter_batch(sub_r, sub_f, L[idx], E[idx], offsets=so)
-    assert (acc[idx] == oa).all() and (obs[idx] == oo).all()
+    idx, n_short, n_long = _short_and_sampled(L, 3, at_least=5000)
+    assert n_short > 1_000_000 and n_long >= 5000
+    _check_varlen(acc, obs, idx, reads, refs, off, L, E, "uneven 2M")
 
 
-def test_served_full_shape_requests_sampled():
+def test_served_full_shape_requests_short_pairs_all_long_sampled():
     reqs = []
     for i in range(6):
         rng = np.random.default_rng(SEED + 5 + i)
@@ -143,16 +163,10 @@ def test_served_full_shape_requests_sampled():
         for t in ts:
             assert S.wait(t) == binding.SS_OK
             outs.append(S.fetch(t))
-    rng = np.random.default_rng(4)
-    for (rc, acc, obs, _), (reads, refs, L, E, off) in zip(outs, reqs):
+    for k, ((rc, acc, obs, _), (reads, refs, L, E, off)) in enumerate(
+            zip(outs, reqs)):
         assert rc == binding.SS_OK
-        # sample: a few pairs per request, the longest included
-        k = min(len(L), 6)
-        idx = np.unique(np.concatenate([rng.integers(0, len(L), k),
-                                        [int(np.argmax(L))]]))
-        sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in idx])
-        sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in idx])
-        so = np.zeros(len(idx) + 1, np.int64)
-        np.cumsum(L[idx], out=so[1:])
-        oa, oo = oracle.filter_batch(sub_r, sub_f, L[idx], E[idx], offsets=so)
-        assert (acc[idx] == oa).all() and (obs[idx] == oo).all()
+        # every pair up to 2 kbp, 2 % of the longer ones (at least one)
+        idx, _, _ = _short_and_sampled(np.asarray(L), 40 + k, at_least=1)
+        _check_varlen(acc, obs, idx, reads, refs, off, np.asarray(L),
+                      np.asarray(E), f"request {k}")

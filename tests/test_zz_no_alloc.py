@@ -13,6 +13,7 @@ already run every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1910_09020_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
@@ -54,10 +55,16 @@ def _batch(F, seed, n):
     F.pack(dev(refs), offsets=dev(off[:-1]), lengths=dL, out=pr,
            out_offsets=dwo)
     F.sync()
-    return pq, pr, dwo, dL, dev(Es)
+    return pq, pr, dwo, dL, dev(Es), (reads, refs, off, L, Es)
 
 
-def _noalloc(pq, pr, dwo, dL, dE):
+def _oracle(host):
+    """The CPU oracle's (accept, obstacles) for a batch made by _batch."""
+    reads, refs, off, L, Es = host
+    return oracle.filter_batch(reads, refs, L, Es, offsets=off)
+
+
+def _noalloc(pq, pr, dwo, dL, dE, host=None):
     torch = _torch()
     n = dL.shape[0]
     acc = torch.full((n,), 7, dtype=torch.uint8, device="cuda")
@@ -78,13 +85,18 @@ def test_noalloc_matches_ss_filter_batch_two_calls_in_a_row():
         small = _batch(F, 72, 333)
         want = []
         for b in (big, small):
-            pq, pr, dwo, dL, dE = b
+            pq, pr, dwo, dL, dE, host = b
             a, o = F.filter(pq, pr, offsets=dwo, lengths=dL, E=dE, sync=True)
             want.append((a.cpu().numpy(), o.cpu().numpy()))
+            # the context path itself equals the oracle on these pairs
+            oa, oo = _oracle(host)
+            assert (want[-1][0] == oa).all() and (want[-1][1] == oo).all()
         # two calls in a row on the shared scratch: larger, then smaller
         got = [_noalloc(*big), _noalloc(*small)]
-        for (ga, go), (wa, wo) in zip(got, want):
+        for (ga, go), (wa, wo), b in zip(got, want, (big, small)):
             assert (ga == wa).all() and (go == wo).all()
+            oa, oo = _oracle(b[-1])
+            assert (ga == oa).all() and (go == oo).all()
         # and the first batch again after the second
         ga, go = _noalloc(*big)
         assert (ga == want[0][0]).all() and (go == want[0][1]).all()
@@ -98,6 +110,9 @@ def test_noalloc_uniform_fixed_stride():
         q = F.pack(torch.from_numpy(reads.reshape(-1).copy()).cuda(), m=m, n=n)
         r = F.pack(torch.from_numpy(refs.reshape(-1).copy()).cuda(), m=m, n=n)
         wa, wo = F.filter(q, r, m=m, e=E, n=n, sync=True)
+        oa, oo = oracle.filter_batch(reads, refs, m, E)
+        assert (wa.cpu().numpy() == oa).all()
+        assert (wo.cpu().numpy() == oo).all()
         acc = torch.empty(n, dtype=torch.uint8, device="cuda")
         obs = torch.empty(n, dtype=torch.int32, device="cuda")
         for _ in range(2):
@@ -119,3 +134,31 @@ def test_noalloc_rejects_batches_beyond_its_scratch():
         x.data_ptr(), x.data_ptr(), 0, 0, 100, 0, 3,
         binding.SS_NOALLOC_MAX_PAIRS + 1, 0, acc.data_ptr(), obs.data_ptr())
     assert rc == binding.SS_ERR_OOM
+
+
+def test_noalloc_marks_bad_pairs_with_minus_one():
+    """A negative length, a negative threshold or a pair longer than 131072
+    bases gets obstacles = -1 and accept = 0 (this entry reports no status);
+    the good pairs around them still equal the oracle."""
+    torch = _torch()
+    with binding.Filter(0) as F:
+        pq, pr, dwo, dL, dE, host = _batch(F, 74, 64)
+        reads, refs, off, L, Es = host
+        L2, E2 = L.copy(), Es.copy()
+        L2[5] = -3          # negative length
+        E2[9] = -1          # negative threshold
+        # too long to stage: with E' > 31 the pair belongs to the CTA-per-
+        # pair classes, which refuse lengths past 131072 before reading a
+        # word (a short threshold would send it to the thread-per-pair
+        # class, which reads m bases from the buffers as given)
+        L2[17] = 131073
+        E2[17] = 1000
+        dL2 = torch.from_numpy(L2).cuda()
+        dE2 = torch.from_numpy(E2).cuda()
+        for _ in range(2):
+            ga, go = _noalloc(pq, pr, dwo, dL2, dE2)
+            bad = np.zeros(len(L), bool)
+            bad[[5, 9, 17]] = True
+            assert (go[bad] == -1).all() and (ga[bad] == 0).all()
+            oa, oo = _oracle(host)
+            assert (ga[~bad] == oa[~bad]).all() and (go[~bad] == oo[~bad]).all()
