@@ -271,8 +271,8 @@ SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
     }
 }
 
-// rw_word_borrow for the plain kernel's row-wise thresholds E >= 5 (11
-// rows or more; E = 6..15 walk columns instead, see kRwColsMinE).  The
+// rw_word_borrow for the plain kernel's row-wise threshold E = 5 (11 rows;
+// from kRwColsMinE on the plain kernels walk columns instead).  The
 // bucketed kernel (E at run time, 2 EMAX + 1 rows) keeps the smear-AND
 // form: with the borrow form its two-length batches at E of 7-10 % of the
 // length ran 2 % slower.
@@ -429,6 +429,21 @@ __device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
     return s_perm[t];
 }
 
+// The plain kernels walk the greedy one column at a time (rw_route_cols)
+// from E = kRwColsMinE on, and row-wise (rw_route) below.
+constexpr int kRwColsMinE = 6;
+
+// The plain kernels' routine for threshold E: min(count, E+1).
+template <int E, class Seq>
+__device__ __forceinline__ int rw_route_plain(const Seq &q, const Seq &r,
+                                              int m, uint32_t neg1)
+{
+    if constexpr (E >= kRwColsMinE)
+        return rw_route_cols<E>(q, r, m);
+    else
+        return rw_route<E, true>(q, r, m, E, neg1);
+}
+
 // Plain launch for long reads: uniform m and E, one thread per pair, one CTA
 // per T pairs.  The CTA stages its pairs (128-bit loads when aligned), orders
 // them by a predicted routing cost so that each warp holds pairs of similar
@@ -493,15 +508,11 @@ __global__ void __launch_bounds__(128)
     if (t < np) {
         const SmemSeq q{sQ + u, ld, w16};
         const SmemSeq r{sR + u, ld, w16};
-        const int cnt = rw_route<E, true>(q, r, a.m, E, a.neg1);
+        const int cnt = rw_route_plain<E>(q, r, a.m, a.neg1);
         a.acc[p0 + u] = (uint8_t)(cnt <= E);
         a.obs[p0 + u] = cnt;
     }
 }
-
-// The plain kernel walks the greedy one column at a time (rw_route_cols)
-// from E = kRwColsMinE to 15, and row-wise (rw_route) otherwise.
-constexpr int kRwColsMinE = 6;
 
 constexpr int kRwGroup = 8;                  // tiles per CTA
 constexpr int kRwPipeMaxW16 = 16;            // m <= 256
@@ -660,17 +671,15 @@ __device__ __forceinline__ void rw_pipe_run(const RwPipeArgs &a, int E,
     }
 }
 
-// Plain launch: uniform m <= 256 and E, the exact greedy; the cost sort
-// from E = 2 (below, nearly every pair routes in one or two steps).
+// Plain launch: uniform m <= 256 and E, the exact greedy (row-wise below
+// E = kRwColsMinE, the column walk from there); the cost sort from E = 2
+// (below, nearly every pair routes in one or two steps).
 template <int E>
 __global__ void __launch_bounds__(128) k_rw_uniform(const RwPipeArgs a)
 {
     rw_pipe_run<(E >= 2)>(a, E, [&](const SmemSeqPad &q,
                                     const SmemSeqPad &r) {
-        if constexpr (E >= kRwColsMinE && E <= 15)
-            return rw_route_cols<E>(q, r, a.m);
-        else
-            return rw_route<E, true>(q, r, a.m, E, a.neg1);
+        return rw_route_plain<E>(q, r, a.m, a.neg1);
     });
 }
 

@@ -1,5 +1,6 @@
 // ss_rwc.cuh -- one thread per pair, the greedy walked one column at a time
-// with the 2E+1 maze rows as the bits of one word (E <= 15).
+// with the 2E+1 maze rows as the bits of one word (E <= 15) or two (E =
+// 16..31).
 //
 // Method (Section 2.4): from checkpoint c the longest escape segment ends
 // at p* = max over rows of the row's first obstacle at or after c.  Walking
@@ -10,14 +11,16 @@
 // end with S non-empty ends the net with no count.  The walk stops once the
 // count exceeds E (only min(count, E+1) is reported).
 //
-// GB300 mapping: bit i of S is diagonal s = i - E.  Column j of the maze
-// (Eq. 1) is one word: the Q bit planes from bit j - E on (one funnel shift
+// GB300 mapping: bit i of S is diagonal s = i - E (rows 32.. in a second
+// word when 2E+1 > 32).  Column j of the maze (Eq. 1) is one word per 32
+// rows: the Q bit planes from bit j - E on (one funnel shift
 // per plane), compared with R[j] broadcast to every row (a byte permute of
 // a multiply-spread R word), and -- only in chunks where a row can leave
 // the query -- ANDed with the "Q base exists" plane (Eq. 1 case 4).  About
-// ten integer operations per column whatever E is, and every thread of a
-// warp executes the same column body, so a warp diverges only where its
-// pairs stop.  Cheaper than the row-wise routing (rw_route) once 2E+1 rows
+// ten integer operations per column for E <= 15 and about fifteen for the
+// two-word form, whatever E is within each, and every thread of a warp
+// executes the same column body, so a warp diverges only where its pairs
+// stop.  Cheaper than the row-wise routing (rw_route) once 2E+1 rows
 // are many and many pairs are dissimilar: a random pair is rejected after
 // a few columns per obstacle, where row-wise routing rebuilds and scans all
 // rows of each word (for a long, similar pair the row-wise form, 32
@@ -73,31 +76,68 @@ struct RwcQ {
     uint32_t lo_p, lo_c, lo_n, hi_p, hi_c, hi_n, v_p, v_c, v_n;
 };
 
+// The rows still free of obstacles since the checkpoint (bit i = diagonal
+// s = i - E).  With 2E+1 <= 32 rows one word holds them; with 33..63 rows
+// (E = 16..31) s0 holds rows 0..31 and s1 rows 32..2E.
+template <int E>
+struct RwcSurv {
+    static constexpr bool kWide = 2 * E + 1 > 32;
+    static constexpr uint32_t kAll0 =
+        kWide ? 0xffffffffu : (uint32_t)((1ull << (2 * E + 1)) - 1u);
+    static constexpr uint32_t kAll1 =
+        kWide ? (uint32_t)((1ull << (2 * E + 1 - 32)) - 1u) : 0u;
+    uint32_t s0 = kAll0, s1 = kAll1;
+};
+
+// 32 bits of a plane from bit O of word C on, 1 <= O < 64, for the upper
+// rows of a wide survivor word: no row above 2E reads past word N (the
+// highest Q index a column reads is its own plus E <= 31), so the bits
+// shifted in above N are never looked at.
+template <int O>
+SS_HD uint32_t rwc_window_up(uint32_t C, uint32_t N)
+{
+    static_assert(O >= 1 && O < 64, "offset");
+    if constexpr (O < 32)
+        return funnel_r(C, N, O);
+    else
+        return N >> (O - 32);
+}
+
 // Column D of the word (before the row end); tl/th: the R bits of D's
 // quad of columns, spread by spread4.
 template <int E, bool EDGE, int D>
-SS_HD void rwc_column(uint32_t &S, int &count, const RwcQ &q, uint32_t tl,
+SS_HD void rwc_column(RwcSurv<E> &S, int &count, const RwcQ &q, uint32_t tl,
                       uint32_t th)
 {
-    constexpr uint32_t kAll = (1u << (2 * E + 1)) - 1u;
     constexpr int O = D - E;  // Q bit of row 0 relative to the word
-    const uint32_t ql = rwc_window<O>(q.lo_p, q.lo_c, q.lo_n);
-    const uint32_t qh = rwc_window<O>(q.hi_p, q.hi_c, q.hi_n);
+    const uint32_t bl = byte_sign<D & 3>(tl);
+    const uint32_t bh = byte_sign<D & 3>(th);
     // one three-input logic op per plane: S & ~(Q plane ^ broadcast R bit)
-    S &= ~(ql ^ byte_sign<D & 3>(tl));
-    S &= ~(qh ^ byte_sign<D & 3>(th));
+    S.s0 &= ~(rwc_window<O>(q.lo_p, q.lo_c, q.lo_n) ^ bl);
+    S.s0 &= ~(rwc_window<O>(q.hi_p, q.hi_c, q.hi_n) ^ bh);
     if (EDGE)
-        S &= rwc_window<O>(q.v_p, q.v_c, q.v_n);
+        S.s0 &= rwc_window<O>(q.v_p, q.v_c, q.v_n);
+    bool z;
+    if constexpr (RwcSurv<E>::kWide) {
+        // rows 32..2E: Q bits from O + 32 on (O + 32 >= 1 since E <= 31)
+        S.s1 &= ~(rwc_window_up<O + 32>(q.lo_c, q.lo_n) ^ bl);
+        S.s1 &= ~(rwc_window_up<O + 32>(q.hi_c, q.hi_n) ^ bh);
+        if (EDGE)
+            S.s1 &= rwc_window_up<O + 32>(q.v_c, q.v_n);
+        z = (S.s0 | S.s1) == 0u;
+        S.s1 = z ? RwcSurv<E>::kAll1 : S.s1;
+    } else {
+        z = S.s0 == 0u;
+    }
     // the last surviving row met its obstacle here: count it, restart
-    const bool z = S == 0u;
     count += z;
-    S = z ? kAll : S;
+    S.s0 = z ? RwcSurv<E>::kAll0 : S.s0;
 }
 
 // Columns D0+I of the word for I in the sequence; with TAIL, only those
 // with I < live (the row end's partial chunk: a uniform test per column).
 template <int E, bool EDGE, int D0, bool TAIL, int... I>
-SS_HD void rwc_columns(uint32_t &S, int &count, const RwcQ &q, uint32_t l0,
+SS_HD void rwc_columns(RwcSurv<E> &S, int &count, const RwcQ &q, uint32_t l0,
                        uint32_t h0, uint32_t l1, uint32_t h1, int live,
                        std::integer_sequence<int, I...>)
 {
@@ -110,7 +150,7 @@ SS_HD void rwc_columns(uint32_t &S, int &count, const RwcQ &q, uint32_t l0,
 
 // Columns D0 .. D0+7 of the word (the first `live` of them with TAIL).
 template <int E, bool EDGE, int D0, bool TAIL = false>
-SS_HD void rwc_chunk(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
+SS_HD void rwc_chunk(RwcSurv<E> &S, int &count, const RwcQ &q, uint32_t rlo,
                      uint32_t rhi, int live = 8)
 {
     const uint32_t l0 = spread4(rlo >> D0), h0 = spread4(rhi >> D0);
@@ -124,7 +164,7 @@ SS_HD void rwc_chunk(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
 // (the row end, or the count past E), else -1.  A chunk is an edge chunk
 // when one of its rows reads a query index below 0 or at/after m.
 template <int E, int D0>
-SS_HD int rwc_chunk_at(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
+SS_HD int rwc_chunk_at(RwcSurv<E> &S, int &count, const RwcQ &q, uint32_t rlo,
                        uint32_t rhi, int base, int m)
 {
     const int c0 = base + D0;
@@ -139,13 +179,13 @@ SS_HD int rwc_chunk_at(uint32_t &S, int &count, const RwcQ &q, uint32_t rlo,
     return count > E ? E + 1 : -1;
 }
 
-// Route one pair of length m with threshold E (1 <= E <= 15); returns
-// min(count, E+1), equal to rw_route's.
+// Route one pair of length m with threshold E (1 <= E <= 31); returns
+// min(count, E+1), equal to rw_route's.  Reads the Q words up to the one
+// after the word being walked (planes k+1), as rw_route does.
 template <int E, class Seq>
 SS_HD int rw_route_cols(const Seq &Qs, const Seq &Rs, int m)
 {
-    static_assert(E >= 1 && E <= 15, "2E+1 rows in one word");
-    constexpr uint32_t kAll = (1u << (2 * E + 1)) - 1u;
+    static_assert(E >= 1 && E <= 31, "2E+1 rows in at most two words");
     const int W32 = (m + 31) >> 5;
     RwcQ q;
     q.lo_p = q.hi_p = q.v_p = 0u;  // before the query: case 4
@@ -153,7 +193,7 @@ SS_HD int rw_route_cols(const Seq &Qs, const Seq &Rs, int m)
     Qs.planes(1, q.lo_n, q.hi_n);
     q.v_c = mask_below(m);
     q.v_n = mask_below(m - 32);
-    uint32_t S = kAll;
+    RwcSurv<E> S;
     int count = 0;
     for (int k = 0; k < W32; ++k) {
         const int base = k << 5;

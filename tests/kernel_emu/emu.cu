@@ -43,7 +43,7 @@ template <int E>
 int cols_one(const uint32_t *q, const uint32_t *r, int m, bool staged)
 {
     const int w16 = (m + 15) / 16;
-    if constexpr (E >= 1 && E <= 15) {
+    if constexpr (E >= 1 && E <= 31) {
         if (staged)
             return rw_route_cols<E>(SmemSeqPad{q}, SmemSeqPad{r}, m);
         return rw_route_cols<E>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m);
@@ -257,7 +257,7 @@ int emu_rw_exact(const uint32_t *q, const uint32_t *r, int m, int E)
 int emu_rw_cols(const uint32_t *q, const uint32_t *r, int m, int E)
 {
     return cols_dispatch(E, q, r, m, false,
-                         std::make_integer_sequence<int, 16>{});
+                         std::make_integer_sequence<int, 32>{});
 }
 
 // Both, over staged words (cols: the column walk, else row-wise).
@@ -266,7 +266,7 @@ int emu_rw_staged(const uint32_t *q, const uint32_t *r, int m, int E,
 {
     if (cols)
         return cols_dispatch(E, q, r, m, true,
-                             std::make_integer_sequence<int, 16>{});
+                             std::make_integer_sequence<int, 32>{});
     return exact_dispatch(E, q, r, m, true,
                           std::make_integer_sequence<int, 32>{});
 }

@@ -48,11 +48,12 @@ def test_rw_exact_matches_oracle(emu, m):
 @pytest.mark.parametrize("m", [1, 2, 7, 8, 9, 15, 16, 17, 31, 32, 33, 40,
                                64, 65, 100, 150, 250, 257])
 def test_rw_cols_matches_oracle(emu, m):
-    """Column-at-a-time routine: every E it supports, lengths around the
-    8-column chunks and 32-column words, edges on both sides."""
+    """Column-at-a-time routine: every E it supports (one survivor word to
+    E = 15, two from 16 to 31), lengths around the 8-column chunks and
+    32-column words, edges on both sides."""
     for Q, R in pairs(1700 + m, 40, m, synth.rate_recipe(0.12)):
         q, r = packed(Q), packed(R)
-        for E in range(1, 16):
+        for E in range(1, 32):
             got = emu.emu_rw_cols(P(q), P(r), m, E)
             want = oracle.filter_pair(Q, R, E).obstacles
             assert got == want, (m, E, Q, R)
@@ -65,7 +66,7 @@ def test_rw_cols_headline_recipe(emu):
     for i in range(400):
         Q, R = reads[i].tobytes(), refs[i].tobytes()
         q, r = packed(Q), packed(R)
-        for E in (2, 4, 5, 6, 8, 10, 15):
+        for E in (2, 4, 5, 6, 8, 10, 15, 16, 20, 31):
             assert emu.emu_rw_cols(P(q), P(r), 100, E) == \
                 oracle.filter_pair(Q, R, E).obstacles, (i, E)
 
@@ -175,7 +176,7 @@ def test_staged_reads_ignore_what_follows(emu, m):
         for E in range(32):
             want = oracle.filter_pair(Q, R, E).obstacles
             assert emu.emu_rw_staged(P(q), P(r), m, E, 0) == want, (m, E)
-            if 1 <= E <= 15:
+            if 1 <= E <= 31:
                 got = emu.emu_rw_staged(P(q), P(r), m, E, 1)
                 assert got == want, ("cols", m, E)
         for E in (0, 2, 5, 9, 15, 31):
