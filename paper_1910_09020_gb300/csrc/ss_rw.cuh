@@ -16,7 +16,7 @@
 // turn the row word into a mask whose AND (or OR) over rows has its lowest
 // (highest) set bit at the farthest first obstacle -- the end of the
 // longest escape segment -- found with one find-first per iteration
-// (rw_word_smear and rw_word_borrow below).  When a run crosses into the
+// (rw_word_smear below).  When a run crosses into the
 // next word, the rows that already met an obstacle since the checkpoint
 // are kept in a bitmask and count as blocked until the next obstacle is
 // found, so runs spanning words are exact.
@@ -89,22 +89,12 @@ struct GlobalSeq {
     }
 };
 
-// Index of the highest set bit of x (x != 0).
-SS_HD int flo32(uint32_t x)
-{
-#ifdef __CUDA_ARCH__
-    return 31 - __clz((int)x);
-#else
-    return 31 - __builtin_clz(x);
-#endif
-}
-
 // Greedy routing inside one 32-column word (Section 2.4 steps 2-4) on its
 // maze row words Z (row r = diagonal r - EMAX), entered with the
 // checkpoint at or before the word start.  deadbits: rows that met an
 // obstacle since that checkpoint (runs continued from the previous word);
 // on return it holds them for the next word, or 0.  count and finished
-// advance as the greedy does.  Two forms, equal results:
+// advance as the greedy does.
 //
 // Smear-AND (plain kernel E <= 4, bucketed kernel): with x_s = Z_s masked to
 // columns >= c, x_s | -x_s sets every bit at or above row s's first
@@ -169,115 +159,6 @@ SS_HD void rw_word_smear(const uint32_t (&Z)[NR], RowBits &deadbits,
     }
 }
 
-// Row flags stacked by funnel shifts (row 0 arrived first, so it sits
-// highest: rows 0..31 at bits min(NR,32)-1-r of lo, rows 32.. at bits
-// NR-1-r of hi) -> a mask with bit r for row r.
-template <class RowBits, int NR>
-SS_HD RowBits rev_rows(uint32_t lo, uint32_t hi)
-{
-    constexpr int NLO = NR < 32 ? NR : 32;
-#ifdef __CUDA_ARCH__
-    RowBits out = (RowBits)(__brev(lo) >> (32 - NLO));
-    if constexpr (NR > 32)
-        out |= (RowBits)(__brev(hi) >> (64 - NR)) << 32;
-#else
-    RowBits out = 0;
-    for (int r = 0; r < NLO; ++r)
-        out |= (RowBits)((lo >> (NLO - 1 - r)) & 1u) << r;
-    if constexpr (NR > 32)
-        for (int r = 32; r < NR; ++r)
-            out |= (RowBits)((hi >> (NR - 1 - r)) & 1u) << r;
-#endif
-    return out;
-}
-
-// Borrow (plain kernel E = 5 and E >= 16): Z_s - 2^cl borrows through the
-// row's zeros from the checkpoint bit cl up to its first obstacle p_s, so
-// Z_s ^ (Z_s - 2^cl) sets exactly bits cl..p_s, and the OR over rows has its
-// highest set bit at max_s p_s: two operations per row and iteration -- the
-// subtraction a multiply-add on the FMA pipe, the logic op on the ALU pipe
-// -- and a find-leading-one per iteration.  A row with no obstacle up to bit
-// 31 borrows out and sets bits cl..31, like an obstacle at bit 31, so bit 31
-// of the OR sends the iteration to an exact per-row test.  The fixed cost
-// per iteration is higher than the smear-AND form's, which stays faster up
-// to nine rows.
-template <int NR, class RowBits>
-SS_HD void rw_word_borrow(const uint32_t (&Z)[NR], RowBits &deadbits,
-                          int base, int m, int E, int &count,
-                          bool &finished, uint32_t neg1)
-{
-    constexpr RowBits kAllRows = (RowBits)(((RowBits)1 << NR) - 1);
-    int cl = 0;  // checkpoint bit
-    for (;;) {
-        const uint32_t npc = (1u << cl) * neg1;  // -2^cl
-        // 1, re-derived every iteration: a multiplier the compiler can
-        // neither fold nor hoist, so z * one_i + npc stays one multiply-add
-        // per row (a hoisted z * 1 would cost a register per row and turn
-        // the subtraction into an ALU add)
-        const uint32_t one_i = (npc * neg1) >> cl;
-        uint32_t B = 0;
-        if (deadbits) {
-            // runs continued from the previous word (cl = 0): rows that
-            // already met an obstacle since the checkpoint read as blocked
-            // at bit 0
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t z =
-                    Z[r] | (uint32_t)((deadbits >> r) & (RowBits)1);
-                B |= z ^ (z * one_i + npc);
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-                B |= Z[r] ^ (Z[r] * one_i + npc);
-        }
-        int e;  // end of the escape segment
-        if (B >> 31) {
-            // a run reaches bit 31.  Row r met an obstacle in bits cl..31
-            // iff Z - 2^cl did not borrow out, i.e. iff bit 31 of
-            // ~(Z - 2^cl) | Z is set; funnel shifts stack those bits.
-            uint32_t d_lo = 0u, d_hi = 0u;  // rows 0..31, rows 32..
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t y = ~(Z[r] * one_i + npc) | Z[r];
-                if (r < 32)
-                    d_lo = funnel_l(y, d_lo, 1);
-                else
-                    d_hi = funnel_l(y, d_hi, 1);
-            }
-            const RowBits d = deadbits | rev_rows<RowBits, NR>(d_lo, d_hi);
-            if (d != kAllRows) {
-                deadbits = d;  // a live row runs past the word end
-                return;
-            }
-            e = base + 31;  // every run ends by bit 31, one exactly there
-        } else {
-            e = base + flo32(B);
-        }
-        deadbits = 0;  // an obstacle ends every run: fresh checkpoint
-        if (e >= m) {  // reached the destination
-            finished = true;
-            return;
-        }
-        ++count;          // its obstacle
-        if (count > E) {  // delay exceeds E: reject
-            finished = true;
-            return;
-        }
-        const int c = e + 1;  // new checkpoint
-        if (c >= base + 32)
-            return;
-        cl = c - base;
-    }
-}
-
-// rw_word_borrow for the plain kernel's row-wise threshold E = 5 (11 rows;
-// from kRwColsMinE on the plain kernels walk columns instead).  The
-// bucketed kernel (E at run time, 2 EMAX + 1 rows) keeps the smear-AND
-// form: with the borrow form its two-length batches at E of 7-10 % of the
-// length ran 2 % slower.
-constexpr int kRwBorrowMinE = 5;
-
 // Route one pair of length m with threshold E (E == EMAX when EXACT);
 // returns min(count, E+1).  Rows |s| > min(E, EMAX) are never built.
 // neg1 must hold 0xffffffff: the subtractions are multiply-adds by values
@@ -337,11 +218,7 @@ SS_HD int rw_route(const Seq &Qs, const Seq &Rs, int m, int E, uint32_t neg1)
             Z[r] = z;
         }
         // Greedy routing inside word k (checkpoint c <= base on entry).
-        if constexpr (EXACT && EMAX >= kRwBorrowMinE)
-            rw_word_borrow<NR>(Z, deadbits, base, m, E, count, finished,
-                               neg1);
-        else
-            rw_word_smear<NR>(Z, deadbits, base, m, E, count, finished, neg1);
+        rw_word_smear<NR>(Z, deadbits, base, m, E, count, finished, neg1);
         // slide the Q window by one word
         qlo_p = qlo_c;
         qhi_p = qhi_c;
@@ -431,7 +308,7 @@ __device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
 
 // The plain kernels walk the greedy one column at a time (rw_route_cols)
 // from E = kRwColsMinE on, and row-wise (rw_route) below.
-constexpr int kRwColsMinE = 6;
+constexpr int kRwColsMinE = 5;
 
 // The plain kernels' routine for threshold E: min(count, E+1).
 template <int E, class Seq>
@@ -439,7 +316,7 @@ __device__ __forceinline__ int rw_route_plain(const Seq &q, const Seq &r,
                                               int m, uint32_t neg1)
 {
     if constexpr (E >= kRwColsMinE)
-        return rw_route_cols<E>(q, r, m);
+        return rw_route_cols<E>(q, r, m, neg1);
     else
         return rw_route<E, true>(q, r, m, E, neg1);
 }

@@ -45,8 +45,10 @@ int cols_one(const uint32_t *q, const uint32_t *r, int m, bool staged)
     const int w16 = (m + 15) / 16;
     if constexpr (E >= 1 && E <= 31) {
         if (staged)
-            return rw_route_cols<E>(SmemSeqPad{q}, SmemSeqPad{r}, m);
-        return rw_route_cols<E>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m);
+            return rw_route_cols<E>(SmemSeqPad{q}, SmemSeqPad{r}, m,
+                                    0xffffffffu);
+        return rw_route_cols<E>(GlobalSeq{q, w16}, GlobalSeq{r, w16}, m,
+                                0xffffffffu);
     } else {
         return -100;
     }
