@@ -149,7 +149,7 @@ int run_bucketed(ss_ctx *ctx, const ssk::PairSet &ps, cudaStream_t st,
     if (!use_graph) {
         SS_CUDA(ssk::launch_bucketed(ps, ws, ctx->tune, ctx->d_status,
                                      ctx->sm_count, st, ctx->side, ctx->fork,
-                                     ctx->join, &launches));
+                                     ctx->join, false, &launches));
         ctx->counters.launches += launches;
         return SS_OK;
     }
@@ -183,7 +183,7 @@ int run_bucketed(ss_ctx *ctx, const ssk::PairSet &ps, cudaStream_t st,
     cudaError_t le = ssk::launch_bucketed(ps, ws, ctx->tune, ctx->d_status,
                                           ctx->sm_count, ctx->stream,
                                           ctx->side, ctx->fork, ctx->join,
-                                          &launches);
+                                          true, &launches);
     cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
         if (graph)

@@ -14,6 +14,8 @@
 #pragma once
 #include <cstdint>
 
+#include "ss_rw_config.h"
+
 namespace ssk {
 
 constexpr int kRwClasses = 5;
@@ -156,10 +158,24 @@ struct PairSet {
 // Workspace of the bucketing pass (device).
 struct BucketWs {
     int *hist;      // kKeys
+    int *ndeferred; // tiles listed in deferred (zeroed with hist)
     int *cursor;    // kKeys
     int *ranges;    // 2 * kClasses: [begin, end) per class in perm
     unsigned *counters;  // kClasses work counters of the persistent kernels
+    int32_t *deferred;   // input tiles (of kRwThreads pairs) left to the classes
     int32_t *perm;  // n pair indices, grouped by key
+};
+
+// Arguments of k_seg_direct (ss_seg.cu): groups of kSegGroup input tiles of
+// kRwThreads pairs per CTA.
+constexpr int kSegGroup = 8;
+struct SegArgs {
+    PairSet ps;
+    BucketWs ws;
+    TuneParams tp;
+    int64_t ntiles;  // ceil(n / kRwThreads)
+    uint32_t neg1;   // 0xffffffff (see rw_route)
+    int *status;
 };
 
 }  // namespace ssk

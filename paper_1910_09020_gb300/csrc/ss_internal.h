@@ -44,11 +44,18 @@ cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
 // per device (called by ss_create, ss_server_start and the allocation-free
 // entry before any capture; safe to call from several host threads).
 cudaError_t bucket_init();
+// conditional: st is being captured; every class kernel goes into an IF
+// node that the pass switches on only when its class has pairs.
 cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
                             const TuneParams &tp, int *status, int sm_count,
                             cudaStream_t st, cudaStream_t side,
                             cudaEvent_t fork, cudaEvent_t join,
-                            int *launches);
+                            bool conditional, int *launches);
+// The first kernel of the pass (ss_seg.cu): uniform input tiles routed on
+// the plain pipeline, the others classified and listed.
+struct SegArgs;
+size_t seg_smem_bytes();
+cudaError_t launch_seg_direct(const SegArgs &a, cudaStream_t st);
 
 // Accuracy harness (ss_verify.cu): banded edit distance, E <= kEdMaxE.
 constexpr int kEdMaxE = 31;

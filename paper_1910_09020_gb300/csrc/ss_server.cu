@@ -287,7 +287,7 @@ int launch_batch(ss_server *s, int slot_idx, std::vector<Request *> &take)
     if (e == cudaSuccess)
         e = ssk::launch_bucketed(ps, ssk::bucket_ws_at(ws, n), ssk::TuneParams(),
                                  b->status, share, st, sl.side, sl.fork,
-                                 sl.join, &launches);
+                                 sl.join, false, &launches);
     if (e == cudaSuccess) {
         const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * s->sm_count);
         k_mark_bad<<<g, 256, 0, st>>>(b->bad, n, b->acc, b->obs);
