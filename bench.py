@@ -426,24 +426,34 @@ def _oracle_model(host, L, E, idx):
     """Oracle time and the op model (per threshold group, the cheaper of
     the row-word and column formulations) on a sample of pairs.  Returns
     (seconds, alu ops, xu ops, cells)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
     reads, refs, off = host
-    t = alu = xu = cells = 0.0
-    for e in np.unique(E[idx]):
+
+    def group(e):
+        # one threshold group on one host thread (the oracle's call
+        # releases the interpreter, so groups run side by side)
         sel = idx[E[idx] == e]
         sub_r = np.concatenate([reads[off[i]:off[i] + L[i]] for i in sel])
         sub_f = np.concatenate([refs[off[i]:off[i] + L[i]] for i in sel])
         so = np.zeros(len(sel) + 1, np.int64)
         np.cumsum(L[sel], out=so[1:])
-        t0 = time.perf_counter()
         _, _, (c, w, it, col) = oracle.filter_batch(sub_r, sub_f, L[sel],
                                                     E[sel], offsets=so,
+                                                    threads=1,
                                                     with_stats=True)
-        t += time.perf_counter() - t0
         a_, x_, _ = model_ops(int(e), w, it, col)  # the cheaper form
-        alu += a_
-        xu += x_
-        cells += c
+        return a_, x_, c
+
+    t0 = time.perf_counter()
+    groups = np.unique(E[idx])
+    with ThreadPoolExecutor(oracle.default_threads()) as ex:
+        res = list(ex.map(group, groups[::-1]))  # largest E first
+    t = time.perf_counter() - t0
+    alu = sum(r[0] for r in res)
+    xu = sum(r[1] for r in res)
+    cells = sum(r[2] for r in res)
     return t, alu, xu, cells
 
 
@@ -468,23 +478,31 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
     persistent = lambda: F.filter(pq, pr, offsets=dwo, lengths=dL, E=dE,
                                   out_accept=acc, out_obstacles=obs)
     t_p = _time_ms(persistent, 10, F.sync)
-    # per-length launches: pairs are sorted by length, so each distinct
-    # length is a fixed-stride block of the same packed buffers
-    starts = np.flatnonzero(np.r_[True, L[1:] != L[:-1]])
-    ends = np.r_[starts[1:], n]
+    # the same batch without the persistent form: pairs are sorted by
+    # length, so each distinct length the plain kernel covers (E <= 31,
+    # m <= 1024) is one fixed-stride plain launch over the same packed
+    # buffers; the pairs it does not cover (the longer ones, E > 31) can
+    # only go through one bucketed call of their own
+    plain_ok = (E <= binding.PLAIN_MAX_E) & (L <= binding.PLAIN_MAX_M)
+    k_tail = int(np.argmin(plain_ok)) if not plain_ok.all() else n
+    assert plain_ok[:k_tail].all() and not plain_ok[k_tail:].any()
+    starts = np.flatnonzero(np.r_[True, L[1:k_tail] != L[:k_tail - 1]])
+    ends = np.r_[starts[1:], k_tail]
     acc2 = torch.empty_like(acc)
     obs2 = torch.empty_like(obs)
 
-    def per_length():
+    def per_class_plain():
         for a, b in zip(starts, ends):
-            m = int(L[a])
-            F.filter(pq[int(woff[a]):], pr[int(woff[a]):], m=m, e=int(E[a]),
-                     n=int(b - a), out_accept=acc2[a:b],
-                     out_obstacles=obs2[a:b],
-                     flags=binding.SS_FLAG_NO_GRAPH)
+            F.filter(pq[int(woff[a]):], pr[int(woff[a]):], m=int(L[a]),
+                     e=int(E[a]), n=int(b - a), out_accept=acc2[a:b],
+                     out_obstacles=obs2[a:b])
+        if k_tail < n:
+            F.filter(pq, pr, offsets=dwo[k_tail:], lengths=dL[k_tail:],
+                     E=dE[k_tail:], out_accept=acc2[k_tail:],
+                     out_obstacles=obs2[k_tail:])
     if not per_length_too:
         return {"persistent_graph_ms": t_p, "pairs": n}
-    t_l = _time_ms(per_length, 2, F.sync)
+    t_l = _time_ms(per_class_plain, 5, F.sync)
     same = bool(torch.equal(acc, acc2) and torch.equal(obs, obs2))
     bases = int(L.sum())
     bytes_alg = float(np.sum(2 * ((L.astype(np.int64) + 3) // 4) + 5 + 16))
@@ -495,9 +513,13 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
         "persistent_graph": {"ms": t_p, "pairs_per_s": n / (t_p * 1e-3),
                              "gbases_per_s": bases / (t_p * 1e-3) / 1e9,
                              "tuning": {"rw_max_e": rmax, "cw_subgrid": k}},
-        "per_length_launches": {"ms": t_l, "pairs_per_s": n / (t_l * 1e-3),
-                                "groups": int(len(starts))},
-        "persistent_over_per_length": t_l / t_p,
+        "per_class_plain": {
+            "ms": t_l, "pairs_per_s": n / (t_l * 1e-3),
+            "plain_launches": int(len(starts)), "plain_pairs": k_tail,
+            "bucketed_tail_pairs": n - k_tail,
+            "form": "one plain launch per distinct length with E <= 31 and "
+                    "m <= 1024, one bucketed call for the longer pairs"},
+        "per_class_plain_over_persistent": t_l / t_p,
         "results_identical": same,
         "accept_rate": float(acc.float().mean().item()),
     }
@@ -520,7 +542,7 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
     roof = {"t_hbm_ms": 1e3 * t_hbm, "algorithmic_bytes": bytes_alg}
     if want_cpu:
         rng = np.random.default_rng(seed)
-        idx = np.sort(rng.choice(n, 1500, replace=False))
+        idx = np.sort(rng.choice(n, 20000, replace=False))
         t_o, alu, xu, cells = _oracle_model(host, L, E, idx)
         scale = n / len(idx)
         t_alu = alu * scale / ipk["lop3"]
@@ -548,18 +570,32 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
     return out
 
 
-def run_two_lengths(F) -> dict:
+def _fixed_model(reads, refs, m, E):
+    """Op model (the cheaper formulation, see K_COL) of fixed-length pairs:
+    per-pair ALU and find-first ops from the oracle's counters."""
+    import oracle
+    _, _, (_, w, it, col) = oracle.filter_batch(reads, refs, m, E,
+                                                with_stats=True)
+    alu, xu, _ = model_ops(E, w, it, col)
+    return alu / len(reads), xu / len(reads)
+
+
+def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
     """10M pairs of 250 bp and 10M of 150 bp, edit rate U[0, 0.12], E = 0 %
-    .. 10 % of length: two plain launches against one persistent graph."""
+    .. 10 % of length: two plain launches against one persistent graph,
+    each with its roofline fraction (HBM bytes of the form; ALU ops of the
+    op model from the oracle's counters on `sample` pairs of each length)."""
     import torch
 
     from paper_1910_09020_gb300 import synth
     n3 = 10_000_000
     seed = 1910_09020 + 3
     rec = synth.rate_recipe(0.12)
+    samples = {}
     bufs = []
     for m, first in ((250, 0), (150, n3)):
         r, f = synth.pairs_fixed(seed, first, n3, m, rec)
+        samples[m] = (r[:sample].copy(), f[:sample].copy())
         q = F.pack(torch.from_numpy(r.reshape(-1)).cuda(), m=m, n=n3)
         g = F.pack(torch.from_numpy(f.reshape(-1)).cuda(), m=m, n=n3)
         F.sync()
@@ -602,14 +638,40 @@ def run_two_lengths(F) -> dict:
             for k, v in enumerate(F.confusion(a[sl], ed, e=e)):
                 conf[k] += v
         ta, fa, fr, tr = conf
-        rows.append({"E_pct": pct, "E": [e250, e150],
-                     "plain_pairs_per_s": 2 * n3 / (tp * 1e-3),
-                     "persistent_pairs_per_s": 2 * n3 / (tb * 1e-3),
-                     "plain_ms": tp, "persistent_ms": tb,
-                     "false_accepts": fa, "false_rejects": fr,
-                     "false_accept_rate": fa / max(fa + tr, 1)})
+        row = {"E_pct": pct, "E": [e250, e150],
+               "plain_pairs_per_s": 2 * n3 / (tp * 1e-3),
+               "persistent_pairs_per_s": 2 * n3 / (tb * 1e-3),
+               "plain_ms": tp, "persistent_ms": tb,
+               "false_accepts": fa, "false_rejects": fr,
+               "false_accept_rate": fa / max(fa + tr, 1)}
+        if ipk and hbm_gbs:
+            # algorithmic bytes: both packed sequences and the results; the
+            # persistent form also reads each pair's offset, length and E
+            b_plain = n3 * (2 * ((250 + 3) // 4) + 5 + 2 * ((150 + 3) // 4)
+                            + 5)
+            b_pers = b_plain + 2 * n3 * 16
+            alu = xu = 0.0
+            for m, e in ((250, e250), (150, e150)):
+                a_, x_ = _fixed_model(*samples[m], m, e)
+                alu += a_ * n3
+                xu += x_ * n3
+            t_alu = 1e3 * alu / ipk["lop3"]
+            t_xu = 1e3 * xu / ipk["bfind"]
+            for form, nb, ms in (("plain", b_plain, tp),
+                                 ("persistent", b_pers, tb)):
+                t_hbm = 1e3 * nb / (hbm_gbs * 1e9)
+                t = max(t_hbm, t_alu, t_xu)
+                row[form + "_roofline"] = {
+                    "bound": "hbm" if t == t_hbm else
+                             "alu" if t == t_alu else "xu",
+                    "t_hbm_ms": t_hbm, "t_alu_ms": t_alu, "t_xu_ms": t_xu,
+                    "frac": t / ms}
+        rows.append(row)
     return {"workload": "10M x 250 bp + 10M x 150 bp, edit rate U[0,0.12], "
                         "E = 0..10 % of length",
+            "roofline_note": "max(HBM, ALU, find-first) time of the form / "
+                             "measured time; ALU from the cheaper op model "
+                             f"on {sample} pairs of each length",
             "per_E": rows, "results_identical": same}
 
 
@@ -749,7 +811,31 @@ def run_compaction(F, pq, pr, acc, n, E) -> dict:
     return out
 
 
-def run_serving(seconds: float, slots: int = 2) -> dict:
+def _pool_model(pool, ipk, sample=400, seed=1910_09020 + 55):
+    """Op model of the served pool (the cheaper formulation per threshold
+    group, as for the uneven batch) from the oracle's counters on `sample`
+    pairs drawn uniformly from all of the pool's pairs: per-pair ALU and
+    find-first ops, and the oracle's time on them."""
+    counts = np.array([len(r[2]) for r in pool])
+    owner = np.repeat(np.arange(len(pool)), counts)
+    within = np.concatenate([np.arange(c) for c in counts])
+    pick = np.sort(np.random.default_rng(seed).choice(
+        len(owner), min(sample, len(owner)), replace=False))
+    offs = [np.concatenate([[0], np.cumsum(r[2])]) for r in pool]
+    L = np.array([pool[owner[i]][2][within[i]] for i in pick], np.int32)
+    E = np.array([pool[owner[i]][3][within[i]] for i in pick], np.int32)
+    rd = np.concatenate([pool[owner[i]][0][offs[owner[i]][within[i]]:
+                                           offs[owner[i]][within[i] + 1]]
+                         for i in pick])
+    rf = np.concatenate([pool[owner[i]][1][offs[owner[i]][within[i]]:
+                                           offs[owner[i]][within[i] + 1]]
+                         for i in pick])
+    off = np.concatenate([[0], np.cumsum(L.astype(np.int64))])
+    t, alu, xu, _ = _oracle_model((rd, rf, off), L, E, np.arange(len(L)))
+    return alu / len(L), xu / len(L), t, len(L)
+
+
+def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
     """Requests of 1..4096 pairs (log-uniform), lengths log-uniform
     100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
     Poisson process at 30 %, 60 % and 90 % of the measured capacity."""
@@ -796,6 +882,20 @@ def run_serving(seconds: float, slots: int = 2) -> dict:
         out["capacity"] = {"pairs_per_s": cap_pairs, "requests_per_s": cap_req,
                            "gbases_per_s": sum(int(r[2].sum()) for r in pool)
                            / dt / 1e9}
+        if ipk:
+            # the burst's roofline: the pool's ALU work (op model) at the
+            # LOP3 peak against the measured burst; the host link and HBM
+            # bytes (2 m ASCII bytes per pair) are far below their rates
+            alu, xu, t_o, k = _pool_model(pool, ipk)
+            t_alu = alu * pairs / ipk["lop3"]
+            t_xu = xu * pairs / ipk["bfind"]
+            t = max(t_alu, t_xu)
+            out["capacity"]["roofline"] = {
+                "bound": "alu" if t == t_alu else "xu",
+                "t_alu_s": t_alu, "t_xu_s": t_xu, "burst_s": dt,
+                "alu_ops_per_pair": alu, "frac": t / dt,
+                "sample": f"op model from the oracle on {k} pairs drawn "
+                          f"uniformly from the pool ({t_o:.1f} s)"}
         loads = []
         for frac in (0.3, 0.6, 0.9):
             rate = frac * cap_req
@@ -1055,9 +1155,10 @@ def run_ours(args):
             F, ipk, peaks["hbm_gbs"], not args.no_cpu,
             n=args.batched_pairs)
         torch.cuda.empty_cache()
-        extras["plain_vs_persistent_two_lengths"] = run_two_lengths(F)
+        extras["plain_vs_persistent_two_lengths"] = run_two_lengths(
+            F, ipk, peaks["hbm_gbs"])
         torch.cuda.empty_cache()
-        extras["served"] = run_serving(args.serve_seconds)
+        extras["served"] = run_serving(args.serve_seconds, ipk=ipk)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s",
         "gbases_per_s": value * M / 1e9, "n_gpus": world,

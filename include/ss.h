@@ -62,6 +62,10 @@ extern "C" {
 #define SS_MODE_BUCKETED 2 /* length/threshold-bucketed persistent launch      */
 #define SS_FLAG_NO_GRAPH 16 /* do not replay the captured CUDA graph           */
 
+/* Largest uniform E and m the plain launch covers. */
+#define SS_PLAIN_MAX_E 31
+#define SS_PLAIN_MAX_M 1024
+
 typedef struct ss_ctx ss_ctx;
 
 /* Create a context on CUDA device `device` with a workspace budget of
@@ -159,12 +163,17 @@ int ss_check_wait_timeout(ss_ctx *ctx, int64_t limit_ns, void *stream);
 
 /* ---- batch scheduling of mixed batches (not in the paper: its GPU
  * version runs one thread per pair, Section 2.6) --------------------------
- * A batch with per-pair lengths or thresholds (or E > 31, or m > 1024) is
- * filtered in the bucketed form: every pair is classified by (m, E') with
- * E' = min(E, m-1), pairs are grouped by class and length (longest first),
- * and one persistent kernel per class routes its pairs from an atomic work
- * queue; the whole sequence is captured once in a CUDA graph and replayed
- * for identical arguments.  Two knobs change speed, never results:
+ * A batch with per-pair lengths or thresholds (or E > SS_PLAIN_MAX_E, or
+ * m > SS_PLAIN_MAX_M) is filtered in the bucketed form.  Its first kernel
+ * walks the batch in tiles of 128 consecutive pairs: a tile whose pairs
+ * share one m <= 256 and one E <= SS_PLAIN_MAX_E and lie back to back
+ * (pair p + 1's words right after pair p's) is routed at once, as the
+ * plain launch routes it.  Every other pair is classified by (m, E') with
+ * E' = min(E, m-1), grouped by class and length (longest first), and one
+ * persistent kernel per class routes its pairs from an atomic work queue.
+ * The whole sequence is captured once in a CUDA graph and replayed for
+ * identical arguments; in the graph a class kernel runs only when its
+ * class has pairs.  Two knobs change speed, never results:
  *   rw_max_e   15 or 31: largest E' routed with one thread per pair (above
  *              it, one warp or one CTA per pair, rows across the lanes);
  *   cw_subgrid 4, 8 or 16: columns evaluated across all rows per step by

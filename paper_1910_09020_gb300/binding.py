@@ -32,6 +32,10 @@ SS_MODE_PLAIN = 1
 SS_MODE_BUCKETED = 2
 SS_FLAG_NO_GRAPH = 16
 
+# largest uniform E and m the plain launch covers (SS_PLAIN_MAX_E/_M)
+PLAIN_MAX_E = 31
+PLAIN_MAX_M = 1024
+
 # every symbol include/ss.h declares (checked by the CPU tests)
 EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",

@@ -133,6 +133,9 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // torch's default stream handle is 0).
 cudaStream_t pick_stream(void *stream) { return (cudaStream_t)stream; }
 
+static_assert(SS_PLAIN_MAX_E == ssk::kRwMaxE && SS_PLAIN_MAX_M == ssk::kRwMaxM,
+              "the header states the plain launch's limits");
+
 bool plain_ok(int32_t m, int32_t e)
 {
     return e <= ssk::kRwMaxE && m <= ssk::kRwMaxM;
