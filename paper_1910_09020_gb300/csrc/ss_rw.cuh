@@ -307,18 +307,28 @@ __device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
 }
 
 // The plain kernels walk the greedy one column at a time (rw_route_cols)
-// from E = kRwColsMinE on, and row-wise (rw_route) below.
-constexpr int kRwColsMinE = 5;
+// from E = kRwColsMinE on, and at E = kRwColsMinE - 1 for reads of at most
+// kRwColsShortM bases; row-wise (rw_route) below.  Measured on GB300 (10M
+// pairs, edit rate U[0, 0.12]): at E = 5 row-wise 1.07 against 1.27 ms at
+// 250 bp and 0.72 against 0.79 ms at 150 bp, but the walk 1.14 against
+// 1.18 ms at 100 bp (30M pairs); from E = 6 the walk at every length.
+constexpr int kRwColsMinE = 6;
+constexpr int kRwColsShortM = 128;
 
 // The plain kernels' routine for threshold E: min(count, E+1).
 template <int E, class Seq>
 __device__ __forceinline__ int rw_route_plain(const Seq &q, const Seq &r,
                                               int m, uint32_t neg1)
 {
-    if constexpr (E >= kRwColsMinE)
+    if constexpr (E >= kRwColsMinE) {
         return rw_route_cols<E>(q, r, m, neg1);
-    else
+    } else if constexpr (E == kRwColsMinE - 1) {
+        if (m <= kRwColsShortM)
+            return rw_route_cols<E>(q, r, m, neg1);
         return rw_route<E, true>(q, r, m, E, neg1);
+    } else {
+        return rw_route<E, true>(q, r, m, E, neg1);
+    }
 }
 
 // Plain launch for long reads: uniform m and E, one thread per pair, one CTA
