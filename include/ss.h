@@ -354,6 +354,8 @@ typedef struct ss_server_stats {
     int64_t device_bytes_in_use;
     double latency_p50_s, latency_p99_s, latency_max_s;
     double span_s;          /* first submission to last completion       */
+    int64_t long_pairs_queued; /* pairs routed by the long-pair queue    */
+    int64_t worker_launches;   /* launches of its long-lived worker      */
 } ss_server_stats;
 int ss_server_create(ss_server **out, int device, size_t hbm_budget_bytes,
                      int slots);

@@ -69,7 +69,9 @@ class ServerStats(ctypes.Structure):
                 ("latency_p50_s", ctypes.c_double),
                 ("latency_p99_s", ctypes.c_double),
                 ("latency_max_s", ctypes.c_double),
-                ("span_s", ctypes.c_double)]
+                ("span_s", ctypes.c_double),
+                ("long_pairs_queued", ctypes.c_int64),
+                ("worker_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

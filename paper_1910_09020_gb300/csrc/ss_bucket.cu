@@ -116,6 +116,42 @@ __global__ void __launch_bounds__(kRwThreads)
     }
 }
 
+// Serving: put the pairs of the CTA-per-pair classes that the long-pair
+// queue takes into its ring (one thread per pair; an entry is published
+// by its seq, written after the entry's other fields).  The batch's
+// descriptor already holds how many there are (the host counts them with
+// the same rule); a different count here latches kStatusUnsupported.
+__global__ void __launch_bounds__(256)
+    k_long_enqueue(const PairSet ps, const BucketWs ws, const LongHook h,
+                   int expect, int *status)
+{
+    __shared__ int s_n;
+    if (threadIdx.x == 0)
+        s_n = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int cls = kRwClasses + kCwwClasses; cls < kClasses; ++cls) {
+        const int begin = ws.ranges[2 * cls], end = ws.ranges[2 * cls + 1];
+        for (int i = begin + (int)threadIdx.x; i < end; i += blockDim.x) {
+            const int64_t p = ws.perm[i];
+            const int m = ps.len(p);
+            if (!long_queued(cls, m, eff_threshold(m, ps.thr(p))))
+                continue;
+            const unsigned long long pos = atomicAdd(h.q.tail, 1ull);
+            LongEntry *e = h.q.ring + (pos & (kLongRing - 1));
+            e->pair = p;
+            e->batch = h.batch;
+            __threadfence();
+            atomicExch(&e->seq, (uint32_t)(pos + 1));
+            ++mine;
+        }
+    }
+    atomicAdd(&s_n, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_n != expect)
+        atomicOr(status, kStatusUnsupported);
+}
+
 // Row-wise class: thread per pair, warps take 32 consecutive entries.
 template <int EMAX>
 __global__ void __launch_bounds__(128) k_rw_bucket(const CwArgs a)
@@ -415,13 +451,18 @@ cudaError_t launch_if(const ScanCond &c, Fan *fan, int h,
     return joined();
 }
 
+// counts (may be null): an upper bound of each class's pairs known on the
+// host; classes it bounds by 0 are not launched.
 template <int K>
 cudaError_t launch_cw_classes(const LaunchCfg &cfg, CwArgs a, int sm_share,
-                              const ScanCond &c, Fan *fan, cudaStream_t st)
+                              const ScanCond &c, Fan *fan, cudaStream_t st,
+                              const int64_t *counts)
 {
     cudaError_t e;
     for (int k = 0; k < kCwwClasses; ++k) {
         a.cls = kRwClasses + k;
+        if (counts && counts[a.cls] == 0)
+            continue;
         a.slice_words = cw_class_slice_words(a.cls);
         const size_t smem = (size_t)4 * a.slice_words * 4;
         if ((e = launch_if(c, fan, a.cls, k_cw_warp<K>,
@@ -432,6 +473,8 @@ cudaError_t launch_cw_classes(const LaunchCfg &cfg, CwArgs a, int sm_share,
     for (int w = 0; w < kCwcWidths; ++w)
         for (int b = 0; b < kCwcMbounds; ++b) {
             a.cls = cwc_class(w, b);
+            if (counts && counts[a.cls] == 0)
+                continue;
             a.slice_words = cw_class_slice_words(a.cls);
             const size_t smem = (size_t)a.slice_words * 4;
             if ((e = launch_if(c, fan, a.cls, k_cw_cta<K>,
@@ -444,7 +487,8 @@ cudaError_t launch_cw_classes(const LaunchCfg &cfg, CwArgs a, int sm_share,
 }
 
 cudaError_t launch_rw_classes(const LaunchCfg &cfg, CwArgs a, int sm_share,
-                              const ScanCond &c, Fan *fan, cudaStream_t st)
+                              const ScanCond &c, Fan *fan, cudaStream_t st,
+                              const int64_t *counts)
 {
     void (*const kern[kRwClasses])(CwArgs) = {
         k_rw_bucket<rw_emax(0)>, k_rw_bucket<rw_emax(1)>,
@@ -452,6 +496,8 @@ cudaError_t launch_rw_classes(const LaunchCfg &cfg, CwArgs a, int sm_share,
         k_rw_bucket<rw_emax(4)>};
     for (int k = 0; k < kRwClasses; ++k) {
         a.cls = k;
+        if (counts && counts[k] == 0)
+            continue;
         const cudaError_t e =
             launch_if(c, fan, k, kern[k], (unsigned)(cfg.rw[k] * sm_share),
                       128, 0, st, a);
@@ -511,7 +557,9 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
                             const TuneParams &tp, int *status, int sm_count,
                             cudaStream_t st, cudaStream_t side,
                             cudaEvent_t fork, cudaEvent_t join,
-                            bool conditional, int *launches)
+                            bool conditional, int *launches,
+                            const LongHook *hook, int hook_expect,
+                            const int64_t *class_counts)
 {
     if (ps.n <= 0)
         return cudaSuccess;
@@ -528,6 +576,14 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
     *launches += 3;
     const int sh = sm_count;  // persistent grids span this many SMs
     CwArgs a{ps, ws, 0, 0};
+    if (hook) {
+        // serving: the queue's share of the CTA-per-pair classes
+        k_long_enqueue<<<1, 256, 0, st>>>(ps, ws, *hook, hook_expect, status);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+        a.queued = 1;
+        *launches += 1;
+    }
     Fan fan;
     cudaStream_t cw_st = st;
     if (conditional) {
@@ -541,12 +597,13 @@ cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
             return e;
         cw_st = side;
     }
-    if ((e = launch_rw_classes(*cfg, a, sh, c, &fan, st)) != cudaSuccess)
+    const int64_t *cc = class_counts;
+    if ((e = launch_rw_classes(*cfg, a, sh, c, &fan, st, cc)) != cudaSuccess)
         return e;
     switch (tp.cw_subgrid) {
-    case 4: e = launch_cw_classes<4>(*cfg, a, sh, c, &fan, cw_st); break;
-    case 16: e = launch_cw_classes<16>(*cfg, a, sh, c, &fan, cw_st); break;
-    default: e = launch_cw_classes<8>(*cfg, a, sh, c, &fan, cw_st); break;
+    case 4: e = launch_cw_classes<4>(*cfg, a, sh, c, &fan, cw_st, cc); break;
+    case 16: e = launch_cw_classes<16>(*cfg, a, sh, c, &fan, cw_st, cc); break;
+    default: e = launch_cw_classes<8>(*cfg, a, sh, c, &fan, cw_st, cc); break;
     }
     if (e != cudaSuccess)
         return e;
@@ -583,10 +640,10 @@ cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
         cudaSuccess)
         return e;
     CwArgs a{ps, ws, 0, 0};
-    if ((e = launch_rw_classes(*cfg, a, sm_count, c, nullptr, st)) !=
-        cudaSuccess)
+    if ((e = launch_rw_classes(*cfg, a, sm_count, c, nullptr, st,
+                               nullptr)) != cudaSuccess)
         return e;
-    return launch_cw_classes<8>(*cfg, a, sm_count, c, nullptr, st);
+    return launch_cw_classes<8>(*cfg, a, sm_count, c, nullptr, st, nullptr);
 }
 
 }  // namespace ssk

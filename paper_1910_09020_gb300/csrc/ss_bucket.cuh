@@ -166,6 +166,52 @@ struct BucketWs {
     int32_t *perm;  // n pair indices, grouped by key
 };
 
+// The serving engine's device-resident queue of long pairs (ss_server.cu):
+// a ring of entries that producers (the enqueue kernel of each batch's
+// pass) fill and a long-lived worker kernel drains.  An entry is published
+// by writing its seq (= ring position + 1) last; a consumer claims position
+// h by moving head from h to h + 1 only once entry h carries seq h + 1.
+struct LongEntry {
+    int64_t pair;
+    int32_t batch;
+    uint32_t seq;
+};
+
+// One batch whose long pairs are queued: where its pairs and results live.
+struct LongBatch {
+    PairSet ps;
+    const uint8_t *bad;  // per-pair invalid-input flags (routed as -1)
+    int remaining;       // queued pairs not yet routed
+    int gen;             // written to done[] when remaining reaches 0
+};
+
+struct LongQueue {
+    LongEntry *ring;             // kLongRing entries
+    unsigned long long *tail;    // positions reserved by producers
+    unsigned long long *head;    // positions claimed by consumers
+    unsigned long long *last;    // time of the last claim by any worker
+    int *busy;                   // worker CTAs routing a pair now
+    LongBatch *batches;          // kLongBatches descriptors
+    volatile int *done;          // host-mapped: gen of each finished batch
+    volatile int *stop;          // host-mapped: workers leave when set
+};
+
+constexpr int kLongRing = 1 << 18;   // entries (a power of two)
+constexpr int kLongBatches = 64;     // descriptors
+constexpr int kLongThreads = 256;    // worker CTA width
+constexpr int kLongWords = 24 * 1024;  // worker shared words per pair
+
+// Whether the queue takes a pair of class cls (m, E'): the CTA-per-pair
+// classes whose staged planes fit the worker's shared memory.
+__host__ __device__ inline bool long_queued(int cls, int m, int Ee);
+
+// A batch's hook into the queue: its descriptor index, passed to the
+// enqueue kernel of its pass.
+struct LongHook {
+    LongQueue q;
+    int batch;
+};
+
 // Arguments of k_seg_direct (ss_seg.cu): groups of kSegGroup input tiles of
 // kRwThreads pairs per CTA.
 constexpr int kSegGroup = 8;

@@ -145,7 +145,53 @@ struct CwArgs {
     int cls;
     int slice_words;  // shared words per staged pair
     uint32_t neg1 = 0xffffffffu;  // passed at run time (see rw_route)
+    int queued = 0;   // skip the pairs the serving queue takes
 };
+
+__host__ __device__ inline bool long_queued(int cls, int m, int Ee)
+{
+    return cls >= kRwClasses + kCwwClasses &&
+           CwLayout::of(m, Ee).words() <= kLongWords;
+}
+
+// Route one pair with the whole CTA (nt threads, any number of row words):
+// the pair staged into smem, then the greedy of Section 2.4 with one CTA
+// maximum per step (red: two 32-entry buffers, buf toggles between
+// steps).  Returns min(count, E+1) (count itself is capped by the loop).
+template <int K>
+__device__ __forceinline__ int cw_cta_route(uint32_t *smem, int (*red)[32],
+                                            int &buf, const uint32_t *gq,
+                                            const uint32_t *gr, int m, int E)
+{
+    const int t = threadIdx.x;
+    const int nt = blockDim.x;
+    const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
+    const int Ee = eff_threshold(m, E);
+    const CwLayout L = CwLayout::of(m, Ee);
+    cw_stage(smem, L, gq, gr, m, t, nt);
+    __syncthreads();
+    const int nwords = (2 * Ee + 1 + 31) >> 5;
+    int c = 0, count = 0;
+    for (;;) {
+        int cand = -1;
+        for (int w = t; w < nwords; w += nt)
+            cand = imax(cand, cw_word<K>(smem, L, m, Ee, c, w));
+        cand = __reduce_max_sync(0xffffffffu, cand);
+        if (lane == 0)
+            red[buf][warp] = cand;
+        __syncthreads();
+        int v = lane < nwarp ? red[buf][lane] : -1;
+        const int pstar = __reduce_max_sync(0xffffffffu, v);
+        buf ^= 1;
+        if (pstar >= m)
+            break;
+        ++count;
+        if (count > E)
+            break;
+        c = pstar + 1;
+    }
+    return count;
+}
 
 // Warp per pair; blockDim.x / 32 warps, each with its own slice.
 template <int K>
@@ -200,8 +246,6 @@ __global__ void __launch_bounds__(1024) k_cw_cta(const CwArgs a)
     __shared__ int red[2][32];
     __shared__ int s_idx;
     const int t = threadIdx.x;
-    const int nt = blockDim.x;
-    const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
     const int begin = a.ws.ranges[2 * a.cls];
     const int end = a.ws.ranges[2 * a.cls + 1];
     int buf = 0;
@@ -214,31 +258,13 @@ __global__ void __launch_bounds__(1024) k_cw_cta(const CwArgs a)
             break;
         const int64_t p = a.ws.perm[idx];
         const int m = a.ps.len(p), E = a.ps.thr(p);
-        const int Ee = eff_threshold(m, E);
-        const CwLayout L = CwLayout::of(m, Ee);
-        const int64_t off = a.ps.off(p);
-        cw_stage(smem, L, a.ps.reads + off, a.ps.refs + off, m, t, nt);
-        __syncthreads();
-        const int nwords = (2 * Ee + 1 + 31) >> 5;
-        int c = 0, count = 0;
-        for (;;) {
-            int cand = -1;
-            for (int w = t; w < nwords; w += nt)
-                cand = imax(cand, cw_word<K>(smem, L, m, Ee, c, w));
-            cand = __reduce_max_sync(0xffffffffu, cand);
-            if (lane == 0)
-                red[buf][warp] = cand;
-            __syncthreads();
-            int v = lane < nwarp ? red[buf][lane] : -1;
-            const int pstar = __reduce_max_sync(0xffffffffu, v);
-            buf ^= 1;
-            if (pstar >= m)
-                break;
-            ++count;
-            if (count > E)
-                break;
-            c = pstar + 1;
+        if (a.queued && long_queued(a.cls, m, eff_threshold(m, E))) {
+            __syncthreads();  // s_idx is reused
+            continue;         // routed by the serving queue's worker
         }
+        const int64_t off = a.ps.off(p);
+        const int count = cw_cta_route<K>(smem, red, buf, a.ps.reads + off,
+                                          a.ps.refs + off, m, E);
         if (t == 0) {
             a.ps.acc[p] = (uint8_t)(count <= E);
             a.ps.obs[p] = count;

@@ -46,11 +46,20 @@ cudaError_t launch_bucketed_one_stream(const PairSet &ps, const BucketWs &ws,
 cudaError_t bucket_init();
 // conditional: st is being captured; every class kernel goes into an IF
 // node that the pass switches on only when its class has pairs.
+// hook (serving only, never while capturing): the CTA-per-pair pairs that
+// fit the long-pair queue's worker go into its ring (hook_expect of them)
+// instead of the class kernels.  class_counts (kClasses entries, may be
+// null): an upper bound of each class's pairs known on the host (pairs
+// the queue takes not counted); classes bounded by 0 are not launched.
+struct LongHook;
 cudaError_t launch_bucketed(const PairSet &ps, const BucketWs &ws,
                             const TuneParams &tp, int *status, int sm_count,
                             cudaStream_t st, cudaStream_t side,
                             cudaEvent_t fork, cudaEvent_t join,
-                            bool conditional, int *launches);
+                            bool conditional, int *launches,
+                            const LongHook *hook = nullptr,
+                            int hook_expect = 0,
+                            const int64_t *class_counts = nullptr);
 // The first kernel of the pass (ss_seg.cu): uniform input tiles routed on
 // the plain pipeline, the others classified and listed.
 struct SegArgs;

@@ -5,12 +5,23 @@
 // thresholds).  A scheduler thread keeps up to `slots` batches in flight:
 // whenever a slot is free it admits pending requests first-in first-out
 // while their device footprint fits the HBM budget, copies them to the
-// device, packs them, and runs the bucketed pass with persistent grids
-// sized to 1/slots of the SMs, so that a batch admitted while others run
-// executes beside them instead of queueing behind them.  A host-function
-// callback on the batch's stream timestamps completion; results stay in
-// device memory until the client fetches them.  No device-side wait exists
-// on this path: the scheduler only polls host state.
+// device (batch memory comes from a memory pool of the server's own), packs
+// them, and runs the bucketed pass with persistent grids sized to 1/slots
+// of the SMs, so that a batch admitted while others run executes beside
+// them instead of queueing behind them.
+//
+// Long pairs do not hold a slot.  The pairs of the CTA-per-pair classes
+// (thresholds above 511, or reads past 16 kbp) that fit the worker's shared
+// memory go into a device-resident ring instead of their batch's class
+// kernels, and one long-lived persistent worker kernel (one CTA per SM)
+// drains that ring for every batch: a slot frees as soon as its pass ends,
+// while its long pairs run beside later batches' work.  The worker exits
+// after a bounded idle time (or when the server stops) and the scheduler
+// relaunches it while queued pairs remain; its waits on the ring are
+// bounded.  A batch is done when its pass has ended (a host-function
+// callback on its stream) and its last queued pair is routed (the worker
+// that routes it writes the batch's generation into host-mapped memory).
+// Results stay in device memory until the client fetches them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +39,7 @@
 
 #include "../../include/ss.h"
 #include "ss_bucket.cuh"
+#include "ss_cw.cuh"
 #include "ss_device.cuh"
 #include "ss_internal.h"
 
@@ -78,6 +90,13 @@ struct Batch {
     std::atomic<bool> done{false};
     double t_done = 0;
     std::vector<char> host_meta;  // staging of offsets/lengths/E
+    // long-pair queue: descriptor index (-1: none queued), generation,
+    // queued pairs, and the descriptor's host staging
+    int lq_batch = -1;
+    int lq_gen = 0;
+    int64_t nlong = 0;
+    ssk::LongBatch lq_desc{};
+    bool pass_seen = false;  // the pass ended (slot released)
 };
 
 struct Slot {
@@ -106,10 +125,24 @@ struct ss_server {
     bool stop = false;
     std::thread thread;
     int64_t max_batch_pairs = 1 << 20;
+    cudaMemPool_t pool = nullptr;  // the server's own batch memory
+    // long-pair queue: device ring, counters and descriptors (lq_dev),
+    // host-mapped done flags and stop word (lq_host), the worker's stream
+    ssk::LongQueue lq{};
+    void *lq_dev = nullptr;
+    int *lq_host = nullptr;
+    cudaStream_t wst = nullptr;
+    cudaEvent_t wev = nullptr;
+    bool worker_launched = false;
+    std::vector<int> lq_free;        // free descriptor indices
+    int lq_gen = 0;
+    int64_t lq_inflight = 0;         // queued pairs not yet routed
+    std::vector<std::shared_ptr<Batch>> draining;  // pass ended, long pairs left
     // statistics
     std::vector<double> latencies;
     int64_t done_requests = 0, done_pairs = 0, done_bases = 0;
     int64_t batches = 0, max_inflight_seen = 0;
+    int64_t long_queued = 0, worker_launches = 0;
     double t_first_submit = 0, t_last_done = 0;
     int sticky_error = SS_OK;
 };
@@ -150,6 +183,129 @@ __global__ void k_mark_bad(const uint8_t *__restrict__ bad, int64_t n,
         }
 }
 
+// The worker's idle bound: it leaves after this long without a queued pair
+// (long enough to stay through the gaps between requests under load).
+constexpr uint64_t kWorkerIdleNs = 100000000ull;  // 100 ms
+constexpr uint32_t kWorkerMaxPolls = 1u << 22;
+
+// Claim the next published entry of the ring: its batch (>= 0) and pair,
+// or -1 once no worker CTA is routing a pair and none has claimed one for
+// idle_ns (or after kWorkerMaxPolls polls), or the server asked the workers
+// to stop.  So the CTAs leave together: one that left while others still
+// route long pairs would shrink a kernel that keeps running, and the host
+// relaunches only a finished one.  A successful claim counts the CTA busy
+// (the caller ends that with long_done).
+__device__ int long_claim(const ssk::LongQueue &q, uint64_t idle_ns,
+                          int64_t &pair)
+{
+    uint64_t t0 = 0;
+    uint32_t sleep_ns = 32;
+    for (uint32_t polls = 0; polls < kWorkerMaxPolls; ++polls) {
+        if (*q.stop)
+            return -1;
+        const unsigned long long h =
+            *(volatile unsigned long long *)q.head;
+        const ssk::LongEntry *e = q.ring + (h & (ssk::kLongRing - 1));
+        const uint32_t seq = *(volatile const uint32_t *)&e->seq;
+        if (seq == (uint32_t)(h + 1)) {
+            if (atomicCAS(q.head, h, h + 1) == h) {
+                *(volatile unsigned long long *)q.last = ssk::global_ns();
+                atomicAdd(q.busy, 1);
+                __threadfence();
+                pair = *(volatile const int64_t *)&e->pair;
+                return *(volatile const int32_t *)&e->batch;
+            }
+            continue;  // another CTA took it: try the next one at once
+        }
+        const uint64_t now = ssk::global_ns();
+        if (t0 == 0)
+            t0 = now;
+        const uint64_t last = *(volatile unsigned long long *)q.last;
+        const uint64_t since = last > t0 ? last : t0;
+        if (now > since && now - since > idle_ns &&
+            *(volatile int *)q.busy == 0)
+            return -1;
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 4096)
+            sleep_ns *= 2;
+    }
+    return -1;
+}
+
+// The long-lived worker: each CTA takes queued pairs one at a time and
+// routes each with the whole CTA (Section 2.4, rows across the threads);
+// the CTA that routes a batch's last queued pair publishes the batch's
+// generation to the host.  Pairs flagged as holding a non-base get
+// obstacles -1 (their batch's request fails alone, as in the pass).
+__global__ void __launch_bounds__(ssk::kLongThreads)
+    k_long_worker(const ssk::LongQueue q, uint64_t idle_ns)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ int red[2][32];
+    __shared__ int64_t s_pair;
+    __shared__ int s_batch;
+    const int t = threadIdx.x;
+    int buf = 0;
+    for (;;) {
+        if (t == 0) {
+            int64_t p = 0;
+            s_batch = long_claim(q, idle_ns, p);
+            s_pair = p;
+        }
+        __syncthreads();
+        const int b = s_batch;
+        if (b < 0)
+            break;
+        const int64_t p = s_pair;
+        const ssk::PairSet ps = q.batches[b].ps;
+        const uint8_t *bad = q.batches[b].bad;
+        const int m = ps.len(p), E = ps.thr(p);
+        int count = -1;
+        if (!(bad && bad[p])) {
+            const int64_t off = ps.off(p);
+            count = ssk::cw_cta_route<8>(smem, red, buf, ps.reads + off,
+                                         ps.refs + off, m, E);
+        }
+        if (t == 0) {
+            ps.acc[p] = (uint8_t)(count >= 0 && count <= E);
+            ps.obs[p] = count;
+            __threadfence();
+            if (atomicSub(&q.batches[b].remaining, 1) == 1) {
+                __threadfence_system();
+                q.done[b] = q.batches[b].gen;
+                __threadfence_system();
+            }
+            atomicSub(q.busy, 1);
+        }
+        __syncthreads();  // the slice and s_batch are reused
+    }
+}
+
+size_t worker_smem() { return (size_t)ssk::kLongWords * 4; }
+
+// Launch the worker if work is in flight (want, or queued pairs remain)
+// and none is running.  It is launched ahead of each batch's kernels: its
+// CTAs need a share of every SM that the batches' persistent grids would
+// otherwise fill.
+void ensure_worker(ss_server *s, bool want = false)
+{
+    if (!want && s->lq_inflight <= 0)
+        return;
+    if (s->worker_launched && cudaEventQuery(s->wev) == cudaErrorNotReady)
+        return;
+    (void)cudaGetLastError();
+    k_long_worker<<<s->sm_count, ssk::kLongThreads, worker_smem(), s->wst>>>(
+        s->lq, kWorkerIdleNs);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaEventRecord(s->wev, s->wst) != cudaSuccess) {
+        (void)cudaGetLastError();
+        s->sticky_error = SS_ERR_CUDA;
+        return;
+    }
+    s->worker_launched = true;
+    s->worker_launches += 1;
+}
+
 void CUDART_CB on_batch_done(void *arg)
 {
     Batch *b = (Batch *)arg;
@@ -184,7 +340,8 @@ int launch_batch(ss_server *s, int slot_idx, std::vector<Request *> &take)
     const size_t a_u8 = align_up((size_t)n, 256);
     b->bytes = a_ws + 2 * a_ascii + 2 * a_pk + 2 * a_i64 + 2 * a_i32 +
                2 * a_u8 + a_i32 + 256;
-    if (cudaMallocAsync(&b->dev, b->bytes, sl.st) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&b->dev, b->bytes, s->pool, sl.st) !=
+        cudaSuccess) {
         (void)cudaGetLastError();
         return SS_ERR_OOM;
     }
@@ -284,10 +441,55 @@ int launch_batch(ss_server *s, int slot_idx, std::vector<Request *> &take)
     ps.obs = b->obs;
     int launches = 0;
     const int share = std::max(1, s->sm_count / s->nslots);
+    ensure_worker(s, true);
+    // the long pairs the queue takes (the device's enqueue applies the
+    // same rule), if a descriptor and ring room are free
+    // and the pairs of every class (the pass launches only the classes
+    // that have some: an empty class kernel of the CTA-per-pair classes
+    // would still wait for shared memory beside the queue's worker)
+    int64_t nlong = 0;
+    std::vector<int64_t> counts(ssk::kClasses, 0), queued(ssk::kClasses, 0);
+    {
+        const ssk::TuneParams tp;
+        for (int64_t k = 0; k < n; ++k) {
+            const int m = h_len[k], E = h_E[k];
+            const int cls = ssk::class_of_tuned(m, E, tp);
+            if (cls < 0)
+                continue;
+            counts[cls] += 1;
+            if (ssk::long_queued(cls, m, ssk::eff_threshold(m, E))) {
+                queued[cls] += 1;
+                ++nlong;
+            }
+        }
+    }
+    ssk::LongHook hook;
+    const ssk::LongHook *hp = nullptr;
+    if (nlong > 0 && !s->lq_free.empty() &&
+        s->lq_inflight + nlong <= ssk::kLongRing) {
+        for (int c = 0; c < ssk::kClasses; ++c)
+            counts[c] -= queued[c];
+        b->lq_batch = s->lq_free.back();
+        s->lq_free.pop_back();
+        b->lq_gen = ++s->lq_gen;
+        b->nlong = nlong;
+        b->lq_desc.ps = ps;
+        b->lq_desc.bad = b->bad;
+        b->lq_desc.remaining = (int)nlong;
+        b->lq_desc.gen = b->lq_gen;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->lq.batches + b->lq_batch, &b->lq_desc,
+                                sizeof(ssk::LongBatch),
+                                cudaMemcpyHostToDevice, st);
+        hook.q = s->lq;
+        hook.batch = b->lq_batch;
+        hp = &hook;
+    }
     if (e == cudaSuccess)
         e = ssk::launch_bucketed(ps, ssk::bucket_ws_at(ws, n), ssk::TuneParams(),
                                  b->status, share, st, sl.side, sl.fork,
-                                 sl.join, false, &launches);
+                                 sl.join, false, &launches, hp,
+                                 hp ? (int)nlong : 0, counts.data());
     if (e == cudaSuccess) {
         const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * s->sm_count);
         k_mark_bad<<<g, 256, 0, st>>>(b->bad, n, b->acc, b->obs);
@@ -299,7 +501,12 @@ int launch_batch(ss_server *s, int slot_idx, std::vector<Request *> &take)
         (void)cudaGetLastError();
         cudaStreamSynchronize(st);
         cudaFreeAsync(b->dev, st);
+        // a descriptor whose enqueue may have run is not reused
         return SS_ERR_CUDA;
+    }
+    if (b->nlong > 0) {
+        s->lq_inflight += b->nlong;
+        s->long_queued += b->nlong;
     }
     const double t = now_s();
     for (Request *r : take) {
@@ -323,56 +530,90 @@ void maybe_free_batch(ss_server *s, const std::shared_ptr<Batch> &b)
     }
 }
 
+// A batch whose pass has ended and whose queued pairs are all routed:
+// read its status words and complete its requests.  Lock held.
+void finish_batch(ss_server *s, const std::shared_ptr<Batch> &b, double t_done)
+{
+    int dev_status = 0;
+    int st = SS_OK;
+    if (read_back(s, &dev_status, b->status, sizeof(int)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = SS_ERR_CUDA;
+    }
+    // a bad base fails its own request only
+    if (dev_status & ssk::kStatusInvalidBase) {
+        b->host_bad.resize((size_t)b->n);
+        if (read_back(s, b->host_bad.data(), b->bad, (size_t)b->n) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            st = SS_ERR_CUDA;
+        }
+    }
+    if (st == SS_OK && (dev_status & ssk::kStatusUnsupported))
+        st = SS_ERR_UNSUPPORTED;
+    for (Request *r : b->reqs) {
+        r->state = kDone;
+        r->status = st;
+        if (!b->host_bad.empty())
+            for (int64_t k = 0; k < r->n; ++k)
+                if (b->host_bad[(size_t)(r->first + k)]) {
+                    r->status = SS_ERR_INVALID_BASE;
+                    break;
+                }
+        r->t_done = t_done;
+        s->latencies.push_back(r->t_done - r->t_submit);
+        s->done_requests += 1;
+        s->done_pairs += r->n;
+        s->done_bases += r->bases;
+    }
+    s->t_last_done = std::max(s->t_last_done, t_done);
+    if (b->lq_batch >= 0) {
+        s->lq_free.push_back(b->lq_batch);
+        s->lq_inflight -= b->nlong;
+        b->lq_batch = -1;
+    }
+}
+
+// The queued pairs of batch b are all routed (the worker published its
+// generation to the host-mapped done word).
+bool drained(const ss_server *s, const Batch &b)
+{
+    return b.lq_batch < 0 ||
+           ((volatile const int *)s->lq_host)[b.lq_batch] == b.lq_gen;
+}
+
 void scheduler(ss_server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lock(s->mu);
     while (!s->stop) {
-        // completions
+        // completions: a slot frees when its pass ends; the batch completes
+        // once its queued long pairs are routed as well
         bool any_done = false;
         for (Slot &sl : s->slots) {
             std::shared_ptr<Batch> b = sl.running;
             if (!b || !b->done.load(std::memory_order_acquire))
                 continue;
-            int dev_status = 0;
-            int st = SS_OK;
-            if (read_back(s, &dev_status, b->status, sizeof(int)) !=
-                cudaSuccess) {
-                (void)cudaGetLastError();
-                st = SS_ERR_CUDA;
-            }
-            // a bad base fails its own request only
-            if (dev_status & ssk::kStatusInvalidBase) {
-                b->host_bad.resize((size_t)b->n);
-                if (read_back(s, b->host_bad.data(), b->bad, (size_t)b->n) !=
-                    cudaSuccess) {
-                    (void)cudaGetLastError();
-                    st = SS_ERR_CUDA;
-                }
-            }
-            if (st == SS_OK && (dev_status & ssk::kStatusUnsupported))
-                st = SS_ERR_UNSUPPORTED;
-            for (Request *r : b->reqs) {
-                r->state = kDone;
-                r->status = st;
-                if (!b->host_bad.empty())
-                    for (int64_t k = 0; k < r->n; ++k)
-                        if (b->host_bad[(size_t)(r->first + k)]) {
-                            r->status = SS_ERR_INVALID_BASE;
-                            break;
-                        }
-                r->t_done = b->t_done;
-                s->latencies.push_back(r->t_done - r->t_submit);
-                s->done_requests += 1;
-                s->done_pairs += r->n;
-                s->done_bases += r->bases;
-            }
-            s->t_last_done = std::max(s->t_last_done, b->t_done);
             sl.running.reset();
+            b->pass_seen = true;
+            s->draining.push_back(b);
+        }
+        for (size_t i = 0; i < s->draining.size();) {
+            std::shared_ptr<Batch> b = s->draining[i];
+            if (!drained(s, *b)) {
+                ++i;
+                continue;
+            }
+            finish_batch(s, b, std::max(b->t_done, b->nlong ? now_s() : 0.0));
+            s->draining.erase(s->draining.begin() + (long)i);
             any_done = true;
         }
         if (any_done)
             s->cv_done.notify_all();
+        bool busy = !s->pending.empty() || !s->draining.empty();
+        for (const Slot &sl : s->slots)
+            busy |= (bool)sl.running;
+        ensure_worker(s, busy);
         // admission: fill free slots first-in first-out within the budget;
         // a backlog is shared out over all free slots (by pairs), so a
         // burst runs on every slot instead of queueing as one batch
@@ -456,19 +697,69 @@ int ss_server_create(ss_server **out, int device, size_t hbm_budget_bytes,
     s->budget = hbm_budget_bytes ? hbm_budget_bytes : ((size_t)8 << 30);
     cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount,
                            device);
-    // keep freed batch memory in the device's pool instead of returning it
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
-        uint64_t keep = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    }
-    (void)cudaGetLastError();
-    if (ssk::bucket_init() != cudaSuccess ||
+    // batch memory from a pool of the server's own, which keeps freed
+    // blocks for the next batches (the process's default pool is left as
+    // it is)
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    uint64_t keep = UINT64_MAX;
+    // the long-pair queue: ring, counters and descriptors on the device;
+    // done words and the stop word in host-mapped memory
+    const size_t ring_bytes = sizeof(ssk::LongEntry) * ssk::kLongRing;
+    const size_t lq_bytes = ring_bytes + 256 +
+                            sizeof(ssk::LongBatch) * ssk::kLongBatches;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold,
+                                &keep) != cudaSuccess ||
+        ssk::bucket_init() != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->wst, cudaStreamNonBlocking) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&s->wev, cudaEventDisableTiming) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_long_worker,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)worker_smem()) != cudaSuccess ||
+        // an SM holding a worker CTA is set up with all its shared memory,
+        // so the batches' kernels still find room beside it (with a
+        // smaller split they waited for the worker to leave)
+        cudaFuncSetAttribute(k_long_worker,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaMalloc(&s->lq_dev, lq_bytes) != cudaSuccess ||
+        cudaMemset(s->lq_dev, 0, lq_bytes) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->lq_host,
+                      sizeof(int) * (ssk::kLongBatches + 1),
+                      cudaHostAllocMapped) != cudaSuccess) {
         (void)cudaGetLastError();
         ss_server_destroy(s);
         return SS_ERR_CUDA;
+    }
+    std::memset(s->lq_host, 0, sizeof(int) * (ssk::kLongBatches + 1));
+    {
+        char *q = (char *)s->lq_dev;
+        s->lq.ring = (ssk::LongEntry *)q;
+        s->lq.tail = (unsigned long long *)(q + ring_bytes);
+        s->lq.head = (unsigned long long *)(q + ring_bytes + 8);
+        s->lq.last = (unsigned long long *)(q + ring_bytes + 16);
+        s->lq.busy = (int *)(q + ring_bytes + 24);
+        s->lq.batches = (ssk::LongBatch *)(q + ring_bytes + 256);
+        int *hd = nullptr;
+        if (cudaHostGetDevicePointer((void **)&hd, s->lq_host, 0) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            ss_server_destroy(s);
+            return SS_ERR_CUDA;
+        }
+        s->lq.done = hd;
+        s->lq.stop = hd + ssk::kLongBatches;
+        for (int i = ssk::kLongBatches - 1; i >= 0; --i)
+            s->lq_free.push_back(i);
     }
     s->slots.resize(slots);
     for (Slot &sl : s->slots) {
@@ -502,7 +793,13 @@ int ss_server_destroy(ss_server *s)
     if (s->thread.joinable())
         s->thread.join();
     cudaSetDevice(s->device);
+    if (s->lq_host)
+        ((volatile int *)s->lq_host)[ssk::kLongBatches] = 1;  // workers leave
     cudaDeviceSynchronize();
+    for (auto &b : s->draining) {
+        b->pinned_refs = 0;
+        maybe_free_batch(s, b);
+    }
     for (auto &kv : s->reqs) {
         Request *r = kv.second.get();
         if (r->batch) {
@@ -527,6 +824,18 @@ int ss_server_destroy(ss_server *s)
     }
     if (s->copy_st)
         cudaStreamDestroy(s->copy_st);
+    if (s->wst)
+        cudaStreamDestroy(s->wst);
+    if (s->wev)
+        cudaEventDestroy(s->wev);
+    cudaDeviceSynchronize();
+    if (s->lq_dev)
+        cudaFree(s->lq_dev);
+    if (s->lq_host)
+        cudaFreeHost(s->lq_host);
+    if (s->pool)
+        cudaMemPoolDestroy(s->pool);
+    (void)cudaGetLastError();
     delete s;
     return SS_OK;
 }
@@ -652,6 +961,8 @@ int ss_server_get_stats(ss_server *s, ss_server_stats *out)
     out->max_inflight = s->max_inflight_seen;
     out->pending = (int64_t)s->pending.size();
     out->device_bytes_in_use = (int64_t)s->in_use;
+    out->long_pairs_queued = s->long_queued;
+    out->worker_launches = s->worker_launches;
     std::vector<double> v = s->latencies;
     if (!v.empty()) {
         std::sort(v.begin(), v.end());
@@ -677,6 +988,7 @@ int ss_server_reset_stats(ss_server *s)
     s->latencies.clear();
     s->done_requests = s->done_pairs = s->done_bases = 0;
     s->batches = s->max_inflight_seen = 0;
+    s->long_queued = s->worker_launches = 0;
     s->t_first_submit = s->t_last_done = 0;
     s->sticky_error = SS_OK;
     return SS_OK;

@@ -1,7 +1,8 @@
 """GPU tests of the continuous-batching server: every request's result is
 the same alone and in the mix (and equals the oracle's), a poisoned request
-fails alone, batches admitted while others run overlap, and admission
-respects the HBM budget."""
+fails alone, batches admitted while others run overlap, admission respects
+the HBM budget, and the long pairs routed by the device-resident queue's
+worker (which leaves when idle and is relaunched) equal the oracle."""
 import threading
 import time
 
@@ -121,7 +122,9 @@ def test_batches_overlap_on_the_device():
         st = S.stats()
         outs = [S.fetch(t) for t in ts]
         S.fetch(tl)
-    assert st["max_inflight"] >= 2
+    # the long pairs ran beside the short batches: in the long-pair queue's
+    # worker (their slot freed at once), or in a slot of their own
+    assert st["long_pairs_queued"] >= len(L) or st["max_inflight"] >= 2
     assert not long_done_first, "short requests waited for the long one"
     for (rc, a, o, _), r in zip(outs, short):
         oa, oo = oracle_of(r)
@@ -169,4 +172,80 @@ def test_unfetched_results_hold_the_budget():
         assert rc == binding.SS_OK
     for req, a, o in ((reqs[0], a1, o1), (reqs[1], a2, o2)):
         oa, oo = oracle_of(req)
+        assert (a == oa).all() and (o == oo).all()
+
+
+def _long_requests(seed, count, n=24):
+    """Requests mixing short pairs with long ones whose threshold (10 % of
+    6-20 kbp) puts them in the CTA-per-pair classes the queue takes."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed + i)
+        L = np.where(rng.random(n) < 0.5,
+                     rng.integers(6000, 20000, n),
+                     rng.integers(50, 400, n)).astype(np.int32)
+        E = synth.thresholds(L, 10)
+        reads, refs, off = synth.pairs_varlen(seed * 100 + i, 0, L,
+                                              synth.rate_recipe(0.12))
+        out.append((reads, refs, L, E, off))
+    return out
+
+
+def test_queued_long_pairs_equal_the_oracle():
+    reqs = _long_requests(700, 5)
+    nlong = sum(int((r[2] >= 6000).sum()) for r in reqs)
+    with binding.Server(0, hbm_budget_bytes=2 << 30, slots=2) as S:
+        ts = [S.submit(*r[:4]) for r in reqs]
+        outs = []
+        for t in ts:
+            assert S.wait(t) == binding.SS_OK
+            outs.append(S.fetch(t))
+        st = S.stats()
+    assert st["long_pairs_queued"] == nlong > 0
+    assert st["worker_launches"] >= 1
+    for (rc, a, o, _), r in zip(outs, reqs):
+        assert rc == binding.SS_OK
+        oa, oo = oracle_of(r)
+        assert (a == oa).all() and (o == oo).all()
+
+
+def test_worker_leaves_when_idle_and_is_relaunched():
+    """The worker's wait for queued pairs is bounded: with nothing queued
+    for longer than that bound it leaves, and the next request's long pairs
+    are routed by a new launch."""
+    reqs = _long_requests(800, 2)
+    with binding.Server(0, hbm_budget_bytes=2 << 30, slots=1) as S:
+        t = S.submit(*reqs[0][:4])
+        assert S.wait(t) == binding.SS_OK
+        r0 = S.fetch(t)
+        time.sleep(0.5)  # five times the worker's idle bound
+        t = S.submit(*reqs[1][:4])
+        assert S.wait(t) == binding.SS_OK
+        r1 = S.fetch(t)
+        st = S.stats()
+    assert st["worker_launches"] >= 2
+    for (rc, a, o, _), r in zip((r0, r1), reqs):
+        assert rc == binding.SS_OK
+        oa, oo = oracle_of(r)
+        assert (a == oa).all() and (o == oo).all()
+
+
+def test_bad_base_in_a_queued_pair_fails_its_request_alone():
+    reqs = _long_requests(900, 3)
+    bad = list(reqs[1])
+    k = int(np.flatnonzero(bad[2] >= 6000)[0])
+    reads = bad[0].copy()
+    reads[bad[4][k] + 17] = ord("N")
+    bad[0] = reads
+    with binding.Server(0, hbm_budget_bytes=2 << 30, slots=2) as S:
+        ts = [S.submit(*reqs[0][:4]), S.submit(*bad[:4]),
+              S.submit(*reqs[2][:4])]
+        for t in ts:
+            S.wait(t)
+        outs = [S.fetch(t) for t in ts]
+    assert outs[1][0] == binding.SS_ERR_INVALID_BASE
+    assert outs[1][2][k] == -1 and outs[1][1][k] == 0
+    for (rc, a, o, _), r in ((outs[0], reqs[0]), (outs[2], reqs[2])):
+        assert rc == binding.SS_OK
+        oa, oo = oracle_of(r)
         assert (a == oa).all() and (o == oo).all()
