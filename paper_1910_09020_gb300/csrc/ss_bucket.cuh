@@ -198,7 +198,12 @@ struct LongQueue {
 
 constexpr int kLongRing = 1 << 18;   // entries (a power of two)
 constexpr int kLongBatches = 64;     // descriptors
-constexpr int kLongThreads = 256;    // worker CTA width
+// Worker shape: one CTA of 512 threads per SM (A/B on GB300 with the
+// served workload at 2 slots: 256 threads 222k pairs/s, 512 threads 260k;
+// 768 or 1024 threads, or two CTAs per SM, left too little of the SM for
+// the batches' own kernels, which then waited for the worker to leave)
+constexpr int kLongThreads = 512;    // worker CTA width
+constexpr int kLongCtasPerSm = 1;    // worker CTAs per SM
 constexpr int kLongWords = 24 * 1024;  // worker shared words per pair
 
 // Whether the queue takes a pair of class cls (m, E'): the CTA-per-pair

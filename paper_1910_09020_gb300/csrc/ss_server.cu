@@ -294,8 +294,8 @@ void ensure_worker(ss_server *s, bool want = false)
     if (s->worker_launched && cudaEventQuery(s->wev) == cudaErrorNotReady)
         return;
     (void)cudaGetLastError();
-    k_long_worker<<<s->sm_count, ssk::kLongThreads, worker_smem(), s->wst>>>(
-        s->lq, kWorkerIdleNs);
+    k_long_worker<<<s->sm_count * ssk::kLongCtasPerSm, ssk::kLongThreads,
+                    worker_smem(), s->wst>>>(s->lq, kWorkerIdleNs);
     if (cudaGetLastError() != cudaSuccess ||
         cudaEventRecord(s->wev, s->wst) != cudaSuccess) {
         (void)cudaGetLastError();
