@@ -860,7 +860,10 @@ def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
     out = {"workload": "requests of 1..4096 pairs (log-uniform), lengths "
                        "log-uniform 100..100000 bp, edit rate U[0,0.15], "
                        "E = 10 % of length, Poisson arrivals",
-           "slots": slots}
+           "slots": slots,
+           "form": "host admission into slots; each batch's pass on its "
+                   "slot, its CTA-per-pair pairs in the device-resident "
+                   "ring drained by one long-lived worker kernel"}
     with binding.Server(0, hbm_budget_bytes=32 << 30, slots=slots) as S:
         # capacity: the whole pool at once, three times; the first warms
         # up and the faster of the other two counts (one burst's time moves
@@ -928,7 +931,9 @@ def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
                           "p99_s": st["latency_p99_s"],
                           "max_s": st["latency_max_s"],
                           "batches": st["batches"],
-                          "max_inflight": st["max_inflight"]})
+                          "max_inflight": st["max_inflight"],
+                          "long_pairs_queued": st["long_pairs_queued"],
+                          "worker_launches": st["worker_launches"]})
         out["loads"] = loads
     return out
 
