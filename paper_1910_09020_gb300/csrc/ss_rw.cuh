@@ -273,20 +273,16 @@ __device__ __forceinline__ int rw_cost_key(const uint32_t *sq,
     return k < 31 ? k : 31;
 }
 
-// Order the tile's pairs by predicted cost (counting sort on the CTA):
-// returns the pair this thread routes.  Word i of the tile's pair u is at
-// sQ[u * pair_ld + i * word_ld] (likewise sR).  s_cnt must be zero on entry.
-__device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
-                                            const uint32_t *sR, int pair_ld,
-                                            int word_ld, int w16, int np,
-                                            int *s_cnt, uint8_t *s_perm)
+// Counting sort of the tile's pairs by a cost key in 0..31 (thread t holds
+// pair t's key, t < np): returns the pair this thread routes.  s_cnt must
+// be zero on entry.
+__device__ __forceinline__ int rw_sort_keys(int key, int np, int *s_cnt,
+                                            uint8_t *s_perm)
 {
     const int t = threadIdx.x;
-    int key = 0, rank = 0;
-    if (t < np) {
-        key = rw_cost_key(sQ + t * pair_ld, sR + t * pair_ld, word_ld, w16);
+    int rank = 0;
+    if (t < np)
         rank = atomicAdd(&s_cnt[key], 1);
-    }
     __syncthreads();
     if (t < 32) {
         const int c = s_cnt[t];
@@ -304,6 +300,21 @@ __device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
         s_perm[s_cnt[key] + rank] = (uint8_t)t;
     __syncthreads();
     return s_perm[t];
+}
+
+// Order the tile's pairs by predicted cost (counting sort on the CTA):
+// returns the pair this thread routes.  Word i of the tile's pair u is at
+// sQ[u * pair_ld + i * word_ld] (likewise sR).  s_cnt must be zero on entry.
+__device__ __forceinline__ int rw_sort_tile(const uint32_t *sQ,
+                                            const uint32_t *sR, int pair_ld,
+                                            int word_ld, int w16, int np,
+                                            int *s_cnt, uint8_t *s_perm)
+{
+    const int t = threadIdx.x;
+    const int key = t < np ? rw_cost_key(sQ + t * pair_ld, sR + t * pair_ld,
+                                         word_ld, w16)
+                           : 0;
+    return rw_sort_keys(key, np, s_cnt, s_perm);
 }
 
 // The plain kernels walk the greedy one column at a time (rw_route_cols)

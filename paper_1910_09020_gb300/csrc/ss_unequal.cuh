@@ -233,4 +233,51 @@ SS_HD int rw_route2_cols(const Seq &Qs, int mQ, const Seq &Rs, int mR,
     return count <= E ? count : E + 1;
 }
 
+// The routine of the row class EMAX (rows 2 EMAX + 1): row-wise for 7 and
+// 63 rows, the column walk for 15 and 31.
+template <int EMAX, class Seq>
+SS_HD int unequal_route(const Seq &q, int mQ, const Seq &r, int mR, int E,
+                        uint32_t neg1)
+{
+    if constexpr (EMAX >= 7 && EMAX <= 15)
+        return rw_route2_cols<EMAX>(q, mQ, r, mR, E);
+    else
+        return rw_route2<EMAX>(q, mQ, r, mR, E, neg1);
+}
+
+// Predicted routing cost of a staged pair of different lengths: the fewest
+// mismatches over reference columns 16..31 on any diagonal of the pair's
+// band, |s| <= min(E, 16).  A read inside a reference window with a
+// random flank of o bases matches on diagonal -o, away from the centre;
+// columns 16..31 read query bases (not the flank) on every such diagonal,
+// so each diagonal counts 16 comparisons.  Words 0..3 of the query and
+// 0..1 of the reference are read (whatever follows a short pair's words in
+// its slot only blurs the estimate).
+SS_HD int uq_cost_key(const uint32_t *sq, const uint32_t *sr, int E)
+{
+    uint32_t qlo, qhi, qlo_n, qhi_n, rlo, rhi;
+    planes_of(sq[0], sq[1], qlo, qhi);
+    planes_of(sq[2], sq[3], qlo_n, qhi_n);
+    planes_of(sr[0], sr[1], rlo, rhi);
+    const int band = E < 16 ? E : 16;
+    int k = 16;
+    for (int s = -band; s <= band; ++s) {
+        uint32_t ql, qh;
+        if (s >= 0) {
+            ql = funnel_r(qlo, qlo_n, (uint32_t)s);
+            qh = funnel_r(qhi, qhi_n, (uint32_t)s);
+        } else {
+            ql = qlo << -s;
+            qh = qhi << -s;
+        }
+        const uint32_t mis = ((ql ^ rlo) | (qh ^ rhi)) & 0xffff0000u;
+#ifdef __CUDA_ARCH__
+        k = imin(k, __popc(mis));
+#else
+        k = imin(k, __builtin_popcount(mis));
+#endif
+    }
+    return k;
+}
+
 }  // namespace ssk

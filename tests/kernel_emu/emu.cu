@@ -182,6 +182,27 @@ int emu_unequal(const uint32_t *q, int mQ, const uint32_t *r, int mR, int E)
     return -2;
 }
 
+// The unequal-length routine of the kernel's class for the pair's rows,
+// reading the pair in place from buffers whose words continue past the
+// sequences (as in a shared-memory slot): count, or -2 past 31 rows.
+int emu_unequal_staged(const uint32_t *q, int mQ, const uint32_t *r, int mR,
+                       int E)
+{
+    const SmemSeqPad Q{q}, R{r};
+    const int rows = unequal_rows(mQ, mR, E);
+    if (rows < 0)
+        return 0;
+    if (rows <= 3)
+        return unequal_route<3>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 7)
+        return unequal_route<7>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 15)
+        return unequal_route<15>(Q, mQ, R, mR, E, 0xffffffffu);
+    if (rows <= 31)
+        return unequal_route<31>(Q, mQ, R, mR, E, 0xffffffffu);
+    return -2;
+}
+
 // Both unequal-length routines at every class they support (form 0:
 // row-wise, 1: column walk; -2 past the class table or the form's rows).
 int emu_unequal_form(const uint32_t *q, int mQ, const uint32_t *r, int mR,

@@ -250,6 +250,31 @@ def test_unequal_lengths_match_oracle(emu):
                 assert got in (want, -2), (form, mq, mr, E, got, want)
 
 
+def test_unequal_staged_reads_ignore_what_follows(emu):
+    """The unequal-length tile kernel routes a pair in place in its
+    shared-memory slot, where the words after its sequences are another
+    pair's (or leftovers): the routine of each row class must give the
+    oracle's result whatever those words hold, at lengths to 256."""
+    rng = np.random.default_rng(12)
+
+    def slot(seq):
+        w = (len(seq) + 15) // 16
+        junk = rng.integers(0, 2**32, 8, dtype=np.uint64).astype(np.uint32)
+        return np.concatenate([oracle.pack_reference(seq)[:w], junk])
+
+    for i in range(240):
+        mq = int(rng.integers(1, 257))
+        mr = int(min(256, max(1, mq + rng.choice([-20, -5, -1, 0, 3, 9, 16]))))
+        rec = synth.rate_recipe(float(rng.choice([0.02, 0.1, 0.3])))
+        Q, R = pairs(3100 + i, 1, max(mq, mr), rec)[0]
+        Q, R = Q[:mq], R[:mr]
+        q, r = slot(Q), slot(R)
+        for E in (0, 2, 3, 5, 7, 10, 15, 16, 31):
+            want = oracle.filter_unequal(Q, R, E).obstacles
+            got = emu.emu_unequal_staged(P(q), mq, P(r), mr, E)
+            assert got in (want, -2), (mq, mr, E, got, want)
+
+
 @pytest.mark.parametrize("K", [4, 8, 16])
 def test_cw_long_reads_match_oracle(emu, K):
     """Column-wise routine on long reads at E = 10 % of the length: edge
