@@ -249,3 +249,40 @@ def test_bad_base_in_a_queued_pair_fails_its_request_alone():
         assert rc == binding.SS_OK
         oa, oo = oracle_of(r)
         assert (a == oa).all() and (o == oo).all()
+
+
+def test_queue_ring_wraps_around():
+    """More queued pairs than the ring holds (2^18), in four requests one
+    after another: the ring's positions wrap and every result still equals
+    the oracle's.  The pairs are 600 bp at E = 520 (the CTA-per-pair class
+    the queue takes); most are a read against itself (one greedy step each),
+    one in fifty carries edits."""
+    import torch  # noqa: F401  (the server needs the CUDA runtime up)
+    n = 80_000
+    outs, reqs = [], []
+    with binding.Server(0, hbm_budget_bytes=8 << 30, slots=2) as S:
+        for k in range(4):
+            rng = np.random.default_rng(500 + k)
+            L = np.full(n, 600, np.int32)
+            E = np.full(n, 520, np.int32)
+            reads, refs, off = synth.pairs_varlen(600 + k, 0, L,
+                                                  synth.rate_recipe(0.05))
+            same = rng.random(n) >= 0.02
+            refs = refs.reshape(n, 600)
+            refs[same] = reads.reshape(n, 600)[same]
+            refs = refs.reshape(-1)
+            t = S.submit(reads, refs, L, E)
+            assert S.wait(t, timeout_s=300.0) == binding.SS_OK
+            outs.append(S.fetch(t))
+            reqs.append((reads, refs, L, E, off, same))
+        st = S.stats()
+    assert st["long_pairs_queued"] == 4 * n > (1 << 18)
+    for (rc, a, o, _), (reads, refs, L, E, off, same) in zip(outs, reqs):
+        assert rc == binding.SS_OK
+        assert (a[same] == 1).all() and (o[same] == 0).all()
+        idx = np.flatnonzero(~same)
+        sub = np.concatenate([np.arange(off[i], off[i] + 600) for i in idx])
+        so = np.arange(len(idx) + 1, dtype=np.int64) * 600
+        oa, oo = oracle.filter_batch(reads[sub], refs[sub], L[idx], E[idx],
+                                     offsets=so)
+        assert (a[idx] == oa).all() and (o[idx] == oo).all()
