@@ -1,137 +1,14 @@
-// ss_unequal.cu -- kernel for pairs of different lengths, thread per pair.
+// ss_unequal.cu -- launches for pairs of different lengths, thread per
+// pair (the kernel is in ss_unequal_tile.cuh).
 //
-// Pairs are routed by the launch of their row class (E' <= 3, 7, 15, 31):
-// one launch when the threshold is uniform (its class bounds every pair's
-// rows), else one per class, each walking all pairs and skipping the
-// others.  The first launch also writes the pairs that need no routing and
-// flags the invalid and unsupported ones.
-#include <cuda_runtime.h>
-
-#include <cstdint>
-
-#include "ss_internal.h"
-#include "ss_rw.cuh"
-#include "ss_unequal.cuh"
+// A uniform threshold e gets one launch with the routine for exactly e
+// (ss_unequal_x0.cu, ss_unequal_x1.cu); per-pair thresholds get one launch
+// per row class (E' <= 3, 7, 15, 31), each walking all pairs and skipping
+// the others.  The first launch also writes the pairs that need no routing
+// and flags the invalid and unsupported ones.
+#include "ss_unequal_tile.cuh"
 
 namespace ssk {
-
-struct UnequalArgs {
-    const uint32_t *reads;
-    const int64_t *read_off;  // words
-    const int32_t *read_len;  // bases
-    const uint32_t *refs;
-    const int64_t *ref_off;
-    const int32_t *ref_len;
-    const int32_t *E;         // per pair, or nullptr: e for all
-    int32_t e;
-    int64_t n;
-    uint8_t *acc;
-    int32_t *obs;
-    int *status;
-};
-
-// How a pair is handled: answered or left to another class (0), or routed
-// by this launch (1).
-enum UqMode { kUqNone = 0, kUqRoute = 1 };
-constexpr int kUqGroup = 1;  // tiles per CTA (A/B at 2M pairs: 1 ahead of 2, 4, 8)
-
-// The words of a pair's first bases for the cost key (0 past its end).
-__device__ __forceinline__ void uq_head(const uint32_t *g, int w16,
-                                        uint32_t (&w)[4])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        w[i] = i < w16 ? __ldg(g + i) : 0u;
-}
-
-// Thread per pair over tiles of kRwThreads consecutive pairs, kUqGroup
-// tiles per CTA: each tile's pairs of this row class (rows in
-// ELO+1..EMAX) are ordered by the flank-aware cost key, so that a warp
-// holds pairs of similar routing work, and each is routed from global
-// memory by the thread the order assigns it to.  (Staging the pairs in
-// shared memory first, gathered half a warp per pair, was slower: 0.17
-// against 0.11 ms at E = 2 on 2M pairs, the gather's load latency exposed
-// before every tile.)  With ELO < 0
-// the launch also answers the pairs that need no routing and flags the
-// invalid and unsupported ones.
-template <int EMAX, int ELO>
-__global__ void __launch_bounds__(kRwThreads) k_unequal_tile(
-    const UnequalArgs a)
-{
-    __shared__ int s_mq[kRwThreads], s_mr[kRwThreads], s_e[kRwThreads];
-    __shared__ int64_t s_qo[kRwThreads], s_ro[kRwThreads];
-    __shared__ uint8_t s_mode[kRwThreads];
-    __shared__ int s_cnt[32];
-    __shared__ uint8_t s_perm[kRwThreads];
-    const int t = threadIdx.x;
-    if (t < 32)
-        s_cnt[t] = 0;
-    int bad = 0;
-    const int64_t ntiles = (a.n + kRwThreads - 1) / kRwThreads;
-    for (int j = 0; j < kUqGroup; ++j) {
-        const int64_t tile = (int64_t)blockIdx.x * kUqGroup + j;
-        if (tile >= ntiles)
-            break;
-        const int64_t p0 = tile * kRwThreads;
-        const int np = (int)min((int64_t)kRwThreads, a.n - p0);
-        const int64_t p = p0 + t;
-        int mQ = 0, mR = 0, E = 0, mode = kUqNone, key = 31;
-        int64_t qo = 0, ro = 0;
-        if (t < np) {
-            mQ = a.read_len[p];
-            mR = a.ref_len[p];
-            E = a.E ? a.E[p] : a.e;
-            const int rows =
-                (mQ < 0 || mR < 0 || E < 0) ? -2 : unequal_rows(mQ, mR, E);
-            if (rows == -2) {
-                if (ELO < 0) {
-                    a.acc[p] = 0;
-                    a.obs[p] = -1;
-                    bad |= kStatusInvalidArg;
-                }
-            } else if (rows < 0) {
-                if (ELO < 0) {
-                    a.acc[p] = 1;
-                    a.obs[p] = 0;
-                }
-            } else if (rows > kRwMaxE) {
-                if (ELO < 0) {
-                    a.acc[p] = 0;
-                    a.obs[p] = -1;
-                    bad |= kStatusUnsupported;
-                }
-            } else if (rows > ELO && rows <= EMAX) {
-                mode = kUqRoute;
-                qo = a.read_off[p];
-                ro = a.ref_off[p];
-                uint32_t wq[4], wr[4];
-                uq_head(a.reads + qo, (mQ + 15) >> 4, wq);
-                uq_head(a.refs + ro, (mR + 15) >> 4, wr);
-                key = uq_cost_key(wq, wr, E);
-            }
-        }
-        s_mq[t] = mQ;
-        s_mr[t] = mR;
-        s_e[t] = E;
-        s_qo[t] = qo;
-        s_ro[t] = ro;
-        s_mode[t] = (uint8_t)mode;
-        const int u = rw_sort_keys(key, np, s_cnt, s_perm);
-        if (t < np && s_mode[u] == kUqRoute) {
-            const int uq = s_mq[u], ur = s_mr[u], uE = s_e[u];
-            const GlobalSeq q{a.reads + s_qo[u], (uq + 15) >> 4};
-            const GlobalSeq r{a.refs + s_ro[u], (ur + 15) >> 4};
-            const int cnt = unequal_route<EMAX>(q, uq, r, ur, uE, 0xffffffffu);
-            a.acc[p0 + u] = (uint8_t)(cnt <= uE);
-            a.obs[p0 + u] = cnt;
-        }
-        if (t < 32)
-            s_cnt[t] = 0;
-        __syncthreads();  // metadata and the sort buffers are free
-    }
-    if (bad)
-        atomicOr(a.status, bad);
-}
 
 cudaError_t launch_unequal(const uint32_t *reads, const int64_t *read_off,
                            const int32_t *read_len, const uint32_t *refs,
@@ -144,29 +21,28 @@ cudaError_t launch_unequal(const uint32_t *reads, const int64_t *read_off,
         return cudaSuccess;
     const UnequalArgs a{reads, read_off, read_len, refs, ref_off, ref_len,
                         E, e, n, acc, obs, status};
-    const int64_t ntiles = (n + kRwThreads - 1) / kRwThreads;
-    const int64_t groups = (ntiles + kUqGroup - 1) / kUqGroup;
-    if (groups > 0x7fffffff)
+    const unsigned grid = unequal_grid(n);
+    if (grid == 0)
         return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)groups;
     if (!E) {
-        // a uniform threshold bounds every pair's rows by min(e, 31): one
-        // launch of that class routes them all
-        if (e <= 3)
-            k_unequal_tile<3, -1><<<grid, kRwThreads, 0, st>>>(a);
-        else if (e <= 7)
-            k_unequal_tile<7, -1><<<grid, kRwThreads, 0, st>>>(a);
-        else if (e <= 15)
-            k_unequal_tile<15, -1><<<grid, kRwThreads, 0, st>>>(a);
-        else
-            k_unequal_tile<31, -1><<<grid, kRwThreads, 0, st>>>(a);
-        return cudaGetLastError();
+        // a uniform threshold: every pair routed for exactly that threshold
+        if (e < 0)
+            return cudaErrorInvalidValue;
+        const int ex = e < kRwMaxE ? e : kRwMaxE;
+        // e above 31 leaves pairs past 31 rows: flagged unsupported by the
+        // class launch, which also answers the others
+        if (e > kRwMaxE) {
+            k_unequal_tile<31, -1, false><<<grid, kRwThreads, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+        return ex <= 15 ? launch_unequal_exact_x0(ex, a, grid, st)
+                        : launch_unequal_exact_x1(ex, a, grid, st);
     }
     // per-pair thresholds: one launch per row class
-    k_unequal_tile<3, -1><<<grid, kRwThreads, 0, st>>>(a);
-    k_unequal_tile<7, 3><<<grid, kRwThreads, 0, st>>>(a);
-    k_unequal_tile<15, 7><<<grid, kRwThreads, 0, st>>>(a);
-    k_unequal_tile<31, 15><<<grid, kRwThreads, 0, st>>>(a);
+    k_unequal_tile<3, -1, false><<<grid, kRwThreads, 0, st>>>(a);
+    k_unequal_tile<7, 3, false><<<grid, kRwThreads, 0, st>>>(a);
+    k_unequal_tile<15, 7, false><<<grid, kRwThreads, 0, st>>>(a);
+    k_unequal_tile<31, 15, false><<<grid, kRwThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -280,4 +280,158 @@ SS_HD int uq_cost_key(const uint32_t *sq, const uint32_t *sr, int E)
     return k;
 }
 
+// ---- exact-E routines (one threshold for every pair of the launch) ------
+
+// Column D of a chunk in the frame form (ss_rwc.cuh) for a pair of
+// different lengths: where a row can leave the query (EDGE) a cell is an
+// obstacle iff it is in range and mismatched, or out of range with equal
+// lengths (nfe: all ones when the lengths are equal, else 0).
+template <int E, bool EDGE, int D>
+SS_HD void uqf_column(uint32_t &s0, int &count, const RwcF &f, uint32_t tl,
+                      uint32_t th, uint32_t two, uint32_t nfe)
+{
+    using Fr = RwcFrame<E>;
+    if constexpr (D > 0)
+        s0 = s0 * two;  // one column right: every row one bit up
+    const uint32_t bl = byte_sign<D & 3>(tl);
+    const uint32_t bh = byte_sign<D & 3>(th);
+    uint32_t t0;
+    if (EDGE) {
+        const uint32_t mis = (f.l0 ^ bl) | (f.h0 ^ bh);
+        t0 = s0 & ~((f.v0 & mis) | (~f.v0 & nfe));
+    } else {
+        t0 = s0 & ~(f.l0 ^ bl);
+        t0 &= ~(f.h0 ^ bh);
+    }
+    const bool z = t0 == 0u;  // the last free row met its obstacle here
+    count += z;
+    s0 = z ? Fr::template all_lo<D>() : t0;
+}
+
+template <int E, bool EDGE, bool TAIL, int... I>
+SS_HD void uqf_columns(uint32_t &s0, int &count, const RwcF &f, uint32_t l0,
+                       uint32_t h0, uint32_t l1, uint32_t h1, uint32_t two,
+                       uint32_t nfe, int live, std::integer_sequence<int, I...>)
+{
+    ((!TAIL || I < live
+          ? uqf_column<E, EDGE, I>(s0, count, f, I < 4 ? l0 : l1,
+                                   I < 4 ? h0 : h1, two, nfe)
+          : void()),
+     ...);
+}
+
+// The chunk of columns D0 .. D0+KC-1 of the reference word (the first
+// `live` of them with TAIL), as rwc_chunk with one survivor word.
+template <int E, bool EDGE, int D0, bool TAIL = false>
+SS_HD void uqf_chunk(uint32_t &s0, int &count, const RwcQ &q, uint32_t rlo,
+                     uint32_t rhi, uint32_t two, uint32_t nfe, int live = 8)
+{
+    using Fr = RwcFrame<E>;
+    static_assert(Fr::W == 1 && Fr::KC >= 4, "one survivor word");
+    constexpr int KC = Fr::KC;
+    constexpr int O = D0 - E;
+    RwcF f;
+    f.l0 = rwc_window<O>(q.lo_p, q.lo_c, q.lo_n);
+    f.h0 = rwc_window<O>(q.hi_p, q.hi_c, q.hi_n);
+    f.v0 = EDGE ? rwc_window<O>(q.v_p, q.v_c, q.v_n) : 0u;
+    f.l1 = f.h1 = f.v1 = 0u;
+    s0 >>= KC - 1;
+    const uint32_t l0 = spread4(rlo >> D0), h0 = spread4(rhi >> D0);
+    const uint32_t l1 = KC > 4 ? spread4(rlo >> (D0 + 4)) : 0u;
+    const uint32_t h1 = KC > 4 ? spread4(rhi >> (D0 + 4)) : 0u;
+    uqf_columns<E, EDGE, TAIL>(s0, count, f, l0, h0, l1, h1, two, nfe, live,
+                               std::make_integer_sequence<int, KC>{});
+}
+
+// Chunk D0 of the reference word at column base: the result if the walk
+// ends here (the reference's end, or the count past E), else -1.
+template <int E, int D0>
+SS_HD int uqf_chunk_at(uint32_t &s0, int &count, const RwcQ &q, uint32_t rlo,
+                       uint32_t rhi, int base, int mQ, int mR, uint32_t two,
+                       uint32_t nfe)
+{
+    constexpr int KC = RwcFrame<E>::KC;
+    const int c0 = base + D0;
+    if (c0 + KC > mR) {
+        uqf_chunk<E, true, D0, true>(s0, count, q, rlo, rhi, two, nfe,
+                                     mR - c0);
+        return count <= E ? count : E + 1;
+    }
+    if (c0 < E || c0 + KC - 1 + E >= mQ)
+        uqf_chunk<E, true, D0>(s0, count, q, rlo, rhi, two, nfe);
+    else
+        uqf_chunk<E, false, D0>(s0, count, q, rlo, rhi, two, nfe);
+    return count > E ? E + 1 : -1;
+}
+
+template <int E, int... J>
+SS_HD int uqf_word(uint32_t &s0, int &count, const RwcQ &q, uint32_t rlo,
+                   uint32_t rhi, int base, int mQ, int mR, uint32_t two,
+                   uint32_t nfe, std::integer_sequence<int, J...>)
+{
+    constexpr int KC = RwcFrame<E>::KC;
+    int res = -1;
+    ((res < 0 ? (res = uqf_chunk_at<E, J * KC>(s0, count, q, rlo, rhi, base,
+                                                mQ, mR, two, nfe),
+                 0)
+              : 0),
+     ...);
+    return res;
+}
+
+// rw_route2's result for threshold E (5 <= E <= 14), walked in the frame
+// form: one column per reference base, the 2E+1 rows in one word.
+template <int E, class Seq>
+SS_HD int rw_route2_frame(const Seq &Qs, int mQ, const Seq &Rs, int mR,
+                          uint32_t neg1)
+{
+    using Fr = RwcFrame<E>;
+    constexpr int KC = Fr::KC;
+    const uint32_t two = 4u + neg1 + neg1;
+    const uint32_t nfe = mQ == mR ? 0xffffffffu : 0u;
+    const int W32 = (mR + 31) >> 5;
+    RwcQ q;
+    q.lo_p = q.hi_p = q.v_p = 0u;  // before the query
+    Qs.planes(0, q.lo_c, q.hi_c);
+    Qs.planes(1, q.lo_n, q.hi_n);
+    q.v_c = mask_below(mQ);
+    q.v_n = mask_below(mQ - 32);
+    uint32_t s0 = Fr::template all_lo<KC - 1>();
+    int count = 0;
+    for (int k = 0; k < W32; ++k) {
+        const int base = k << 5;
+        uint32_t rlo, rhi;
+        Rs.planes(k, rlo, rhi);
+        const int res =
+            uqf_word<E>(s0, count, q, rlo, rhi, base, mQ, mR, two, nfe,
+                        std::make_integer_sequence<int, 32 / KC>{});
+        if (res >= 0)
+            return res;
+        q.lo_p = q.lo_c;
+        q.hi_p = q.hi_c;
+        q.v_p = q.v_c;
+        q.lo_c = q.lo_n;
+        q.hi_c = q.hi_n;
+        q.v_c = q.v_n;
+        Qs.planes(k + 2, q.lo_n, q.hi_n);
+        q.v_n = mask_below(mQ - 32 * (k + 2));
+    }
+    return count <= E ? count : E + 1;
+}
+
+// The routine for one threshold E shared by every pair of a launch:
+// row-wise with exactly 2E+1 rows up to E = 4 and above 15, the frame-form
+// column walk for 5..14, the column walk with shifted query windows at 15.
+template <int E, class Seq>
+SS_HD int unequal_route_exact(const Seq &q, int mQ, const Seq &r, int mR,
+                              uint32_t neg1)
+{
+    if constexpr (E >= 5 && E <= 14)
+        return rw_route2_frame<E>(q, mQ, r, mR, neg1);
+    else if constexpr (E == 15)
+        return rw_route2_cols<15>(q, mQ, r, mR, E);
+    else
+        return rw_route2<E>(q, mQ, r, mR, E, neg1);
+}
+
 }  // namespace ssk

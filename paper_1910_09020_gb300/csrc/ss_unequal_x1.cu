@@ -1,0 +1,15 @@
+// ss_unequal_x1.cu -- exact-threshold instantiations of the tile kernel
+// for pairs of different lengths, E = 16..31 (split across
+// translation units so that they compile in parallel).
+#include "ss_unequal_tile.cuh"
+
+namespace ssk {
+
+cudaError_t launch_unequal_exact_x1(int e, const UnequalArgs &a,
+                                    unsigned grid, cudaStream_t st)
+{
+    return unequal_exact_range<16>(e, a, grid, st,
+                                    std::make_integer_sequence<int, 16>{});
+}
+
+}  // namespace ssk

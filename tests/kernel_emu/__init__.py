@@ -53,6 +53,8 @@ def load():
                                      ctypes.c_int, ctypes.c_int]
     lib.emu_unequal_staged.argtypes = [P, ctypes.c_int, P, ctypes.c_int,
                                        ctypes.c_int]
+    lib.emu_unequal_exact.argtypes = [P, ctypes.c_int, P, ctypes.c_int,
+                                      ctypes.c_int]
     lib.emu_submaze.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int]
     lib.emu_submaze_rows.argtypes = [P, P, ctypes.c_int, ctypes.c_int,

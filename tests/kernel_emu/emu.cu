@@ -63,6 +63,22 @@ int cols_dispatch(int E, const uint32_t *q, const uint32_t *r, int m,
     return out;
 }
 
+template <int E>
+int uq_exact_one(const uint32_t *q, int mQ, const uint32_t *r, int mR)
+{
+    const GlobalSeq Q{q, (mQ + 15) / 16}, R{r, (mR + 15) / 16};
+    return unequal_route_exact<E>(Q, mQ, R, mR, 0xffffffffu);
+}
+
+template <int... Es>
+int uq_exact_dispatch(int E, const uint32_t *q, int mQ, const uint32_t *r,
+                      int mR, std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    ((E == Es ? (out = uq_exact_one<Es>(q, mQ, r, mR), 0) : 0), ...);
+    return out;
+}
+
 template <int EMAX>
 int runtime_one(const uint32_t *q, const uint32_t *r, int m, int E)
 {
@@ -201,6 +217,16 @@ int emu_unequal_staged(const uint32_t *q, int mQ, const uint32_t *r, int mR,
     if (rows <= 31)
         return unequal_route<31>(Q, mQ, R, mR, E, 0xffffffffu);
     return -2;
+}
+
+// The exact-threshold routine of the uniform-threshold launch.
+int emu_unequal_exact(const uint32_t *q, int mQ, const uint32_t *r, int mR,
+                      int E)
+{
+    if (unequal_rows(mQ, mR, E) < 0)
+        return 0;
+    return uq_exact_dispatch(E, q, mQ, r, mR,
+                             std::make_integer_sequence<int, 32>{});
 }
 
 // Both unequal-length routines at every class they support (form 0:

@@ -250,6 +250,25 @@ def test_unequal_lengths_match_oracle(emu):
                 assert got in (want, -2), (form, mq, mr, E, got, want)
 
 
+def test_unequal_exact_threshold_routines_match_oracle(emu):
+    """The uniform-threshold launch's routine for every E from 0 to 31
+    (row-wise, the frame-form column walk from 5 to 14, the shifted-window
+    walk at 15), on pairs of different and equal lengths around the 8-column
+    chunks, the 32-column words and the ends."""
+    rng = np.random.default_rng(13)
+    for i in range(160):
+        mq = int(rng.integers(1, 300))
+        mr = max(1, mq + int(rng.choice([-40, -9, -3, -1, 0, 1, 2, 5, 17, 70])))
+        rec = synth.rate_recipe(float(rng.choice([0.02, 0.1, 0.3])))
+        Q, R = pairs(4100 + i, 1, max(mq, mr), rec)[0]
+        Q, R = Q[:mq], R[:mr]
+        q, r = packed(Q), packed(R)
+        for E in range(32):
+            want = oracle.filter_unequal(Q, R, E).obstacles
+            got = emu.emu_unequal_exact(P(q), mq, P(r), mr, E)
+            assert got == want, (mq, mr, E, got, want)
+
+
 def test_unequal_staged_reads_ignore_what_follows(emu):
     """The unequal-length tile kernel routes a pair in place in its
     shared-memory slot, where the words after its sequences are another
