@@ -111,6 +111,7 @@ class Oracle:
                                                    ctypes.c_int, P]
         lib.sso_exhaustive_lower_bound.restype = i64
         lib.sso_pack_reference.argtypes = [P, i64, P]
+        lib.sso_pack_sliced.argtypes = [P, i64, i64, P]
         lib.sso_cell2.argtypes = [P, i64, P, i64, i64, i64, i64]
         lib.sso_cell2.restype = ctypes.c_int
         lib.sso_filter2.argtypes = [P, i64, P, i64, i64, ctypes.c_int, P, P]
@@ -281,6 +282,18 @@ class Oracle:
             raise ValueError("invalid base")
         return out[: (m + 15) // 16]
 
+    def pack_sliced(self, seqs: np.ndarray) -> np.ndarray:
+        """n sequences of m bases (uint8 array (n, m)) -> the bit-sliced
+        layout, 8 * ceil(m/4) * ceil(n/32) uint32 words."""
+        s = np.ascontiguousarray(seqs, dtype=np.uint8)
+        n, m = s.shape
+        out = np.zeros(max(8 * ((m + 3) // 4) * ((n + 31) // 32), 1),
+                       dtype=np.uint32)
+        rc = self.lib.sso_pack_sliced(_p(s), n, m, _p(out))
+        if rc != OK:
+            raise ValueError("invalid base")
+        return out[: 8 * ((m + 3) // 4) * ((n + 31) // 32)]
+
     def default_threads(self) -> int:
         return int(self.lib.sso_default_threads())
 
@@ -341,6 +354,10 @@ def filter_batch(reads, refs, lengths, Es, offsets=None, threads=0,
 
 def pack_reference(seq):
     return get().pack_reference(seq)
+
+
+def pack_sliced(seqs):
+    return get().pack_sliced(seqs)
 
 
 def default_threads():

@@ -289,6 +289,32 @@ int sso_pack_reference(const uint8_t *seq, int64_t m, uint32_t *out)
     return SSO_OK;
 }
 
+int sso_pack_sliced(const uint8_t *seq, int64_t n, int64_t m, uint32_t *out)
+{
+    const int64_t G = (n + 31) / 32;
+    const int64_t words = 8 * ((m + 3) / 4) * G;
+    for (int64_t w = 0; w < words; ++w)
+        out[w] = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t g = p / 32;
+        const uint32_t bit = 1u << (p % 32);
+        for (int64_t j = 0; j < m; ++j) {
+            uint32_t code;
+            switch (base_of(seq[p * m + j])) {
+            case 'A': code = 0; break;
+            case 'C': code = 1; break;
+            case 'G': code = 2; break;
+            case 'T': code = 3; break;
+            default: return SSO_ERR_INVALID_BASE;
+            }
+            for (int b = 0; b < 2; ++b)
+                if ((code >> b) & 1u)
+                    out[((j / 4 * G + g) * 2 + b) * 4 + j % 4] |= bit;
+        }
+    }
+    return SSO_OK;
+}
+
 int sso_default_threads(void)
 {
     long n = sysconf(_SC_NPROCESSORS_ONLN);

@@ -139,6 +139,16 @@ int64_t sso_exhaustive_lower_bound(int m, int Emax, int threads,
  * SSO_ERR_INVALID_BASE. */
 int sso_pack_reference(const uint8_t *seq, int64_t m, uint32_t *out);
 
+/* Reference packer of the library's bit-sliced format, written from its
+ * written definition: n sequences of m bases (sequence p at seq + p*m) in
+ * groups of 32 (sequence p is bit p%32 of group p/32, G = ceil(n/32)
+ * groups); bit b (0 or 1) of the code of base j of the group's sequences
+ * forms one 32-bit word, stored at index ((j/4 * G + g) * 2 + b) * 4 + j%4.
+ * Codes as above; bits of sequences p >= n and words of bases j >= m are
+ * zero.  out has 8 * ceil(m/4) * G words.  Returns SSO_OK or
+ * SSO_ERR_INVALID_BASE. */
+int sso_pack_sliced(const uint8_t *seq, int64_t n, int64_t m, uint32_t *out);
+
 /* Number of host threads the batch routines use for threads = 0. */
 int sso_default_threads(void);
 

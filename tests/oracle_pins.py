@@ -324,6 +324,41 @@ def pin_pack_reference(O):
     assert list(O.pack_reference("C" * 17)) == [0x0000FFFF, 0x00000001]
 
 
+def pin_pack_sliced(O):
+    """The library's bit-sliced format: sequence p is bit p%32 of group
+    p/32; code bit b of base j of group g is word ((j/4*G + g)*2 + b)*4 +
+    j%4.  Values by hand, then every bit against the 2-bit packer."""
+    two = np.frombuffer(b"ACGTATTTTC", np.uint8).reshape(2, 5)
+    # base j: (lo, hi) of seq 0 in bit 0, of seq 1 in bit 1
+    #   j=0 A,T  j=1 C,T  j=2 G,T  j=3 T,T  j=4 A,C
+    assert list(O.pack_sliced(two)) == [2, 3, 2, 3, 2, 2, 3, 3,
+                                        2, 0, 0, 0, 0, 0, 0, 0]
+    g33 = np.full((33, 1), ord("G"), np.uint8)  # two groups, G = 2
+    w = O.pack_sliced(g33)
+    assert len(w) == 16
+    assert (w[0], w[4], w[8], w[12]) == (0, 0xFFFFFFFF, 0, 1)
+    assert not w[[1, 2, 3, 5, 6, 7, 9, 10, 11, 13, 14, 15]].any()
+    rng = random.Random(31)
+    n, m = 70, 23
+    seqs = [rand_seq(rng, m) for _ in range(n)]
+    arr = np.frombuffer("".join(seqs).encode(), np.uint8).reshape(n, m)
+    w = O.pack_sliced(arr)
+    G = (n + 31) // 32
+    assert len(w) == 8 * ((m + 3) // 4) * G
+    for p in range(n):
+        packed = O.pack_reference(seqs[p])
+        for j in range(m):
+            for b in range(2):
+                want = (int(packed[j // 16]) >> (16 * b + j % 16)) & 1
+                got = (int(w[((j // 4 * G + p // 32) * 2 + b) * 4 + j % 4])
+                       >> (p % 32)) & 1
+                assert got == want, (p, j, b)
+    # nothing else set: pad sequences of the last group, bases past m
+    total = sum(bin(int(x)).count("1") for x in w)
+    assert total == sum(bin(int(x)).count("1")
+                        for s in seqs for x in O.pack_reference(s))
+
+
 def pin_batch_matches_single(O):
     rng = random.Random(22)
     n, m = 64, 70
@@ -527,7 +562,7 @@ ALL_PINS = [
     pin_monotone_in_E, pin_cap, pin_cap_counterexample, pin_E_at_least_m,
     pin_optimality, pin_lower_bound_random, pin_lower_bound_exhaustive,
     pin_edit_distance_textbook, pin_edit_distance_bfs, pin_case_and_invalid,
-    pin_pack_reference, pin_batch_matches_single,
+    pin_pack_reference, pin_pack_sliced, pin_batch_matches_single,
     pin_submaze_worked_example, pin_submaze_reduces_to_full,
     pin_submaze_underestimates,
     pin_unequal_equal_lengths_unchanged, pin_unequal_free_flanks,

@@ -91,6 +91,14 @@ MUTANTS = {
         "                if (sso_cell2",
         "            for (int64_t j = checkpoint; j <= mQ; ++j) {\n"
         "                if (sso_cell2"),
+    # bit-sliced packer: groups and blocks swapped in the word index
+    "sliced_index_swapped": ("out[((j / 4 * G + g) * 2 + b) * 4 + j % 4]",
+                             "out[((g * ((m + 3) / 4) + j / 4) * 2 + b) * 4"
+                             " + j % 4]"),
+    # bit-sliced packer: the two code bits' planes swapped
+    "sliced_planes_swapped": ("out[((j / 4 * G + g) * 2 + b) * 4 + j % 4]",
+                              "out[((j / 4 * G + g) * 2 + 1 - b) * 4"
+                              " + j % 4]"),
     # min-obstacle DP: a segment may hold two obstacles
     "dp_two_obstacles": (
         "                if (sso_cell(Q, R, m, E, i, e) != 0)\n"
