@@ -55,12 +55,27 @@ extern "C" {
  *   bits are zero.  ss_pack() writes this format.                          */
 #define SS_FMT_ASCII 0
 #define SS_FMT_PACKED2 1
+/* SS_FMT_SLICED2 : 2 bits per base, bit-sliced over groups of 32 pairs,
+ *   for fixed-stride batches (every pair of length m).  Pair p is bit p%32
+ *   of group g = p/32 (G = ceil(n/32) groups).  Bit b (0 or 1) of the code
+ *   of base j of the group's 32 sequences is one uint32 word, at index
+ *       ((j/4 * G + g) * 2 + b) * 4 + j%4
+ *   so four consecutive bases of one code bit are 16 contiguous bytes.
+ *   One side (reads or refs) of n pairs takes ss_sliced_words(m, n) =
+ *   8 * ceil(m/4) * G words (2 bits per base, 25 bytes per pair at m =
+ *   100); bits of pairs p >= n and words of bases j >= m are zero.
+ *   ss_pack_sliced() writes this format.  The filter walks the 32 pairs of
+ *   a group at once, one pair per bit. */
+#define SS_FMT_SLICED2 2
 
 /* ---- filter modes (flags of ss_filter_batch) -------------------------- */
 #define SS_MODE_AUTO 0     /* plain launch if m and E are uniform, else bucketed */
 #define SS_MODE_PLAIN 1    /* one launch per (m, E) group, no queue            */
 #define SS_MODE_BUCKETED 2 /* length/threshold-bucketed persistent launch      */
 #define SS_FLAG_NO_GRAPH 16 /* do not replay the captured CUDA graph           */
+
+/* Largest E of the plain launch over SS_FMT_SLICED2 input. */
+#define SS_SLICED_MAX_E 15
 
 /* Largest uniform E and m the plain launch covers. */
 #define SS_PLAIN_MAX_E 31
@@ -101,8 +116,25 @@ int ss_pack(ss_ctx *ctx, const uint8_t *ascii, const int64_t *offsets,
             const int32_t *lengths, int32_t m, int64_t n, uint32_t *packed,
             const int64_t *packed_offsets, void *stream);
 
+/* Words of the SS_FMT_SLICED2 format for n sequences of m bases:
+ * 8 * ceil(m/4) * ceil(n/32) (0 if n or m is not positive). */
+int64_t ss_sliced_words(int64_t m, int64_t n);
+
+/* Pack n fixed-stride ASCII sequences of m bases (sequence p at ascii +
+ * p*m, device) into the SS_FMT_SLICED2 format at `sliced` (device,
+ * ss_sliced_words(m, n) words, 16-byte aligned).  Every word of the output
+ * is written.  A non-ACGT byte latches SS_ERR_INVALID_BASE (returned by
+ * ss_sync), its code taken as A.  Returns SS_OK, SS_ERR_INVALID_ARG or
+ * SS_ERR_CUDA. */
+int ss_pack_sliced(ss_ctx *ctx, const uint8_t *ascii, int32_t m, int64_t n,
+                   uint32_t *sliced, void *stream);
+
 /* Filter n equal-length read/reference pairs (Section 2.4).
- *   reads, refs    device; format SS_FMT_ASCII or SS_FMT_PACKED2.  Pair p's
+ *   reads, refs    device; format SS_FMT_ASCII, SS_FMT_PACKED2 or
+ *                  SS_FMT_SLICED2 (the last with a fixed stride, uniform m,
+ *                  scalar e <= SS_SLICED_MAX_E, 16-byte aligned reads,
+ *                  refs; SS_ERR_UNSUPPORTED for a larger e or
+ *                  SS_MODE_BUCKETED).  Pair p's
  *                  query is reads + offsets[p] and its reference is
  *                  refs + offsets[p] (units: bytes for ASCII, 32-bit words
  *                  for PACKED2).  offsets == NULL means a fixed stride of m

@@ -26,6 +26,7 @@ SS_ERR_UNSUPPORTED = -7
 
 SS_FMT_ASCII = 0
 SS_FMT_PACKED2 = 1
+SS_FMT_SLICED2 = 2
 
 SS_MODE_AUTO = 0
 SS_MODE_PLAIN = 1
@@ -35,11 +36,14 @@ SS_FLAG_NO_GRAPH = 16
 # largest uniform E and m the plain launch covers (SS_PLAIN_MAX_E/_M)
 PLAIN_MAX_E = 31
 PLAIN_MAX_M = 1024
+# largest E of the plain launch over SS_FMT_SLICED2 input (SS_SLICED_MAX_E)
+SLICED_MAX_E = 15
 
 # every symbol include/ss.h declares (checked by the CPU tests)
 EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
+    "ss_sliced_words", "ss_pack_sliced",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
@@ -110,6 +114,9 @@ def load(build_if_needed: bool = True):
     lib.ss_packed_words.argtypes = [I64]
     lib.ss_packed_words.restype = I64
     lib.ss_pack.argtypes = [P, P, P, P, I32, I64, P, P, P]
+    lib.ss_sliced_words.argtypes = [I64, I64]
+    lib.ss_sliced_words.restype = I64
+    lib.ss_pack_sliced.argtypes = [P, P, I32, I64, P, P]
     lib.ss_filter_batch.argtypes = [P, P, P, ctypes.c_int, P, P, I32, P, I32,
                                     I64, ctypes.c_int, P, P, P]
     lib.ss_filter_host.argtypes = [P, P, P, ctypes.c_int, I32, P,
@@ -179,6 +186,15 @@ def ss_version() -> int:
 
 def ss_packed_words(m: int) -> int:
     return int(load().ss_packed_words(m))
+
+
+def ss_sliced_words(m: int, n: int) -> int:
+    return int(load().ss_sliced_words(m, n))
+
+
+def ss_pack_sliced(ctx, ascii, m, n, sliced, stream) -> int:
+    return load().ss_pack_sliced(ctx, ascii or None, m, n, sliced or None,
+                                 stream or None)
 
 
 def ss_pack(ctx, ascii, offsets, lengths, m, n, packed, packed_offsets,
@@ -286,6 +302,8 @@ def _seq_bytes(fmt: int, n: int, m: int) -> int:
     """Bytes of n fixed-stride sequences of m bases in format fmt."""
     if n <= 0 or m <= 0:
         return 0
+    if fmt == SS_FMT_SLICED2:
+        return 4 * ss_sliced_words(m, n)
     return n * m if fmt == SS_FMT_ASCII else n * 4 * ss_packed_words(m)
 
 
@@ -343,6 +361,25 @@ class Filter:
                      _dptr(out_offsets, d, "out_offsets", 8 * n),
                      _stream_handle(stream))
         _check(rc, "ss_pack")
+        return out
+
+    def pack_sliced(self, ascii, m: int, n: Optional[int] = None, out=None,
+                    stream=None):
+        """Fixed-stride ASCII (uint8, device) -> the bit-sliced layout
+        (int32 words, device, ss_sliced_words(m, n) of them)."""
+        import torch
+        n = ascii.shape[0] if n is None else n
+        if out is None:
+            out = torch.empty(max(ss_sliced_words(m, n), 1),
+                              dtype=torch.int32, device=ascii.device)
+        d = self.device
+        rc = ss_pack_sliced(self.ctx,
+                            _dptr(ascii, d, "ascii",
+                                  _seq_bytes(SS_FMT_ASCII, n, m)), m, n,
+                            _dptr(out, d, "out",
+                                  _seq_bytes(SS_FMT_SLICED2, n, m)),
+                            _stream_handle(stream))
+        _check(rc, "ss_pack_sliced")
         return out
 
     def filter(self, reads, refs, *, m: int = 0, e: int = 0, n=None,

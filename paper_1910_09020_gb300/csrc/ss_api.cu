@@ -133,6 +133,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // torch's default stream handle is 0).
 cudaStream_t pick_stream(void *stream) { return (cudaStream_t)stream; }
 
+static_assert(SS_SLICED_MAX_E == ssk::kSlicedMaxE, "sliced limit");
 static_assert(SS_PLAIN_MAX_E == ssk::kRwMaxE && SS_PLAIN_MAX_M == ssk::kRwMaxM,
               "the header states the plain launch's limits");
 
@@ -337,7 +338,7 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
 
 extern "C" {
 
-int ss_version(void) { return 200; }
+int ss_version(void) { return 300; }
 
 const char *ss_strerror(int code)
 {
@@ -355,6 +356,13 @@ const char *ss_strerror(int code)
 }
 
 int64_t ss_packed_words(int64_t m) { return m <= 0 ? 0 : (m + 15) / 16; }
+
+int64_t ss_sliced_words(int64_t m, int64_t n)
+{
+    if (m <= 0 || n <= 0)
+        return 0;
+    return 8 * ((m + 3) / 4) * ((n + 31) / 32);
+}
 
 int ss_create(ss_ctx **out, int device, size_t workspace_bytes)
 {
@@ -455,6 +463,35 @@ int ss_pack(ss_ctx *ctx, const uint8_t *ascii, const int64_t *offsets,
     return SS_OK;
 }
 
+int ss_pack_sliced(ss_ctx *ctx, const uint8_t *ascii, int32_t m, int64_t n,
+                   uint32_t *sliced, void *stream)
+{
+    if (!ctx || n < 0 || m < 0)
+        return SS_ERR_INVALID_ARG;
+    if (n == 0 || m == 0)
+        return SS_OK;
+    if (!ascii || !sliced || ((uintptr_t)sliced & 15))
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok)
+        return SS_ERR_CUDA;
+    SS_CUDA(ssk::launch_pack_sliced(ascii, n, m, sliced, ctx->d_status,
+                                    pick_stream(stream)));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
+// The plain launch over SS_FMT_SLICED2 input (fixed stride, uniform m and
+// e, validated by the caller).
+static int filter_sliced(ss_ctx *ctx, const uint32_t *q, const uint32_t *r,
+                         int32_t m, int32_t e, int64_t n, uint8_t *acc,
+                         int32_t *obs, cudaStream_t st)
+{
+    SS_CUDA(ssk::launch_sliced(q, r, n, m, e, acc, obs, st));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
 int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
                     int format, const int64_t *offsets,
                     const int32_t *lengths, int32_t m, const int32_t *E,
@@ -463,7 +500,8 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
 {
     if (!ctx || n < 0)
         return SS_ERR_INVALID_ARG;
-    if (format != SS_FMT_ASCII && format != SS_FMT_PACKED2)
+    if (format != SS_FMT_ASCII && format != SS_FMT_PACKED2 &&
+        format != SS_FMT_SLICED2)
         return SS_ERR_INVALID_ARG;
     if ((flags & 3) == 3)
         return SS_ERR_INVALID_ARG;
@@ -487,6 +525,17 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
         SS_CUDA(cudaMemsetAsync(out_accept, 1, (size_t)n, st));
         SS_CUDA(cudaMemsetAsync(out_obstacles, 0, (size_t)n * 4, st));
         return SS_OK;
+    }
+    if (format == SS_FMT_SLICED2) {
+        if (!uniform_len || E)
+            return SS_ERR_INVALID_ARG;  // the layout has a fixed stride
+        if ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15)
+            return SS_ERR_INVALID_ARG;
+        if (e > ssk::kSlicedMaxE || (flags & 3) == SS_MODE_BUCKETED)
+            return SS_ERR_UNSUPPORTED;
+        return filter_sliced(ctx, (const uint32_t *)reads,
+                             (const uint32_t *)refs, m, e, n, out_accept,
+                             out_obstacles, st);
     }
     const bool needs_bucket = !(uniform_len && !E && plain_ok(m, e)) ||
                               (flags & 3) == SS_MODE_BUCKETED;

@@ -22,6 +22,16 @@ cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
                                int *status, int sm_count, cudaStream_t st,
                                uint8_t *bad_flags = nullptr);
 
+// Bit-sliced layout (SS_FMT_SLICED2): fixed-stride ASCII -> sliced words
+// (8 * ceil(m/4) * ceil(n/32) of them), and the plain launch over it for
+// 0 <= E <= kSlicedMaxE.
+constexpr int kSlicedMaxE = 15;
+cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
+                               uint32_t *out, int *status, cudaStream_t st);
+cudaError_t launch_sliced(const uint32_t *reads, const uint32_t *refs,
+                          int64_t n, int32_t m, int32_t E, uint8_t *acc,
+                          int32_t *obs, cudaStream_t st);
+
 // K3a plain launch for 0 <= E <= kRwMaxE, m <= kRwMaxM.  status: device
 // word for latched errors.
 cudaError_t launch_rw_uniform(int E, const uint32_t *reads,

@@ -17,6 +17,7 @@
 #include "ss_device.cuh"
 #include "ss_internal.h"
 #include "ss_pack.cuh"
+#include "ss_sliced.cuh"
 
 namespace ssk {
 
@@ -197,6 +198,67 @@ __global__ void k_pack_varlen(const uint8_t *__restrict__ ascii,
     }
     if (any_bad && lane == 0)
         atomicOr(status, kStatusInvalidBase);
+}
+
+// Fixed stride -> the bit-sliced layout (SS_FMT_SLICED2): one warp per
+// group of 32 pairs.  Lane i packs 16 bases of pair 32g + i into one word
+// (bit t = code bit 0 of base t, bit 16 + t = code bit 1); the warp then
+// transposes the 32 words (lanes x bits), so lane r holds code bit r/16 of
+// base r%16 of all 32 pairs, which is one word of the layout.
+constexpr int kPackSlicedWarps = 8;
+
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane)
+{
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const uint32_t x = __shfl_xor_sync(0xffffffffu, v, d);
+        v = transpose_level(v, x, lane, d);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(32 * kPackSlicedWarps)
+    k_pack_sliced(const uint8_t *__restrict__ ascii, int64_t n, int32_t m,
+                  int64_t G, uint32_t *__restrict__ out, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g =
+        (int64_t)blockIdx.x * kPackSlicedWarps + (threadIdx.x >> 5);
+    if (g >= G)
+        return;  // the whole warp
+    const int64_t p = g * 32 + lane;
+    const bool live = p < n;
+    const uint8_t *src = ascii + (live ? p : 0) * (int64_t)m;
+    const bool aligned4 = ((uintptr_t)src & 3) == 0;
+    const int w16 = (m + 15) >> 4;
+    const int nb4 = 4 * ((m + 3) >> 2);  // bases of the stored blocks
+    uint32_t err = 0;
+    for (int c = 0; c < w16; ++c) {
+        uint32_t w = 0u;
+        if (live)
+            w = pack16(src + 16 * c, min(16, m - 16 * c), aligned4, err);
+        w = warp_transpose32(w, lane);
+        const int j = 16 * c + (lane & 15);
+        if (j < nb4)
+            out[((int64_t)(j >> 2) * G + g) * 8 + (lane >> 4) * 4 + (j & 3)] =
+                w;
+    }
+    if (__any_sync(0xffffffffu, err != 0u) && lane == 0)
+        atomicOr(status, kStatusInvalidBase);
+}
+
+cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
+                               uint32_t *out, int *status, cudaStream_t st)
+{
+    if (n <= 0 || m <= 0)
+        return cudaSuccess;
+    const int64_t G = (n + 31) / 32;
+    const int64_t blocks = (G + kPackSlicedWarps - 1) / kPackSlicedWarps;
+    if (blocks > 0x7fffffff)
+        return cudaErrorInvalidValue;
+    k_pack_sliced<<<(unsigned)blocks, 32 * kPackSlicedWarps, 0, st>>>(
+        ascii, n, m, G, out, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_fixed(const uint8_t *ascii, int64_t n, int32_t m,

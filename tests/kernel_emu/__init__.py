@@ -62,5 +62,8 @@ def load():
     lib.emu_submaze_cols.argtypes = [P, P, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int]
     lib.emu_submaze_staged.argtypes = [P, P] + [ctypes.c_int] * 5
+    lib.emu_sliced.argtypes = [P, P, ctypes.c_int64, ctypes.c_int,
+                               ctypes.c_int, P, P]
+    lib.emu_transpose32.argtypes = [P, P]
     _lib = lib
     return lib

@@ -2,13 +2,16 @@
 // host, so the CPU suite can check their logic against the oracle without a
 // GPU.  Not part of the library and never loaded by it; the GPU tests remain
 // the parity tests proper.
+#include <algorithm>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 #include "ss_cw.cuh"
 #include "ss_pack.cuh"
 #include "ss_rw.cuh"
 #include "ss_rwc.cuh"
+#include "ss_sliced.cuh"
 #include "ss_submaze.cuh"
 #include "ss_unequal.cuh"
 #include "ss_verify.cuh"
@@ -157,9 +160,94 @@ int submaze_form(const Seq &Q, const Seq &R, int m, int E, int t, int y,
     return -2;
 }
 
+// One group of the bit-sliced layout in host memory (the kernel's loads).
+struct HostSliced {
+    const uint32_t *q, *r;
+    int64_t G, g;
+    void load(const uint32_t *base, int blk, uint32_t (&lo)[4],
+              uint32_t (&hi)[4]) const
+    {
+        const uint32_t *p = base + ((int64_t)blk * G + g) * 8;
+        for (int x = 0; x < 4; ++x) {
+            lo[x] = p[x];
+            hi[x] = p[4 + x];
+        }
+    }
+    void query(int blk, int nb, uint32_t (&lo)[4], uint32_t (&hi)[4]) const
+    {
+        if (blk < 0 || blk >= nb) {
+            for (int x = 0; x < 4; ++x)
+                lo[x] = hi[x] = 0u;
+            return;
+        }
+        load(q, blk, lo, hi);
+    }
+    void ref(int blk, uint32_t (&lo)[4], uint32_t (&hi)[4]) const
+    {
+        load(r, blk, lo, hi);
+    }
+};
+
+template <int E>
+void sliced_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
+                   uint8_t *acc, int32_t *obs)
+{
+    const int64_t G = (n + 31) / 32;
+    for (int64_t g = 0; g < G; ++g) {
+        const int np = (int)std::min<int64_t>(32, n - 32 * g);
+        const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
+        uint32_t T[E + 2];
+        sliced_walk<E>(HostSliced{q, r, G, g}, m, pad, T, 1u);
+        uint32_t cb[SlicedShape<E>::NB];
+        sliced_binary<E>(T, cb);
+        for (int i = 0; i < np; ++i) {
+            obs[32 * g + i] = sliced_count<E>(cb, i);
+            acc[32 * g + i] = (uint8_t)(((~T[E + 1]) >> i) & 1u);
+        }
+    }
+}
+
+template <int... Es>
+int sliced_dispatch(int E, const uint32_t *q, const uint32_t *r, int64_t n,
+                    int m, uint8_t *acc, int32_t *obs,
+                    std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    ((E == Es ? (sliced_groups<Es>(q, r, n, m, acc, obs), out = 0) : 0), ...);
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
+
+// The bit-sliced walk over every group of a sliced layout (n pairs of
+// length m): the plain sliced launch's results.  Returns -100 if E is not
+// built.
+int emu_sliced(const uint32_t *q, const uint32_t *r, int64_t n, int m, int E,
+               uint8_t *acc, int32_t *obs)
+{
+    return sliced_dispatch(E, q, r, n, m, acc, obs,
+                           std::make_integer_sequence<int, 16>{});
+}
+
+// The warp transpose of the sliced packer, the 32 lanes simulated in turn:
+// v[32] in, out[32] out (lane r gets bit r of every lane's word).
+void emu_transpose32(const uint32_t *v, uint32_t *out)
+{
+    uint32_t a[32];
+    for (int i = 0; i < 32; ++i)
+        a[i] = v[i];
+    for (int d = 16; d >= 1; d >>= 1) {
+        uint32_t b[32];
+        for (int lane = 0; lane < 32; ++lane)
+            b[lane] = transpose_level(a[lane], a[lane ^ d], lane, d);
+        for (int i = 0; i < 32; ++i)
+            a[i] = b[i];
+    }
+    for (int i = 0; i < 32; ++i)
+        out[i] = a[i];
+}
 
 // Pack arithmetic: 16 ASCII bytes -> packed word, error bits.
 uint32_t emu_pack_chunk(const uint8_t *b16, uint32_t *err)

@@ -1,0 +1,146 @@
+"""GPU parity of the bit-sliced layout (SS_FMT_SLICED2): its packer against
+the oracle's reference packer word for word, and the plain launch over it
+against the oracle element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_same, oracle_fixed, to_dev, torch_cuda
+from paper_1910_09020_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+SLICED = binding.SS_FMT_SLICED2
+
+
+@pytest.fixture(scope="module")
+def F():
+    torch_cuda()
+    f = binding.Filter(0)
+    yield f
+    f.close()
+
+
+def sliced_filter(F, q, r, n, m, E, out_accept=None, out_obstacles=None):
+    acc, obs = F.filter(q, r, m=m, e=E, n=n, fmt=SLICED,
+                        out_accept=out_accept, out_obstacles=out_obstacles)
+    F.sync()
+    return acc.cpu().numpy(), obs.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (31, 3), (32, 4), (33, 5),
+                                 (100, 16), (257, 17), (1000, 100),
+                                 (999, 101), (300, 150), (64, 250),
+                                 (40, 1000), (100003, 100)])
+def test_pack_sliced_matches_reference(F, n, m):
+    reads, _ = synth.pairs_fixed(200 + m, 0, n, m, synth.SHORT_UNIFORM_K)
+    rng = np.random.default_rng(n + m)
+    lower = rng.random(reads.shape) < 0.3
+    reads = np.where(lower, reads | 0x20, reads).astype(np.uint8)
+    got = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+    F.sync()
+    got = got.cpu().numpy().view(np.uint32)[:binding.ss_sliced_words(m, n)]
+    want = oracle.pack_sliced(reads)
+    assert len(got) == len(want)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, (n, m, bad[:5], got[bad[:5]], want[bad[:5]])
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_pack_sliced_unaligned_input(F, shift):
+    torch = torch_cuda()
+    n, m = 777, 100
+    reads, _ = synth.pairs_fixed(211, 0, n, m, synth.SHORT_POISSON)
+    buf = torch.zeros(n * m + 16, dtype=torch.uint8, device="cuda")
+    buf[shift:shift + n * m] = to_dev(reads.reshape(-1))
+    got = F.pack_sliced(buf[shift:shift + n * m], m=m, n=n)
+    F.sync()
+    got = got.cpu().numpy().view(np.uint32)
+    assert (got == oracle.pack_sliced(reads)).all()
+
+
+def test_pack_sliced_flags_a_bad_base(F):
+    n, m = 70, 33
+    reads, _ = synth.pairs_fixed(212, 0, n, m, synth.SHORT_POISSON)
+    reads[45, 32] = ord("N")
+    F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+    with pytest.raises(binding.SSError) as e:
+        F.sync()
+    assert e.value.code == binding.SS_ERR_INVALID_BASE
+    F.sync()  # taken: the context stays usable
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 9, 15, 16, 31, 33, 64, 100,
+                               101, 150, 250, 1000])
+def test_sliced_filter_every_E(F, m):
+    """Every E the sliced launch is built for, ragged last group, pairs from
+    near-identical to random."""
+    n = 4099 if m <= 250 else 700
+    reads, refs = synth.pairs_fixed(300 + m, 0, n, m, synth.rate_recipe(0.2))
+    # a quarter of the pairs unrelated (random reference)
+    rnd, _ = synth.pairs_fixed(301 + m, 0, n // 4, m, synth.SHORT_POISSON)
+    refs[: n // 4] = rnd
+    q = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n)
+    for E in range(binding.SLICED_MAX_E + 1):
+        acc, obs = sliced_filter(F, q, r, n, m, E)
+        oacc, oobs = oracle_fixed(reads, refs, E)
+        assert_same(acc, obs, oacc, oobs, f"sliced m={m} E={E}")
+
+
+@pytest.mark.parametrize("recipe", ["poisson", "uniform_k"])
+def test_sliced_filter_many_groups(F, recipe):
+    """Enough groups for thousands of CTAs at the headline length."""
+    n, m = 200_000, 100
+    rec = synth.SHORT_POISSON if recipe == "poisson" else synth.SHORT_UNIFORM_K
+    reads, refs = synth.pairs_fixed(310, 0, n, m, rec)
+    q = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n)
+    for E in (0, 2, 4, 6, 8, 10, 15):
+        acc, obs = sliced_filter(F, q, r, n, m, E)
+        oacc, oobs = oracle_fixed(reads, refs, E)
+        assert_same(acc, obs, oacc, oobs, f"{recipe} E={E}")
+
+
+def test_sliced_unaligned_outputs(F):
+    """Outputs not 16-byte aligned: every pair written one by one."""
+    torch = torch_cuda()
+    n, m = 1000, 100
+    reads, refs = synth.pairs_fixed(320, 0, n, m, synth.SHORT_POISSON)
+    q = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n)
+    acc_buf = torch.full((n + 16,), 7, dtype=torch.uint8, device="cuda")
+    obs_buf = torch.full((n + 4,), -9, dtype=torch.int32, device="cuda")
+    acc, obs = sliced_filter(F, q, r, n, m, 4, out_accept=acc_buf[3:3 + n],
+                             out_obstacles=obs_buf[1:1 + n])
+    oacc, oobs = oracle_fixed(reads, refs, 4)
+    assert_same(acc, obs, oacc, oobs, "unaligned outputs")
+    assert int(acc_buf[:3].sum()) == 21 and int(obs_buf[0]) == -9
+    assert int(obs_buf[1 + n]) == -9 and int(acc_buf[3 + n]) == 7
+
+
+def test_sliced_argument_errors(F):
+    torch = torch_cuda()
+    n, m = 64, 40
+    q = torch.zeros(binding.ss_sliced_words(m, n) + 4, dtype=torch.int32,
+                    device="cuda")
+    acc = torch.empty(n, dtype=torch.uint8, device="cuda")
+    obs = torch.empty(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(binding.SSError) as e:
+        F.filter(q, q, m=m, e=binding.SLICED_MAX_E + 1, n=n, fmt=SLICED)
+    assert e.value.code == binding.SS_ERR_UNSUPPORTED
+    with pytest.raises(binding.SSError) as e:  # not 16-byte aligned
+        F.filter(q[1:], q[1:], m=m, e=3, n=n, fmt=SLICED)
+    assert e.value.code == binding.SS_ERR_INVALID_ARG
+    with pytest.raises(binding.SSError) as e:
+        F.filter(q, q, m=m, e=3, n=n, fmt=SLICED,
+                 flags=binding.SS_MODE_BUCKETED)
+    assert e.value.code == binding.SS_ERR_UNSUPPORTED
+    Es = torch.full((n,), 3, dtype=torch.int32, device="cuda")
+    with pytest.raises(binding.SSError) as e:  # per-pair thresholds
+        F.filter(q, q, m=m, E=Es, n=n, fmt=SLICED)
+    assert e.value.code == binding.SS_ERR_INVALID_ARG
+    # m = 0: every pair accepted with no obstacle
+    a, o = F.filter(q, q, m=0, e=3, n=n, fmt=SLICED, out_accept=acc,
+                    out_obstacles=obs, sync=True)
+    assert (a.cpu().numpy() == 1).all() and (o.cpu().numpy() == 0).all()

@@ -309,3 +309,39 @@ def test_cw_long_reads_match_oracle(emu, K):
         got = emu.emu_cw(P(q), P(r), m, E, K)
         want = oracle.filter_pair(Q, R, E).obstacles
         assert got == want, (m, E, K)
+
+
+def test_sliced_transpose_is_the_bit_transpose(emu):
+    """The sliced packer's warp transpose (32 lanes simulated): lane r ends
+    with bit r of every lane's word, bit i from lane i."""
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        v = rng.integers(0, 2**32, 32, dtype=np.uint64).astype(np.uint32)
+        out = np.zeros(32, np.uint32)
+        emu.emu_transpose32(P(v), P(out))
+        bits = (v[:, None] >> np.arange(32, dtype=np.uint32)) & 1  # [i][r]
+        want = (bits.T.astype(np.uint64) << np.arange(32, dtype=np.uint64)
+                ).sum(axis=1).astype(np.uint32)
+        assert (out == want).all()
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 7, 9, 15, 16, 31, 33, 64, 100,
+                               101, 150, 251])
+def test_sliced_walk_matches_oracle(emu, m):
+    """The bit-sliced walk (32 pairs per thread, columns in blocks of four,
+    the query window either side) at every E it is built for, on groups
+    mixing near and far pairs, a ragged last group, lengths below, at and
+    around E and the block edges."""
+    rng = np.random.default_rng(1000 + m)
+    n = int(rng.choice([1, 31, 32, 33, 95]))
+    rec = synth.rate_recipe(float(rng.choice([0.03, 0.12, 0.4])))
+    reads, refs = synth.pairs_fixed(7000 + m, 0, n, m, rec)
+    q = oracle.pack_sliced(reads)
+    r = oracle.pack_sliced(refs)
+    for E in range(16):
+        acc = np.zeros(n, np.uint8)
+        obs = np.zeros(n, np.int32)
+        assert emu.emu_sliced(P(q), P(r), n, m, E, P(acc), P(obs)) == 0
+        oacc, oobs = oracle.filter_batch(reads, refs, m, E)
+        bad = np.flatnonzero((acc != oacc) | (obs != oobs))
+        assert bad.size == 0, (m, n, E, bad[:5], obs[bad[:5]], oobs[bad[:5]])
