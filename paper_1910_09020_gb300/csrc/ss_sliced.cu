@@ -70,6 +70,16 @@ __device__ __forceinline__ uint32_t flag_bytes(uint32_t ok, int q)
 template <int E>
 __global__ void __launch_bounds__(kSlicedThreads) k_sliced(const SlicedArgs a)
 {
+    // the validity words of the edge blocks, the same for every thread
+    using Ed = SlicedEdges<E>;
+    constexpr int WW = SlicedShape<E>::WW;
+    __shared__ __align__(16) uint32_t vtab[Ed::kRows * WW];
+    {
+        const Ed ed(a.m);
+        for (int i = threadIdx.x; i < ed.rows() * WW; i += kSlicedThreads)
+            vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, a.m);
+    }
+    __syncthreads();
     const int64_t g = (int64_t)blockIdx.x * kSlicedThreads + threadIdx.x;
     if (g >= a.G)
         return;
@@ -77,7 +87,7 @@ __global__ void __launch_bounds__(kSlicedThreads) k_sliced(const SlicedArgs a)
     const int np = (int)min((int64_t)32, a.n - p0);
     const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
     uint32_t T[E + 2];
-    sliced_walk<E>(SlicedSrc{a.q, a.r, a.G, g}, a.m, pad, T, a.one);
+    sliced_walk<E>(SlicedSrc{a.q, a.r, a.G, g}, a.m, pad, T, vtab, a.one);
     uint32_t cb[SlicedShape<E>::NB];
     sliced_binary<E>(T, cb);
     const uint32_t ok = ~T[E + 1];  // count <= E (Section 2.4 step 5)

@@ -56,44 +56,136 @@ struct SlicedShape {
                                             : 1;
 };
 
-// The block's columns j0 + u for u < live (at most 4).  ql/qh: the window's
-// query words (word w = query base j0 - 4 NBH + w); rl/rh: the reference
-// bases j0..j0+3.  With EDGE, a diagonal that reads a query base outside
-// 0..m-1 meets an obstacle (Eq. 1 case 4); without, every base read is in
-// range.  one holds 1 (a run-time value: S_d * one + z is a multiply-add).
+// Any three-input bitwise function as one logic op: bit i of the result is
+// bit (4 a_i + 2 b_i + c_i) of LUT.  Written as one lop3 so that the walk's
+// steps stay one instruction each.  The tables used: 0x90 = a & ~(b ^ c),
+// 0xFE = a | b | c, 0xF4 = a | (b & ~c), 0xF3 = a | ~b.
+template <uint32_t LUT>
+SS_HD uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
+{
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;"
+        : "=r"(d)
+        : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
+#else
+    uint32_t d = 0u;
+    for (int k = 0; k < 8; ++k)
+        if ((LUT >> k) & 1u)
+            d |= ((k & 4) ? a : ~a) & ((k & 2) ? b : ~b) & ((k & 1) ? c : ~c);
+    return d;
+#endif
+}
+
+// OR of x[0..N-1] as a tree of three-input ORs (one logic op each).
+template <int N>
+SS_HD uint32_t or_tree(const uint32_t (&x)[N])
+{
+    if constexpr (N == 1) {
+        return x[0];
+    } else {
+        constexpr int M = (N + 2) / 3;
+        uint32_t y[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const uint32_t b = 3 * i + 1 < N ? x[3 * i + 1] : 0u;
+            const uint32_t c = 3 * i + 2 < N ? x[3 * i + 2] : 0u;
+            y[i] = 3 * i + 1 < N ? lop3<0xFE>(x[3 * i], b, c) : x[3 * i];
+        }
+        return or_tree<M>(y);
+    }
+}
+
+// The edge blocks of a walk of m columns: a block k is an edge block when
+// one of its columns has a diagonal that reads a query base outside 0..m-1
+// (Eq. 1 case 4): k < kl (j0 < E) or k >= kr (j0 + 3 + E >= m).  Their
+// validity words -- all ones or zero per window word, the same for every
+// pair -- are rows of a table: row k for k < kl, row kl + k - max(kr, kl)
+// for k >= kr.  At most 2 NBH + 2 rows.
+template <int E>
+struct SlicedEdges {
+    static constexpr int kRows = 2 * SlicedShape<E>::NBH + 2;
+    int nb, kl, kr;
+    SS_HD SlicedEdges(int m)
+    {
+        nb = (m + 3) >> 2;
+        kl = imin(nb, SlicedShape<E>::NBH);
+        // first k with 4k + 3 + E >= m
+        const int r = m - 3 - E;
+        kr = imax(kl, r <= 0 ? 0 : (r + 3) >> 2);
+    }
+    SS_HD int rows() const { return kl + (nb - kr); }
+    SS_HD int row_of(int k) const { return k < kl ? k : kl + (k - kr); }
+    SS_HD int block_of(int row) const
+    {
+        return row < kl ? row : kr + (row - kl);
+    }
+    // validity word w of the window of block k
+    SS_HD static uint32_t valid(int k, int w, int m)
+    {
+        return (uint32_t)(4 * k - 4 * SlicedShape<E>::NBH + w) < (uint32_t)m
+                   ? 0xffffffffu
+                   : 0u;
+    }
+};
+
+// Column j0 + u of a block.  ql/qh: the window's query words (word w =
+// query base j0 - 4 NBH + w); rl/rh: the reference bases j0..j0+3.  With
+// EDGE, vw holds the block's validity words: a diagonal that reads a query
+// base outside 0..m-1 meets an obstacle (Eq. 1 case 4).  one holds 1 (a
+// run-time value: S_d * one + z is a multiply-add on the FMA pipe).
+template <int E, bool EDGE, int U>
+SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
+                         uint32_t (&T)[E + 2],
+                         const uint32_t (&ql)[SlicedShape<E>::WW],
+                         const uint32_t (&qh)[SlicedShape<E>::WW],
+                         const uint32_t (&rl)[4], const uint32_t (&rh)[4],
+                         const uint32_t *vw, uint32_t one)
+{
+    using Sh = SlicedShape<E>;
+#pragma unroll
+    for (int d = 0; d < Sh::ND; ++d) {
+        const int w = Sh::OFF + U + d;
+        // (S_d | z) & ~(Q lo ^ R lo) & ~(Q hi ^ R hi)
+        uint32_t s = S[d] * one + z;
+        s = lop3<0x90>(s, ql[w], rl[U]);
+        s = lop3<0x90>(s, qh[w], rh[U]);
+        if (EDGE)
+            s &= vw[w];
+        S[d] = s;
+    }
+    // the pairs with every row dead: count this column's obstacle
+    // (T_c |= T_c-1 & ~nz), restart at the next column
+    const uint32_t nz = or_tree<Sh::ND>(S);
+#pragma unroll
+    for (int c = E + 1; c >= 2; --c)
+        T[c] = lop3<0xF4>(T[c], T[c - 1], nz);
+    T[1] = lop3<0xF3>(T[1], nz, 0u);
+    z = ~nz;
+}
+
+// The block's columns j0 + u for u < live (1..4; below 4 only in the last
+// block).
 template <int E, bool EDGE>
 SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
                         uint32_t (&T)[E + 2],
                         const uint32_t (&ql)[SlicedShape<E>::WW],
                         const uint32_t (&qh)[SlicedShape<E>::WW],
                         const uint32_t (&rl)[4], const uint32_t (&rh)[4],
-                        int j0, int m, int live, uint32_t one)
+                        const uint32_t *vw, int live, uint32_t one)
 {
-    using Sh = SlicedShape<E>;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        if (u < live) {
-            uint32_t nz = 0u;
-#pragma unroll
-            for (int d = 0; d < Sh::ND; ++d) {
-                const int w = Sh::OFF + u + d;
-                uint32_t s = S[d] * one + z;
-                s &= ~(ql[w] ^ rl[u]);
-                s &= ~(qh[w] ^ rh[u]);
-                if (EDGE) {
-                    const int qi = j0 + u + d - E;
-                    if (qi < 0 || qi >= m)
-                        s = 0u;
-                }
-                S[d] = s;
-                nz |= s;
-            }
-            z = ~nz;
-#pragma unroll
-            for (int c = E + 1; c >= 2; --c)
-                T[c] |= T[c - 1] & z;
-            T[1] |= z;
-        }
+    if (live >= 4) {
+        sliced_column<E, EDGE, 0>(S, z, T, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 1>(S, z, T, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 2>(S, z, T, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 3>(S, z, T, ql, qh, rl, rh, vw, one);
+    } else {
+        sliced_column<E, EDGE, 0>(S, z, T, ql, qh, rl, rh, vw, one);
+        if (live > 1)
+            sliced_column<E, EDGE, 1>(S, z, T, ql, qh, rl, rh, vw, one);
+        if (live > 2)
+            sliced_column<E, EDGE, 2>(S, z, T, ql, qh, rl, rh, vw, one);
     }
 }
 
@@ -102,13 +194,16 @@ SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
 // min(count, E+1) in thermometer form.  pad: pairs that do not exist (the
 // last group's), counted as past E so that the group can stop early.
 // src.query(blk, nb, lo, hi) / src.ref(blk, lo, hi) load the four words of
-// each plane of a block (zero for a query block outside 0..nb-1).
+// each plane of a block (zero for a query block outside 0..nb-1); vtab:
+// the validity table of SlicedEdges<E>(m), WW words per row.
 template <int E, class Src>
 SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
-                       uint32_t (&T)[E + 2], uint32_t one)
+                       uint32_t (&T)[E + 2], const uint32_t *vtab,
+                       uint32_t one)
 {
     using Sh = SlicedShape<E>;
-    const int nb = (m + 3) >> 2;
+    const SlicedEdges<E> ed(m);
+    const int nb = ed.nb;
     uint32_t ql[Sh::WW], qh[Sh::WW];
 #pragma unroll
     for (int b = 0; b < 2 * Sh::NBH + 1; ++b) {
@@ -138,12 +233,13 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
         src.query(k + Sh::NBH + 1, nb, nql, nqh);
         if (k + 1 < nb)
             src.ref(k + 1, nrl, nrh);
-        const int j0 = 4 * k;
-        const int live = imin(4, m - j0);
-        if (j0 < E || j0 + 3 + E >= m)
-            sliced_block<E, true>(S, z, T, ql, qh, rl, rh, j0, m, live, one);
+        const int live = imin(4, m - 4 * k);
+        if (k < ed.kl || k >= ed.kr)
+            sliced_block<E, true>(S, z, T, ql, qh, rl, rh,
+                                  vtab + ed.row_of(k) * Sh::WW, live, one);
         else
-            sliced_block<E, false>(S, z, T, ql, qh, rl, rh, j0, m, live, one);
+            sliced_block<E, false>(S, z, T, ql, qh, rl, rh, nullptr, live,
+                                   one);
         if (T[E + 1] == 0xffffffffu)
             break;  // every pair of the group is past E
 #pragma unroll

@@ -196,8 +196,14 @@ void sliced_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
     for (int64_t g = 0; g < G; ++g) {
         const int np = (int)std::min<int64_t>(32, n - 32 * g);
         const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
+        using Ed = SlicedEdges<E>;
+        constexpr int WW = SlicedShape<E>::WW;
+        const Ed ed(m);
+        std::vector<uint32_t> vtab(Ed::kRows * WW);
+        for (int i = 0; i < ed.rows() * WW; ++i)
+            vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, m);
         uint32_t T[E + 2];
-        sliced_walk<E>(HostSliced{q, r, G, g}, m, pad, T, 1u);
+        sliced_walk<E>(HostSliced{q, r, G, g}, m, pad, T, vtab.data(), 1u);
         uint32_t cb[SlicedShape<E>::NB];
         sliced_binary<E>(T, cb);
         for (int i = 0; i < np; ++i) {
