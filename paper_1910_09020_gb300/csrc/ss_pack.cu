@@ -12,6 +12,7 @@
 // two consecutive code-stream words, and zeroes the codes past the pair's
 // end.  The kernel is bound by HBM bandwidth (m bytes read, 4 * ceil(m/16)
 // written per sequence).
+#include <algorithm>
 #include <cstdint>
 
 #include "ss_device.cuh"
@@ -247,12 +248,108 @@ __global__ void __launch_bounds__(32 * kPackSlicedWarps)
         atomicOr(status, kStatusInvalidBase);
 }
 
+// Two-phase form for reads up to kPackSpanMaxM bases: a CTA's groups (gpc of
+// them, 32 gpc consecutive pairs) are one contiguous span of the input.
+// Phase 1 reads the span as aligned 16-byte chunks, coalesced, and turns
+// each into one word of a code stream in shared memory (pack_chunk_pairs:
+// the chunk's base t at bits 2t and 2t+1).  Phase 2 gives each lane its
+// pair's 16-base windows, one funnel shift of two consecutive stream words
+// each, with the codes past the pair's end cleared, and the warp transposes
+// them as above (lane r then holds code bit r%2 of base r/2).
+constexpr int kPackSpanMaxWords = 12 * 1024;  // 48 KB of code stream
+constexpr int kPackSpanMaxM = (kPackSpanMaxWords - 3) / 2;
+
+__global__ void __launch_bounds__(32 * kPackSlicedWarps)
+    k_pack_sliced_span(const uint8_t *__restrict__ ascii, int64_t n,
+                       int32_t m, int64_t G, int gpc,
+                       uint32_t *__restrict__ out, int *status)
+{
+    extern __shared__ uint32_t code[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * gpc;
+    const int64_t p0 = g0 * 32;
+    const int64_t p1 = min(n, p0 + 32 * (int64_t)gpc);  // pairs [p0, p1)
+    const int64_t cb = (p0 * m) >> 4;                   // first chunk
+    // chunks [cb, cb + nc): the span, plus one (windows read word k+1)
+    const int nc = (int)(((p1 * m + 15) >> 4) - cb) + 1;
+    const int64_t limit = n * (int64_t)m;
+    const bool aligned = ((uintptr_t)ascii & 15) == 0;
+    uint32_t err = 0;
+#pragma unroll 4
+    for (int c = threadIdx.x; c < nc; c += 32 * kPackSlicedWarps) {
+        const int64_t at = (cb + c) * 16;
+        uint32_t x[4];
+        if (aligned && at + 16 <= limit) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ascii + at));
+            x[0] = v.x;
+            x[1] = v.y;
+            x[2] = v.z;
+            x[3] = v.w;
+        } else {
+            // the input's last partial chunk, or an unaligned input: bytes
+            // past the end count as 'A'
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t w = 0;
+                for (int b = 0; b < 4; ++b) {
+                    const int64_t j = at + 4 * q + b;
+                    const uint32_t ch =
+                        j < limit ? (uint32_t)__ldg(ascii + j) : 0x41u;
+                    w |= ch << (8 * b);
+                }
+                x[q] = w;
+            }
+        }
+        code[c] = pack_chunk_pairs(x, err);
+    }
+    __syncthreads();
+    const int64_t g = g0 + warp;
+    if (warp < gpc && g < G) {
+        const int64_t p = g * 32 + lane;
+        const bool live = p < n;
+        const int w16 = (m + 15) >> 4;
+        const int nb4 = 4 * ((m + 3) >> 2);  // bases of the stored blocks
+        // bit of the stream where the pair's base 0 sits
+        const uint32_t o0 = live ? (uint32_t)(2 * (p * m - cb * 16)) : 0u;
+        for (int c = 0; c < w16; ++c) {
+            uint32_t w = 0u;
+            if (live) {
+                const uint32_t o = o0 + 32u * (uint32_t)c;
+                const uint32_t k = o >> 5;
+                w = funnel_r(code[k], code[k + 1], o & 31u) &
+                    mask_below(2 * (m - 16 * c));
+            }
+            w = warp_transpose32(w, lane);
+            const int j = 16 * c + (lane >> 1);
+            if (j < nb4)
+                out[((int64_t)(j >> 2) * G + g) * 8 + (lane & 1) * 4 +
+                    (j & 3)] = w;
+        }
+    }
+    if (__any_sync(0xffffffffu, err != 0u) && lane == 0)
+        atomicOr(status, kStatusInvalidBase);
+}
+
 cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
                                uint32_t *out, int *status, cudaStream_t st)
 {
     if (n <= 0 || m <= 0)
         return cudaSuccess;
     const int64_t G = (n + 31) / 32;
+    if (m <= kPackSpanMaxM) {
+        // groups per CTA: as many as the warps, while the span's code
+        // stream fits
+        const int gpc = (int)std::min<int64_t>(
+            kPackSlicedWarps, (kPackSpanMaxWords - 3) / (2 * (int64_t)m));
+        const int64_t blocks = (G + gpc - 1) / gpc;
+        if (blocks > 0x7fffffff)
+            return cudaErrorInvalidValue;
+        const size_t smem = ((size_t)2 * gpc * m + 3) * 4;
+        k_pack_sliced_span<<<(unsigned)blocks, 32 * kPackSlicedWarps, smem,
+                             st>>>(ascii, n, m, G, gpc, out, status);
+        return cudaGetLastError();
+    }
     const int64_t blocks = (G + kPackSlicedWarps - 1) / kPackSlicedWarps;
     if (blocks > 0x7fffffff)
         return cudaErrorInvalidValue;

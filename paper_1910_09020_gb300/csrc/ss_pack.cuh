@@ -45,6 +45,30 @@ SS_HD uint32_t pack_chunk(const uint32_t x[4], uint32_t &err)
     return prmt(prmt(lo01, lo23, 0x73u), prmt(hi01, hi23, 0x73u), 0x5410u);
 }
 
+// 16 ASCII bytes -> their 32 code bits in base order, base t's code at bits
+// 2t (code bit 0) and 2t+1 (code bit 1); err as above.  Word x[q] holds
+// bases 4q..4q+3: y = (x ^ x >> 1) & 0x06060606 keeps, for byte i, code bit
+// 0 at bit 8i+1 and code bit 1 at 8i+2, and one multiply by 2^23 + 2^17 +
+// 2^11 + 2^5 moves them to bits 24+2i and 25+2i.  Its partial products, bit
+// 8i+1+b times 2^(23-6k), land at 24 + 8i - 6k + b, distinct for all i, k
+// in 0..3 and b in 0..1, so nothing carries; the top bytes of the four
+// products are the four bytes of the result.
+SS_HD uint32_t pack_chunk_pairs(const uint32_t x[4], uint32_t &err)
+{
+    uint32_t p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t f = x[q] >> 1;
+        const uint32_t y = (x[q] ^ f) & 0x06060606u;
+        p[q] = y * 0x00820820u;
+        const uint32_t t = (x[q] >> 2) & ~f & 0x01010101u;  // b2 & ~b1
+        const uint32_t d = (x[q] & 0xD9D9D9D9u) ^ 0x41414141u;
+        err |= d ^ (t * 17u);
+    }
+    return prmt(prmt(p[0], p[1], 0x0073u), prmt(p[2], p[3], 0x0073u),
+                0x5410u);
+}
+
 // 16 codes starting at base r (0..15) of two consecutive packed words c0, c1
 // of one base stream.
 SS_HD uint32_t pack_window(uint32_t c0, uint32_t c1, uint32_t r)

@@ -294,10 +294,13 @@ SS_HD int sliced_count(const uint32_t (&cb)[SlicedShape<E>::NB], int i)
 SS_HD uint32_t transpose_level(uint32_t v, uint32_t x, int lane, int d)
 {
     const bool keep_low = (lane & d) == 0;
+    // whole bytes and half-words: one byte permute of the two words
+    if (d == 16)
+        return prmt(v, x, keep_low ? 0x5410u : 0x3276u);
+    if (d == 8)
+        return prmt(v, x, keep_low ? 0x6240u : 0x3715u);
     uint32_t ml;  // bits whose index has bit d clear
     switch (d) {
-    case 16: ml = 0x0000ffffu; break;
-    case 8: ml = 0x00ff00ffu; break;
     case 4: ml = 0x0f0f0f0fu; break;
     case 2: ml = 0x33333333u; break;
     default: ml = 0x55555555u; break;

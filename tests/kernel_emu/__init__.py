@@ -45,6 +45,8 @@ def load():
     lib.emu_ed.argtypes = [P, P, ctypes.c_int, ctypes.c_int]
     lib.emu_pack_chunk.argtypes = [P, P]
     lib.emu_pack_chunk.restype = ctypes.c_uint32
+    lib.emu_pack_chunk_pairs.argtypes = [P, P]
+    lib.emu_pack_chunk_pairs.restype = ctypes.c_uint32
     lib.emu_pack_window.argtypes = [ctypes.c_uint32] * 3
     lib.emu_pack_window.restype = ctypes.c_uint32
     lib.emu_unequal.argtypes = [P, ctypes.c_int, P, ctypes.c_int,

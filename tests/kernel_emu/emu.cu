@@ -269,6 +269,21 @@ uint32_t emu_pack_chunk(const uint8_t *b16, uint32_t *err)
     return r;
 }
 
+// The sliced packer's arithmetic: 16 ASCII bytes -> 32 code bits in base
+// order (base t at bits 2t, 2t+1), error bits.
+uint32_t emu_pack_chunk_pairs(const uint8_t *b16, uint32_t *err)
+{
+    uint32_t x[4];
+    for (int q = 0; q < 4; ++q)
+        x[q] = (uint32_t)b16[4 * q] | ((uint32_t)b16[4 * q + 1] << 8) |
+               ((uint32_t)b16[4 * q + 2] << 16) |
+               ((uint32_t)b16[4 * q + 3] << 24);
+    uint32_t e = 0;
+    const uint32_t r = pack_chunk_pairs(x, e);
+    *err = e;
+    return r;
+}
+
 uint32_t emu_pack_window(uint32_t c0, uint32_t c1, uint32_t r)
 {
     return pack_window(c0, c1, r);

@@ -31,7 +31,7 @@ def sliced_filter(F, q, r, n, m, E, out_accept=None, out_obstacles=None):
 @pytest.mark.parametrize("n,m", [(1, 1), (31, 3), (32, 4), (33, 5),
                                  (100, 16), (257, 17), (1000, 100),
                                  (999, 101), (300, 150), (64, 250),
-                                 (40, 1000), (100003, 100)])
+                                 (40, 1000), (33, 7000), (100003, 100)])
 def test_pack_sliced_matches_reference(F, n, m):
     reads, _ = synth.pairs_fixed(200 + m, 0, n, m, synth.SHORT_UNIFORM_K)
     rng = np.random.default_rng(n + m)

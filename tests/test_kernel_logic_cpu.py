@@ -209,6 +209,39 @@ def test_pack_chunk_every_byte_value_every_position(emu):
                 assert got == int(oracle.pack_reference(bytes(buf))[0]), (pos, b)
 
 
+def pair_order(packed_word: int) -> int:
+    """The oracle's 2-bit word (bit t: code bit 0, bit 16+t: code bit 1)
+    rearranged to base order: base t at bits 2t and 2t+1."""
+    out = 0
+    for t in range(16):
+        out |= ((packed_word >> t) & 1) << (2 * t)
+        out |= ((packed_word >> (16 + t)) & 1) << (2 * t + 1)
+    return out
+
+
+def test_pack_chunk_pairs_every_byte_value_every_position(emu):
+    """The sliced packer's arithmetic (code bits in base order) on all 256
+    byte values at each of the 16 positions, against the oracle's packer."""
+    err = ctypes.c_uint32()
+    for pos in range(16):
+        for b in range(256):
+            buf = bytearray(b"A" * 16)
+            buf[pos] = b
+            arr = np.frombuffer(bytes(buf), np.uint8).copy()
+            got = emu.emu_pack_chunk_pairs(P(arr), ctypes.byref(err))
+            assert (err.value == 0) == (b in CODE), (pos, b)
+            if b in CODE:
+                want = pair_order(int(oracle.pack_reference(bytes(buf))[0]))
+                assert got == want, (pos, b)
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        s = rng.choice(list(b"ACGTacgt"), 16).astype(np.uint8).tobytes()
+        arr = np.frombuffer(s, np.uint8).copy()
+        got = emu.emu_pack_chunk_pairs(P(arr), ctypes.byref(err))
+        assert err.value == 0
+        assert got == pair_order(int(oracle.pack_reference(s)[0]))
+
+
 def test_pack_chunk_and_window_random_streams(emu):
     rng = np.random.default_rng(3)
     err = ctypes.c_uint32()
