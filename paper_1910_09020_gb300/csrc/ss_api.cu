@@ -550,20 +550,31 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
     // ASCII input: fixed stride only; packed chunk by chunk into workspace.
     if (!uniform_len)
         return SS_ERR_UNSUPPORTED;  // pack first with ss_pack
+    // a uniform threshold from 1 to kSlicedMaxE: packed to the bit-sliced
+    // layout and filtered 32 pairs per thread (at E = 0 the pair-major
+    // pack and filter are cheaper)
+    const bool sliced = !E && e >= 1 && e <= ssk::kSlicedMaxE &&
+                        (flags & 3) != SS_MODE_BUCKETED;
     const int64_t w16 = (m + 15) / 16;
-    const size_t per_pair =
-        (size_t)2 * (size_t)w16 * 4 + (needs_bucket ? 4 : 0);
+    // bytes of one packed sequence (the sliced layout: 32 ceil(m/4) bytes
+    // per group of 32 sequences)
+    const size_t seq = sliced ? (size_t)((m + 3) / 4) + 1 : (size_t)w16 * 4;
+    const size_t per_pair = 2 * seq + (needs_bucket ? 4 : 0);
     const size_t fixed =
-        needs_bucket ? ssk::bucket_ws_bytes(0) + 2048 : 1024;
+        needs_bucket ? ssk::bucket_ws_bytes(0) + 2048 : 2048;
     if (ctx->budget <= fixed)
         return SS_ERR_OOM;
     int64_t chunk = (int64_t)((ctx->budget - fixed) / per_pair);
+    if (sliced && chunk < n)
+        chunk &= ~(int64_t)31;  // whole groups of 32 pairs
     if (chunk < 1)
         return SS_ERR_OOM;
     chunk = std::min(chunk, n);
     const size_t bws =
         needs_bucket ? align_up(ssk::bucket_ws_bytes(chunk), 256) : 0;
-    const size_t seq_bytes = align_up((size_t)chunk * w16 * 4, 256);
+    const size_t seq_bytes =
+        sliced ? align_up((size_t)ss_sliced_words(m, chunk) * 4, 256)
+               : align_up((size_t)chunk * w16 * 4, 256);
     SS_TRY(ensure_workspace(ctx, bws + 2 * seq_bytes));
     uint32_t *pq = (uint32_t *)((char *)ctx->ws + bws);
     uint32_t *pr = (uint32_t *)((char *)ctx->ws + bws + seq_bytes);
@@ -571,6 +582,14 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
         const int64_t cn = std::min(chunk, n - p0);
         const uint8_t *rq = (const uint8_t *)reads + p0 * (int64_t)m;
         const uint8_t *rr = (const uint8_t *)refs + p0 * (int64_t)m;
+        if (sliced) {
+            SS_CUDA(ssk::launch_pack_sliced(rq, cn, m, pq, ctx->d_status, st));
+            SS_CUDA(ssk::launch_pack_sliced(rr, cn, m, pr, ctx->d_status, st));
+            ctx->counters.launches += 2;
+            SS_TRY(filter_sliced(ctx, pq, pr, m, e, cn, out_accept + p0,
+                                 out_obstacles + p0, st));
+            continue;
+        }
         SS_CUDA(ssk::launch_pack_fixed(rq, cn, m, pq, ctx->d_status, st));
         SS_CUDA(ssk::launch_pack_fixed(rr, cn, m, pr, ctx->d_status, st));
         ctx->counters.launches += 2;
@@ -605,9 +624,15 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     if (!g.ok)
         return SS_ERR_CUDA;
     const int64_t w16 = (m + 15) / 16;
+    // ASCII input with every threshold up to kSlicedMaxE: each chunk packed
+    // once to the bit-sliced layout, every threshold filtered over it
+    bool sliced = format == SS_FMT_ASCII && m > 0;
+    for (int t = 0; t < n_e; ++t)
+        sliced &= e_list[t] <= ssk::kSlicedMaxE;
     // bytes of one sequence in the input format
     const size_t seq_in = format == SS_FMT_ASCII ? (size_t)m : (size_t)w16 * 4;
-    const size_t packed = (size_t)w16 * 4;
+    const size_t packed = sliced ? (size_t)((m + 3) / 4) + 1
+                                 : (size_t)w16 * 4;
     const size_t per_pair = 2 * seq_in +
                             (format == SS_FMT_ASCII ? 2 * packed : 0) +
                             (size_t)n_e * 5 + (all_plain ? 0 : 2);
@@ -618,14 +643,20 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
     // fills the GPU.
     int64_t chunk = (int64_t)(ctx->budget / (2 * per_pair + 2048));
     chunk = std::min<int64_t>(chunk, (int64_t)1 << 21);
+    if (sliced && chunk < n)
+        chunk &= ~(int64_t)31;  // whole groups of 32 pairs
     chunk = std::min(chunk, n);
     if (chunk < 1)
         return SS_ERR_OOM;
     const size_t a_in = align_up((size_t)chunk * seq_in, 256);
     const size_t a_pk =
-        format == SS_FMT_ASCII ? align_up((size_t)chunk * packed, 256) : 0;
-    const size_t a_acc = align_up((size_t)chunk * n_e, 256);
-    const size_t a_obs = align_up((size_t)chunk * 4 * n_e, 256);
+        format != SS_FMT_ASCII ? 0
+        : sliced ? align_up((size_t)ss_sliced_words(m, chunk) * 4, 256)
+                 : align_up((size_t)chunk * packed, 256);
+    // per threshold, results at 16-byte aligned offsets
+    const size_t acc_stride = align_up((size_t)chunk, 16);
+    const size_t a_acc = align_up(acc_stride * n_e, 256);
+    const size_t a_obs = align_up(acc_stride * 4 * n_e, 256);
     const size_t slot = 2 * a_in + 2 * a_pk + a_acc + a_obs;
     // the bucket area (thresholds beyond the plain kernel) sits first
     const size_t bws =
@@ -649,7 +680,13 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
         SS_CUDA(cudaMemcpyAsync(dr, (const char *)refs + p0 * seq_in,
                                 in_bytes, cudaMemcpyHostToDevice, st));
         const uint32_t *fq = (const uint32_t *)dq, *fr = (const uint32_t *)dr;
-        if (format == SS_FMT_ASCII) {
+        if (sliced) {
+            SS_CUDA(ssk::launch_pack_sliced((const uint8_t *)dq, cn, m, pq,
+                                            ctx->d_status, st));
+            SS_CUDA(ssk::launch_pack_sliced((const uint8_t *)dr, cn, m, pr,
+                                            ctx->d_status, st));
+            ctx->counters.launches += 2;
+        } else if (format == SS_FMT_ASCII) {
             SS_CUDA(ssk::launch_pack_fixed((const uint8_t *)dq, cn, m, pq,
                                            ctx->d_status, st));
             SS_CUDA(ssk::launch_pack_fixed((const uint8_t *)dr, cn, m, pr,
@@ -659,9 +696,12 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
             fr = pr;
         }
         for (int t = 0; t < n_e; ++t) {
-            uint8_t *ta = dacc + (size_t)t * cn;
-            int32_t *to = dobs + (size_t)t * cn;
-            if (m == 0) {
+            uint8_t *ta = dacc + (size_t)t * acc_stride;
+            int32_t *to = dobs + (size_t)t * acc_stride;
+            if (sliced) {
+                SS_TRY(filter_sliced(ctx, pq, pr, m, e_list[t], cn, ta, to,
+                                     st));
+            } else if (m == 0) {
                 SS_CUDA(cudaMemsetAsync(ta, 1, (size_t)cn, st));
                 SS_CUDA(cudaMemsetAsync(to, 0, (size_t)cn * 4, st));
             } else {

@@ -144,3 +144,38 @@ def test_sliced_argument_errors(F):
     a, o = F.filter(q, q, m=0, e=3, n=n, fmt=SLICED, out_accept=acc,
                     out_obstacles=obs, sync=True)
     assert (a.cpu().numpy() == 1).all() and (o.cpu().numpy() == 0).all()
+
+
+def test_filter_host_ascii_uses_sliced_chunks():
+    """ss_filter_host from ASCII host buffers: thresholds up to 15 go through
+    the sliced layout (chunks of whole groups), a sweep with a larger one
+    through the pair-major form; both against the oracle, several chunks."""
+    torch = torch_cuda()
+    n, m = 5001, 150
+    reads, refs = synth.pairs_fixed(330, 0, n, m, synth.rate_recipe(0.12))
+    hq = torch.from_numpy(reads.reshape(-1).copy()).pin_memory().view(n, m)
+    hr = torch.from_numpy(refs.reshape(-1).copy()).pin_memory().view(n, m)
+    with binding.Filter(0, workspace_bytes=1 << 20) as F2:
+        for sweep in ([0, 1, 7, 15], [3, 20]):
+            acc, obs = F2.filter_host(hq, hr, m=m, e=sweep,
+                                      fmt=binding.SS_FMT_ASCII)
+            for t, E in enumerate(sweep):
+                oacc, oobs = oracle_fixed(reads, refs, E)
+                assert_same(acc[t].numpy(), obs[t].numpy(), oacc, oobs,
+                            f"filter_host {sweep} E={E}")
+
+
+def test_filter_batch_ascii_uses_sliced_chunks():
+    """ss_filter_batch on resident ASCII with a small workspace: E from 1 to
+    15 packs to the sliced layout chunk by chunk (whole groups), E = 0 the
+    pair-major form."""
+    n, m = 10007, 100
+    reads, refs = synth.pairs_fixed(331, 0, n, m, synth.SHORT_POISSON)
+    dq, dr = to_dev(reads.reshape(-1)), to_dev(refs.reshape(-1))
+    with binding.Filter(0, workspace_bytes=256 << 10) as F2:
+        for E in (0, 1, 5, 15):
+            acc, obs = F2.filter(dq, dr, m=m, e=E, n=n,
+                                 fmt=binding.SS_FMT_ASCII, sync=True)
+            oacc, oobs = oracle_fixed(reads, refs, E)
+            assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                        f"ascii E={E}")
