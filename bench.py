@@ -8,10 +8,13 @@ odd pairs are independent random sequences (the shape of the paper's
 100 bp datasets, Section 3.1) -- filtered at E = 0, 2, 4, 6, 8, 10.
 
 One step = the whole hot path over the batch: pack the resident ASCII reads
-and references to 2 bits (2 launches) and run one plain filter launch per
-threshold (6 launches).  ``value`` counts pair decisions (pairs x
+and references to 2 bits per base in the bit-sliced layout (SS_FMT_SLICED2,
+2 launches) and run one plain filter launch per threshold over it (6
+launches, 32 pairs per thread).  ``value`` counts pair decisions (pairs x
 thresholds) per second with the inputs resident in HBM; the inputs (6 GB
-ASCII + 1.7 GB packed) are far larger than L2, so no flush is needed.
+ASCII + 1.5 GB packed) are far larger than L2, so no flush is needed.
+``pair_major_form`` times the same step with the pair-major packed format
+and its one-pair-per-thread kernel, beside the headline.
 ``e2e`` runs the same sweep through ``ss_filter_host`` from pinned host
 buffers (copies inside the timed region).  ``cpu_baseline`` times the CPU
 oracle on the host cores over every pair of the workload at every
@@ -61,6 +64,13 @@ PACK_BYTES_PER_PAIR = 2 * M + 2 * ((M + 3) // 4)
 #   rows, each 7 ops (2 funnel shifts of the query planes, 2 XORs with the
 #   broadcast reference base, 1 OR, 1 AND into the surviving rows, 1 for
 #   the broadcast); per iteration 4 bookkeeping ops; no find-first.
+# * bit-sliced columns: 32 pairs of one length walked together, one pair
+#   per bit; per column and 32 pairs two three-input logic ops per row (the
+#   two code bits' equality), E three-input ORs for the column's "all rows
+#   dead" and E+1 ops of the saturating count: (6E+3)/32 logic ops per pair
+#   and column, over all m columns (a group of 32 stops early only when all
+#   of its pairs are past E).  The S_d | z restarts are adds on the FMA pipe
+#   and are not counted against the logic pipe.
 K_WORD, K_RED, K_ITER = 7, 1, 4
 K_COL = 7
 
@@ -194,6 +204,9 @@ KERNEL_SOURCES = {
                      "ss_rwc.cuh", "ss_rw_launch.cuh", "ss_rw_e0.cu",
                      "ss_rw_e1.cu", "ss_rw_e2.cu", "ss_rw_e3.cu"],
     "k_pack_fixed": ["ss_device.cuh", "ss_pack.cuh", "ss_pack.cu"],
+    "k_sliced": ["ss_device.cuh", "ss_sliced.cuh", "ss_sliced.cu"],
+    "k_pack_sliced_span": ["ss_device.cuh", "ss_pack.cuh", "ss_sliced.cuh",
+                           "ss_pack.cu"],
 }
 
 
@@ -293,28 +306,43 @@ def column_ops(E: int, iters, cols):
     return cols * ((2 * E + 1 + 31) // 32) * K_COL + iters * K_ITER
 
 
-def model_ops(E: int, words, iters, cols):
-    """ALU and find-first ops of the cheaper formulation (see K_COL), and
-    which one it is."""
+def sliced_ops(E: int, m: int, n: int):
+    """ALU ops of the bit-sliced column formulation for n pairs of length m
+    (every column walked)."""
+    return n * m * (6 * E + 3) / 32
+
+
+def model_ops(E: int, words, iters, cols, sliced=None):
+    """ALU and find-first ops of the cheapest formulation (see K_COL), and
+    which one it is.  sliced: the bit-sliced formulation's ops where the
+    pairs come in groups of one length (else not a candidate)."""
     rows = row_word_ops(E, words, iters)
     by_col = column_ops(E, iters, cols)
-    if by_col < rows:
-        return by_col, 0, "columns"
-    return rows, words, "row words"
+    best = (rows, words, "row words")
+    if by_col < best[0]:
+        best = (by_col, 0, "columns")
+    if sliced is not None and sliced < best[0]:
+        best = (sliced, 0, "bit-sliced columns")
+    return best
 
 
-def op_model(stats: dict, n: int) -> dict:
-    """Per-pair algorithmic ALU and find-first ops of each threshold."""
+def op_model(stats: dict, n: int, m: int | None = None) -> dict:
+    """Per-pair algorithmic ALU and find-first ops of each threshold (with
+    m: the bit-sliced formulation is a candidate, uniform length m)."""
     out = {}
     for E, (cells, words, iters, cols) in stats.items():
-        alu, xu, form = model_ops(E, words, iters, cols)
+        sl = sliced_ops(E, m, n) if m else None
+        alu, xu, form = model_ops(E, words, iters, cols, sl)
         out[E] = {"alu_ops_per_pair": alu / n, "xu_ops_per_pair": xu / n,
                   "model": form,
                   "alu_ops_row_words_per_pair":
                       row_word_ops(E, words, iters) / n,
+                  "alu_ops_columns_per_pair": column_ops(E, iters, cols) / n,
                   "iterations_per_pair": iters / n,
                   "columns_per_pair": cols / n,
                   "cells_per_pair": cells / n}
+        if sl is not None:
+            out[E]["alu_ops_sliced_per_pair"] = sl / n
     return out
 
 
@@ -371,8 +399,9 @@ def run_reference(args):
 def config_dict(world: int, n_override: int | None = None) -> dict:
     return {"workload": WORKLOAD, "pairs_per_gpu": n_override or N_PAIRS,
             "read_length": M, "thresholds": SWEEP, "format": "ASCII resident, "
-            "packed to 2 bits in the step", "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2 (6 GB ASCII + 1.7 GB packed)"}
+            "packed in the step to 2 bits per base, bit-sliced (32 pairs per "
+            "word)", "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (6 GB ASCII + 1.5 GB packed)"}
 
 
 # ---- batched and served forms (configurations beside the headline) ------------
@@ -962,9 +991,9 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     F = binding.Filter(local, workspace_bytes=8 << 30)
-    W16 = binding.ss_packed_words(M)
-    pq = torch.empty(n * W16, dtype=torch.int32, device=dev)
-    pr = torch.empty(n * W16, dtype=torch.int32, device=dev)
+    SL = binding.ss_sliced_words(M, n)
+    sq = torch.empty(SL, dtype=torch.int32, device=dev)
+    sr = torch.empty(SL, dtype=torch.int32, device=dev)
     acc = torch.empty((len(SWEEP), n), dtype=torch.uint8, device=dev)
     obs = torch.empty((len(SWEEP), n), dtype=torch.int32, device=dev)
     # events on the stream the kernels are launched on (torch's current
@@ -977,15 +1006,15 @@ def run_ours(args):
     def step(ev):
         if ev:
             ev[0].record()
-        F.pack(dq, m=M, n=n, out=pq)
-        F.pack(dr, m=M, n=n, out=pr)
+        F.pack_sliced(dq, m=M, n=n, out=sq)
+        F.pack_sliced(dr, m=M, n=n, out=sr)
         if ev:
             ev[1].record()
         for t, E in enumerate(SWEEP):
             if ev:
                 ev[2 + 2 * t].record()
-            F.filter(pq, pr, m=M, e=E, n=n, out_accept=acc[t],
-                     out_obstacles=obs[t])
+            F.filter(sq, sr, m=M, e=E, n=n, fmt=binding.SS_FMT_SLICED2,
+                     out_accept=acc[t], out_obstacles=obs[t])
             if ev:
                 ev[3 + 2 * t].record()
 
@@ -1063,6 +1092,30 @@ def run_ours(args):
         dist.destroy_process_group()
         return 0
 
+    # the same step in the pair-major packed format (one pair per thread),
+    # beside the headline; its results must equal the sliced form's
+    del sq, sr
+    W16 = binding.ss_packed_words(M)
+    pq = torch.empty(n * W16, dtype=torch.int32, device=dev)
+    pr = torch.empty(n * W16, dtype=torch.int32, device=dev)
+    pm_acc = torch.empty(n, dtype=torch.uint8, device=dev)
+    pm_obs = torch.empty(n, dtype=torch.int32, device=dev)
+    pair_major = {"per_E_ms": {}, "results_identical": True}
+    pair_major["pack_ms"] = _time_ms(
+        lambda: (F.pack(dq, m=M, n=n, out=pq), F.pack(dr, m=M, n=n, out=pr)),
+        3, F.sync)
+    for t, E in enumerate(SWEEP):
+        pair_major["per_E_ms"][E] = _time_ms(
+            lambda: F.filter(pq, pr, m=M, e=E, n=n, out_accept=pm_acc,
+                             out_obstacles=pm_obs), 3, F.sync)
+        pair_major["results_identical"] &= bool(
+            torch.equal(pm_acc, acc[t]) and torch.equal(pm_obs, obs[t]))
+    pair_major["step_ms"] = (pair_major["pack_ms"]
+                             + sum(pair_major["per_E_ms"].values()))
+    pair_major["pairs_per_s"] = (n * len(SWEEP)
+                                 / (pair_major["step_ms"] * 1e-3))
+    pair_major["kernels"] = "k_pack_fixed x2, k_rw_uniform<E> x6"
+
     # roofline of the dominant kernel: the filter launches of the sweep
     peaks = measured_peaks()
     ipk = measure_int_peaks(local)
@@ -1073,7 +1126,7 @@ def run_ours(args):
         cpu, stats, parity = cpu_oracle_full(
             hq.numpy().reshape(n, M), hr.numpy().reshape(n, M),
             acc.cpu().numpy(), obs.cpu().numpy())
-        model = op_model(stats, n)
+        model = op_model(stats, n, M)
     hbm = peaks["hbm_gbs"] * 1e9
     per_launch = []
     roof_total = meas_total = 0.0
@@ -1092,6 +1145,10 @@ def run_ours(args):
                       "alu_ops_per_pair": model[E]["alu_ops_per_pair"],
                       "alu_ops_row_words_per_pair":
                           model[E]["alu_ops_row_words_per_pair"],
+                      "alu_ops_columns_per_pair":
+                          model[E]["alu_ops_columns_per_pair"],
+                      "alu_ops_sliced_per_pair":
+                          model[E].get("alu_ops_sliced_per_pair"),
                       "columns_per_pair": model[E]["columns_per_pair"],
                       "tops": n * model[E]["alu_ops_per_pair"] / (ms * 1e-3)
                       / 1e12})
@@ -1114,15 +1171,18 @@ def run_ours(args):
         ops = sum(n * model[E]["alu_ops_per_pair"] for E in SWEEP)
         achieved = ops / (filter_ms * 1e-3) / 1e12
         peak, unit = ipk["lop3"] / 1e12, "Tops/s"
-    traffic = ncu_traffic("k_rw_uniform")
+    traffic = ncu_traffic("k_sliced")
     roofline = {
-        "kernel": "k_rw_uniform (plain filter, one launch per E)",
+        "kernel": "k_sliced (plain filter over the bit-sliced layout, one "
+                  "launch per E)",
         "bound": dom_bound, "achieved": achieved, "peak": peak, "unit": unit,
         "frac": roof_total / meas_total,
         "frac_note": "sum over the sweep of max(HBM, ALU, find-first) "
                      "roofline time / measured time; the ALU term counts "
-                     "the cheaper of the row-word and column formulations "
-                     "of the greedy for each E (per_launch[].model)",
+                     "the cheapest of three formulations of the greedy for "
+                     "each E (per_launch[].model): row words, columns one "
+                     "pair per thread, bit-sliced columns (32 pairs per "
+                     "word, every column walked)",
         "traffic": None if traffic is None else traffic * n,
         "algorithmic_bytes_per_launch": n * FILTER_BYTES_PER_PAIR,
         "peak_source": f"HBM {peaks['hbm_source']} ({peaks['hbm_gbs']} GB/s); "
@@ -1177,6 +1237,7 @@ def run_ours(args):
         "breakdown": {"pack_ms": pack_ms, "filter_ms": filter_ms,
                       "pack_gbs": n * PACK_BYTES_PER_PAIR / (pack_ms * 1e-3)
                       / 1e9, "generate_s": gen_s},
+        "pair_major_form": pair_major,
         "accuracy": accuracy,
         **extras,
     }
