@@ -274,58 +274,80 @@ __global__ void __launch_bounds__(32 * kPackSlicedWarps)
     // chunks [cb, cb + nc): the span, plus one (windows read word k+1)
     const int nc = (int)(((p1 * m + 15) >> 4) - cb) + 1;
     const int64_t limit = n * (int64_t)m;
-    const bool aligned = ((uintptr_t)ascii & 15) == 0;
+    // every chunk whole, 16-byte aligned and inside the input: the common
+    // case, one uniform branch for the CTA
+    const bool fast =
+        ((uintptr_t)ascii & 15) == 0 && (cb + nc) * 16 <= limit;
     uint32_t err = 0;
+    if (fast) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(ascii) + cb;
 #pragma unroll 4
-    for (int c = threadIdx.x; c < nc; c += 32 * kPackSlicedWarps) {
-        const int64_t at = (cb + c) * 16;
-        uint32_t x[4];
-        if (aligned && at + 16 <= limit) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(ascii + at));
-            x[0] = v.x;
-            x[1] = v.y;
-            x[2] = v.z;
-            x[3] = v.w;
-        } else {
-            // the input's last partial chunk, or an unaligned input: bytes
-            // past the end count as 'A'
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t w = 0;
-                for (int b = 0; b < 4; ++b) {
-                    const int64_t j = at + 4 * q + b;
-                    const uint32_t ch =
-                        j < limit ? (uint32_t)__ldg(ascii + j) : 0x41u;
-                    w |= ch << (8 * b);
-                }
-                x[q] = w;
-            }
+        for (int c = threadIdx.x; c < nc; c += 32 * kPackSlicedWarps) {
+            const uint4 v = __ldg(src + c);
+            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+            code[c] = pack_chunk_pairs(x, err);
         }
-        code[c] = pack_chunk_pairs(x, err);
+    } else {
+        for (int c = threadIdx.x; c < nc; c += 32 * kPackSlicedWarps) {
+            const int64_t at = (cb + c) * 16;
+            uint32_t x[4];
+            if (((uintptr_t)ascii & 15) == 0 && at + 16 <= limit) {
+                const uint4 v =
+                    __ldg(reinterpret_cast<const uint4 *>(ascii + at));
+                x[0] = v.x;
+                x[1] = v.y;
+                x[2] = v.z;
+                x[3] = v.w;
+            } else {
+                // the input's last partial chunk, or an unaligned input:
+                // bytes past the end count as 'A'
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t w = 0;
+                    for (int b = 0; b < 4; ++b) {
+                        const int64_t j = at + 4 * q + b;
+                        const uint32_t ch =
+                            j < limit ? (uint32_t)__ldg(ascii + j) : 0x41u;
+                        w |= ch << (8 * b);
+                    }
+                    x[q] = w;
+                }
+            }
+            code[c] = pack_chunk_pairs(x, err);
+        }
     }
     __syncthreads();
     const int64_t g = g0 + warp;
     if (warp < gpc && g < G) {
         const int64_t p = g * 32 + lane;
-        const bool live = p < n;
+        const uint32_t live = p < n ? 0xffffffffu : 0u;
         const int w16 = (m + 15) >> 4;
-        const int nb4 = 4 * ((m + 3) >> 2);  // bases of the stored blocks
-        // bit of the stream where the pair's base 0 sits
-        const uint32_t o0 = live ? (uint32_t)(2 * (p * m - cb * 16)) : 0u;
-        for (int c = 0; c < w16; ++c) {
-            uint32_t w = 0u;
-            if (live) {
-                const uint32_t o = o0 + 32u * (uint32_t)c;
-                const uint32_t k = o >> 5;
-                w = funnel_r(code[k], code[k + 1], o & 31u) &
-                    mask_below(2 * (m - 16 * c));
-            }
+        // bit of the stream where the pair's base 0 sits (pad lanes read
+        // the group's first pair and keep nothing)
+        const uint32_t o0 =
+            (uint32_t)(2 * ((p < n ? p : g * 32) * m - cb * 16));
+        // lane r stores code bit r%2 of base 16c + r/2: word
+        // ((4c + r/8) * G + g) * 8 + (r%2) * 4 + (r/2)%4
+        uint32_t *dst = out + ((int64_t)(lane >> 3) * G + g) * 8 +
+                        (lane & 1) * 4 + ((lane >> 1) & 3);
+        const int64_t step = 32 * G;  // four blocks
+        for (int c = 0; c + 1 < w16; ++c) {
+            const uint32_t o = o0 + 32u * (uint32_t)c;
+            const uint32_t k = o >> 5;
+            uint32_t w = funnel_r(code[k], code[k + 1], o & 31u) & live;
             w = warp_transpose32(w, lane);
-            const int j = 16 * c + (lane >> 1);
-            if (j < nb4)
-                out[((int64_t)(j >> 2) * G + g) * 8 + (lane & 1) * 4 +
-                    (j & 3)] = w;
+            dst[c * step] = w;
         }
+        // the last 16 bases: codes past the pair's end cleared, words of
+        // blocks past the last one not stored
+        const int c = w16 - 1;
+        const uint32_t o = o0 + 32u * (uint32_t)c;
+        const uint32_t k = o >> 5;
+        uint32_t w = funnel_r(code[k], code[k + 1], o & 31u) & live &
+                     mask_below(2 * (m - 16 * c));
+        w = warp_transpose32(w, lane);
+        if (16 * c + (lane >> 1) < 4 * ((m + 3) >> 2))
+            dst[c * step] = w;
     }
     if (__any_sync(0xffffffffu, err != 0u) && lane == 0)
         atomicOr(status, kStatusInvalidBase);
