@@ -75,7 +75,7 @@ extern "C" {
 #define SS_FLAG_NO_GRAPH 16 /* do not replay the captured CUDA graph           */
 
 /* Largest E of the plain launch over SS_FMT_SLICED2 input. */
-#define SS_SLICED_MAX_E 15
+#define SS_SLICED_MAX_E 31
 
 /* Largest uniform E and m the plain launch covers. */
 #define SS_PLAIN_MAX_E 31

@@ -37,7 +37,7 @@ SS_FLAG_NO_GRAPH = 16
 PLAIN_MAX_E = 31
 PLAIN_MAX_M = 1024
 # largest E of the plain launch over SS_FMT_SLICED2 input (SS_SLICED_MAX_E)
-SLICED_MAX_E = 15
+SLICED_MAX_E = 31
 
 # every symbol include/ss.h declares (checked by the CPU tests)
 EXPORTED = (

@@ -25,7 +25,7 @@ cudaError_t launch_pack_varlen(const uint8_t *ascii, const int64_t *offsets,
 // Bit-sliced layout (SS_FMT_SLICED2): fixed-stride ASCII -> sliced words
 // (8 * ceil(m/4) * ceil(n/32) of them), and the plain launch over it for
 // 0 <= E <= kSlicedMaxE.
-constexpr int kSlicedMaxE = 15;
+constexpr int kSlicedMaxE = 31;
 cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
                                uint32_t *out, int *status, cudaStream_t st);
 cudaError_t launch_sliced(const uint32_t *reads, const uint32_t *refs,

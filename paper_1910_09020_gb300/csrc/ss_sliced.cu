@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(kSlicedThreads) k_sliced(const SlicedArgs a)
     const int64_t p0 = g * 32;
     const int np = (int)min((int64_t)32, a.n - p0);
     const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
-    uint32_t T[E + 2];
-    sliced_walk<E>(SlicedSrc{a.q, a.r, a.G, g}, a.m, pad, T, vtab, a.one);
+    SlicedCount<E> cnt;
+    sliced_walk<E>(SlicedSrc{a.q, a.r, a.G, g}, a.m, pad, cnt, vtab, a.one);
     uint32_t cb[SlicedShape<E>::NB];
-    sliced_binary<E>(T, cb);
-    const uint32_t ok = ~T[E + 1];  // count <= E (Section 2.4 step 5)
+    cnt.bits(cb);
+    const uint32_t ok = ~cnt.done();  // count <= E (Section 2.4 step 5)
     if (np == 32 && a.vec) {
         uint4 *o = reinterpret_cast<uint4 *>(a.obs + p0);
 #pragma unroll

@@ -97,6 +97,94 @@ SS_HD uint32_t or_tree(const uint32_t (&x)[N])
     }
 }
 
+// min(count, E+1) of the 32 pairs of a group, bit-sliced.  Below
+// kSlicedBinaryFromE a thermometer: T[c] = pairs with count >= c, c = 1..E+1
+// (E+1 logic ops per column, saturating by construction).  From it a
+// saturating binary count: bit b of the count in c[b] (NB words) and the
+// pairs that reached E+1 in dn; per column one op for the increment
+// (restarted and not done), two per bit for the ripple and about NB/2 for
+// "reached E+1" -- fewer ops and registers than the thermometer once E+1
+// passes about 12.
+constexpr int kSlicedBinaryFromE = 11;
+
+template <int E, bool BIN = (E >= kSlicedBinaryFromE)>
+struct SlicedCount;
+
+template <int E>
+struct SlicedCount<E, false> {
+    uint32_t T[E + 2];
+    // pad: pairs that do not exist, counted as past E
+    SS_HD void init(uint32_t pad)
+    {
+#pragma unroll
+        for (int c = 0; c <= E; ++c)
+            T[c] = 0u;
+        T[E + 1] = pad;
+    }
+    // nz: the pairs with a row still alive at this column (the others
+    // count one obstacle): T_c |= T_c-1 & ~nz, T_1 |= ~nz
+    SS_HD void step(uint32_t nz)
+    {
+#pragma unroll
+        for (int c = E + 1; c >= 2; --c)
+            T[c] = lop3<0xF4>(T[c], T[c - 1], nz);
+        T[1] = lop3<0xF3>(T[1], nz, 0u);
+    }
+    // pairs whose count reached E+1
+    SS_HD uint32_t done() const { return T[E + 1]; }
+    // binary bits of min(count, E+1): bit b is the XOR of T[c] over the
+    // multiples c of 2^b (T[c] = count >= c, so that XOR is the parity of
+    // floor(count / 2^b))
+    SS_HD void bits(uint32_t (&cb)[SlicedShape<E>::NB]) const
+    {
+#pragma unroll
+        for (int b = 0; b < SlicedShape<E>::NB; ++b) {
+            uint32_t x = 0u;
+#pragma unroll
+            for (int c = 1 << b; c <= E + 1; c += 1 << b)
+                x ^= T[c];
+            cb[b] = x;
+        }
+    }
+};
+
+template <int E>
+struct SlicedCount<E, true> {
+    static constexpr int NB = SlicedShape<E>::NB;
+    uint32_t c[NB];
+    uint32_t dn;  // pairs whose count is E+1 (and the padding)
+    SS_HD void init(uint32_t pad)
+    {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            c[b] = 0u;
+        dn = pad;
+    }
+    SS_HD void step(uint32_t nz)
+    {
+        // +1 for the pairs with every row dead, unless already at E+1
+        uint32_t k = lop3<0x03>(nz, dn, 0u);  // ~(nz | dn)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const uint32_t x = c[b];
+            c[b] = x ^ k;
+            k &= x;
+        }
+        uint32_t eq = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            eq &= (((E + 1) >> b) & 1) ? c[b] : ~c[b];
+        dn |= eq;
+    }
+    SS_HD uint32_t done() const { return dn; }
+    SS_HD void bits(uint32_t (&cb)[NB]) const
+    {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            cb[b] = c[b];
+    }
+};
+
 // The edge blocks of a walk of m columns: a block k is an edge block when
 // one of its columns has a diagonal that reads a query base outside 0..m-1
 // (Eq. 1 case 4): k < kl (j0 < E) or k >= kr (j0 + 3 + E >= m).  Their
@@ -137,7 +225,7 @@ struct SlicedEdges {
 // run-time value: S_d * one + z is a multiply-add on the FMA pipe).
 template <int E, bool EDGE, int U>
 SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
-                         uint32_t (&T)[E + 2],
+                         SlicedCount<E> &cnt,
                          const uint32_t (&ql)[SlicedShape<E>::WW],
                          const uint32_t (&qh)[SlicedShape<E>::WW],
                          const uint32_t (&rl)[4], const uint32_t (&rh)[4],
@@ -155,13 +243,10 @@ SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
             s &= vw[w];
         S[d] = s;
     }
-    // the pairs with every row dead: count this column's obstacle
-    // (T_c |= T_c-1 & ~nz), restart at the next column
+    // the pairs with every row dead: count this column's obstacle,
+    // restart at the next column
     const uint32_t nz = or_tree<Sh::ND>(S);
-#pragma unroll
-    for (int c = E + 1; c >= 2; --c)
-        T[c] = lop3<0xF4>(T[c], T[c - 1], nz);
-    T[1] = lop3<0xF3>(T[1], nz, 0u);
+    cnt.step(nz);
     z = ~nz;
 }
 
@@ -169,36 +254,35 @@ SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
 // block).
 template <int E, bool EDGE>
 SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
-                        uint32_t (&T)[E + 2],
+                        SlicedCount<E> &cnt,
                         const uint32_t (&ql)[SlicedShape<E>::WW],
                         const uint32_t (&qh)[SlicedShape<E>::WW],
                         const uint32_t (&rl)[4], const uint32_t (&rh)[4],
                         const uint32_t *vw, int live, uint32_t one)
 {
     if (live >= 4) {
-        sliced_column<E, EDGE, 0>(S, z, T, ql, qh, rl, rh, vw, one);
-        sliced_column<E, EDGE, 1>(S, z, T, ql, qh, rl, rh, vw, one);
-        sliced_column<E, EDGE, 2>(S, z, T, ql, qh, rl, rh, vw, one);
-        sliced_column<E, EDGE, 3>(S, z, T, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 0>(S, z, cnt, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 1>(S, z, cnt, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 2>(S, z, cnt, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 3>(S, z, cnt, ql, qh, rl, rh, vw, one);
     } else {
-        sliced_column<E, EDGE, 0>(S, z, T, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 0>(S, z, cnt, ql, qh, rl, rh, vw, one);
         if (live > 1)
-            sliced_column<E, EDGE, 1>(S, z, T, ql, qh, rl, rh, vw, one);
+            sliced_column<E, EDGE, 1>(S, z, cnt, ql, qh, rl, rh, vw, one);
         if (live > 2)
-            sliced_column<E, EDGE, 2>(S, z, T, ql, qh, rl, rh, vw, one);
+            sliced_column<E, EDGE, 2>(S, z, cnt, ql, qh, rl, rh, vw, one);
     }
 }
 
-// Walk the 32 pairs of one group over all m columns; on return T[c] (c =
-// 1..E+1) holds the pairs whose count reached c, i.e. bit i of the pair's
-// min(count, E+1) in thermometer form.  pad: pairs that do not exist (the
-// last group's), counted as past E so that the group can stop early.
+// Walk the 32 pairs of one group over all m columns; on return cnt holds
+// each pair's min(count, E+1).  pad: pairs that do not exist (the last
+// group's), counted as past E so that the group can stop early.
 // src.query(blk, nb, lo, hi) / src.ref(blk, lo, hi) load the four words of
 // each plane of a block (zero for a query block outside 0..nb-1); vtab:
 // the validity table of SlicedEdges<E>(m), WW words per row.
 template <int E, class Src>
 SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
-                       uint32_t (&T)[E + 2], const uint32_t *vtab,
+                       SlicedCount<E> &cnt, const uint32_t *vtab,
                        uint32_t one)
 {
     using Sh = SlicedShape<E>;
@@ -220,10 +304,7 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
     for (int d = 0; d < Sh::ND; ++d)
         S[d] = 0xffffffffu;
     uint32_t z = 0u;
-#pragma unroll
-    for (int c = 0; c <= E; ++c)
-        T[c] = 0u;
-    T[E + 1] = pad;
+    cnt.init(pad);
     uint32_t rl[4], rh[4];
     if (nb > 0)
         src.ref(0, rl, rh);
@@ -235,12 +316,12 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
             src.ref(k + 1, nrl, nrh);
         const int live = imin(4, m - 4 * k);
         if (k < ed.kl || k >= ed.kr)
-            sliced_block<E, true>(S, z, T, ql, qh, rl, rh,
+            sliced_block<E, true>(S, z, cnt, ql, qh, rl, rh,
                                   vtab + ed.row_of(k) * Sh::WW, live, one);
         else
-            sliced_block<E, false>(S, z, T, ql, qh, rl, rh, nullptr, live,
+            sliced_block<E, false>(S, z, cnt, ql, qh, rl, rh, nullptr, live,
                                    one);
-        if (T[E + 1] == 0xffffffffu)
+        if (cnt.done() == 0xffffffffu)
             break;  // every pair of the group is past E
 #pragma unroll
         for (int w = 0; w + 4 < Sh::WW; ++w) {
@@ -254,23 +335,6 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
             rl[x] = nrl[x];
             rh[x] = nrh[x];
         }
-    }
-}
-
-// Binary bits of the thermometer count: bit b of min(count, E+1) is the XOR
-// of T[c] over the multiples c of 2^b (T[c] = count >= c, so that XOR is
-// the parity of floor(count / 2^b)).
-template <int E>
-SS_HD void sliced_binary(const uint32_t (&T)[E + 2],
-                         uint32_t (&cb)[SlicedShape<E>::NB])
-{
-#pragma unroll
-    for (int b = 0; b < SlicedShape<E>::NB; ++b) {
-        uint32_t x = 0u;
-#pragma unroll
-        for (int c = 1 << b; c <= E + 1; c += 1 << b)
-            x ^= T[c];
-        cb[b] = x;
     }
 }
 

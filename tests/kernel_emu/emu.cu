@@ -202,13 +202,13 @@ void sliced_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
         std::vector<uint32_t> vtab(Ed::kRows * WW);
         for (int i = 0; i < ed.rows() * WW; ++i)
             vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, m);
-        uint32_t T[E + 2];
-        sliced_walk<E>(HostSliced{q, r, G, g}, m, pad, T, vtab.data(), 1u);
+        SlicedCount<E> cnt;
+        sliced_walk<E>(HostSliced{q, r, G, g}, m, pad, cnt, vtab.data(), 1u);
         uint32_t cb[SlicedShape<E>::NB];
-        sliced_binary<E>(T, cb);
+        cnt.bits(cb);
         for (int i = 0; i < np; ++i) {
             obs[32 * g + i] = sliced_count<E>(cb, i);
-            acc[32 * g + i] = (uint8_t)(((~T[E + 1]) >> i) & 1u);
+            acc[32 * g + i] = (uint8_t)(((~cnt.done()) >> i) & 1u);
         }
     }
 }
@@ -234,7 +234,7 @@ int emu_sliced(const uint32_t *q, const uint32_t *r, int64_t n, int m, int E,
                uint8_t *acc, int32_t *obs)
 {
     return sliced_dispatch(E, q, r, n, m, acc, obs,
-                           std::make_integer_sequence<int, 16>{});
+                           std::make_integer_sequence<int, 32>{});
 }
 
 // The warp transpose of the sliced packer, the 32 lanes simulated in turn:

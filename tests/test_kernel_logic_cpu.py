@@ -362,7 +362,8 @@ def test_sliced_transpose_is_the_bit_transpose(emu):
                                101, 150, 251])
 def test_sliced_walk_matches_oracle(emu, m):
     """The bit-sliced walk (32 pairs per thread, columns in blocks of four,
-    the query window either side) at every E it is built for, on groups
+    the query window either side, the thermometer count below E = 11 and
+    the saturating binary count from it) at every E it is built for, on groups
     mixing near and far pairs, a ragged last group, lengths below, at and
     around E and the block edges."""
     rng = np.random.default_rng(1000 + m)
@@ -371,7 +372,7 @@ def test_sliced_walk_matches_oracle(emu, m):
     reads, refs = synth.pairs_fixed(7000 + m, 0, n, m, rec)
     q = oracle.pack_sliced(reads)
     r = oracle.pack_sliced(refs)
-    for E in range(16):
+    for E in range(32):
         acc = np.zeros(n, np.uint8)
         obs = np.zeros(n, np.int32)
         assert emu.emu_sliced(P(q), P(r), n, m, E, P(acc), P(obs)) == 0
