@@ -59,6 +59,18 @@ struct SlicedSrc {
     {
         load(r, blk, lo, hi);
     }
+    // both planes of a block are 32 contiguous bytes: one L1 line each
+    __device__ __forceinline__ void prefetch(int qblk, int rblk, int nb) const
+    {
+        if (qblk >= 0 && qblk < nb)
+            asm volatile("prefetch.global.L1 [%0];"
+                         :
+                         : "l"(q + ((int64_t)qblk * G + g) * 2));
+        if (rblk < nb)
+            asm volatile("prefetch.global.L1 [%0];"
+                         :
+                         : "l"(r + ((int64_t)rblk * G + g) * 2));
+    }
 };
 
 // Bytes 0..3 of the result: 1 for the pairs 4q..4q+3 of `ok` that are set.

@@ -186,6 +186,7 @@ struct HostSliced {
     {
         load(r, blk, lo, hi);
     }
+    void prefetch(int, int, int) const {}
 };
 
 template <int E>
