@@ -218,6 +218,42 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane)
     return v;
 }
 
+// The same transpose with its per-lane constants computed once per thread
+// (transpose_level's byte selectors, rotations and masks for this lane).
+struct LaneTranspose {
+    uint32_t s16, s8, a4, a2, a1, k4, k2, k1;
+    __device__ __forceinline__ explicit LaneTranspose(int lane)
+    {
+        s16 = (lane & 16) ? 0x3276u : 0x5410u;
+        s8 = (lane & 8) ? 0x3715u : 0x6240u;
+        a4 = (lane & 4) ? 28u : 4u;
+        a2 = (lane & 2) ? 30u : 2u;
+        a1 = (lane & 1) ? 31u : 1u;
+        k4 = (lane & 4) ? 0xf0f0f0f0u : 0x0f0f0f0fu;
+        k2 = (lane & 2) ? 0xccccccccu : 0x33333333u;
+        k1 = (lane & 1) ? 0xaaaaaaaau : 0x55555555u;
+    }
+    // (v & k) | (rotl(x, a) & ~k): one rotate and one lop3 per level
+    __device__ __forceinline__ static uint32_t level(uint32_t v, uint32_t x,
+                                                     uint32_t a, uint32_t k)
+    {
+        return lop3<0xE4>(v, funnel_l(x, x, a), k);
+    }
+    __device__ __forceinline__ uint32_t operator()(uint32_t v) const
+    {
+        uint32_t x = __shfl_xor_sync(0xffffffffu, v, 16);
+        v = prmt(v, x, s16);
+        x = __shfl_xor_sync(0xffffffffu, v, 8);
+        v = prmt(v, x, s8);
+        x = __shfl_xor_sync(0xffffffffu, v, 4);
+        v = level(v, x, a4, k4);
+        x = __shfl_xor_sync(0xffffffffu, v, 2);
+        v = level(v, x, a2, k2);
+        x = __shfl_xor_sync(0xffffffffu, v, 1);
+        return level(v, x, a1, k1);
+    }
+};
+
 __global__ void __launch_bounds__(32 * kPackSlicedWarps)
     k_pack_sliced(const uint8_t *__restrict__ ascii, int64_t n, int32_t m,
                   int64_t G, uint32_t *__restrict__ out, int *status)
@@ -322,30 +358,30 @@ __global__ void __launch_bounds__(32 * kPackSlicedWarps)
         const int64_t p = g * 32 + lane;
         const uint32_t live = p < n ? 0xffffffffu : 0u;
         const int w16 = (m + 15) >> 4;
+        const LaneTranspose tr(lane);
         // bit of the stream where the pair's base 0 sits (pad lanes read
-        // the group's first pair and keep nothing)
+        // the group's first pair and keep nothing): its 16-base windows are
+        // one funnel shift by o0 % 32 of stream words o0/32 + c, + c + 1
         const uint32_t o0 =
             (uint32_t)(2 * ((p < n ? p : g * 32) * m - cb * 16));
+        const uint32_t sh = o0 & 31u;
+        const uint32_t *src = code + (o0 >> 5);
         // lane r stores code bit r%2 of base 16c + r/2: word
         // ((4c + r/8) * G + g) * 8 + (r%2) * 4 + (r/2)%4
         uint32_t *dst = out + ((int64_t)(lane >> 3) * G + g) * 8 +
                         (lane & 1) * 4 + ((lane >> 1) & 3);
         const int64_t step = 32 * G;  // four blocks
+        uint32_t cur = src[0];
         for (int c = 0; c + 1 < w16; ++c) {
-            const uint32_t o = o0 + 32u * (uint32_t)c;
-            const uint32_t k = o >> 5;
-            uint32_t w = funnel_r(code[k], code[k + 1], o & 31u) & live;
-            w = warp_transpose32(w, lane);
-            dst[c * step] = w;
+            const uint32_t nxt = src[c + 1];
+            dst[c * step] = tr(funnel_r(cur, nxt, sh) & live);
+            cur = nxt;
         }
         // the last 16 bases: codes past the pair's end cleared, words of
         // blocks past the last one not stored
         const int c = w16 - 1;
-        const uint32_t o = o0 + 32u * (uint32_t)c;
-        const uint32_t k = o >> 5;
-        uint32_t w = funnel_r(code[k], code[k + 1], o & 31u) & live &
-                     mask_below(2 * (m - 16 * c));
-        w = warp_transpose32(w, lane);
+        const uint32_t w = tr(funnel_r(cur, src[c + 1], sh) & live &
+                              mask_below(2 * (m - 16 * c)));
         if (16 * c + (lane >> 1) < 4 * ((m + 3) >> 2))
             dst[c * step] = w;
     }
