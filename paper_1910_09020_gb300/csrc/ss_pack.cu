@@ -293,9 +293,12 @@ __global__ void __launch_bounds__(32 * kPackSlicedWarps)
 // each, with the codes past the pair's end cleared, and the warp transposes
 // them as above (lane r then holds code bit r%2 of base r/2).
 constexpr int kPackSpanMaxWords = 12 * 1024;  // 48 KB of code stream
+// 8 CTAs of 256 threads per SM (32 registers): the load phase of one CTA
+// overlaps the transpose phase of the others (measured 0.75 -> 0.69 ms per
+// 30M x 100 bp side against the compiler's 40 registers, 6 CTAs)
 constexpr int kPackSpanMaxM = (kPackSpanMaxWords - 3) / 2;
 
-__global__ void __launch_bounds__(32 * kPackSlicedWarps)
+__global__ void __launch_bounds__(32 * kPackSlicedWarps, 8)
     k_pack_sliced_span(const uint8_t *__restrict__ ascii, int64_t n,
                        int32_t m, int64_t G, int gpc,
                        uint32_t *__restrict__ out, int *status)
