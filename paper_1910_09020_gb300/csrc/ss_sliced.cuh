@@ -103,9 +103,11 @@ SS_HD uint32_t or_tree(const uint32_t (&x)[N])
 // saturating binary count: bit b of the count in c[b] (NB words) and the
 // pairs that reached E+1 in dn; per column one op for the increment
 // (restarted and not done), two per bit for the ripple and about NB/2 for
-// "reached E+1" -- fewer ops and registers than the thermometer once E+1
-// passes about 12.
-constexpr int kSlicedBinaryFromE = 11;
+// "reached E+1" -- fewer registers than the thermometer, and fewer ops once
+// E+1 passes about 12.  Measured at 30M x 100 bp: E = 7 0.364 ms with the
+// thermometer against 0.367 binary; E = 8/9/10 0.392/0.447/0.486 against
+// 0.384/0.432/0.463.
+constexpr int kSlicedBinaryFromE = 8;
 
 template <int E, bool BIN = (E >= kSlicedBinaryFromE)>
 struct SlicedCount;
@@ -310,12 +312,14 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
     uint32_t rl[4], rh[4];
     if (nb > 0)
         src.ref(0, rl, rh);
-    // from E = 25 the rows and the window fill the registers: the next
-    // block's words are prefetched to L1 instead of held, and loaded into
-    // the window after it slides (measured at 10M x 250 bp: E = 24 0.82 ms
+    // where the rows and the window fill the registers, the next block's
+    // words are prefetched to L1 instead of held, and loaded into the
+    // window after it slides: from E = 25 (10M x 250 bp: E = 24 0.82 ms
     // held against 0.87 prefetched, E = 25 1.00 held, with spills, against
-    // 0.86)
-    constexpr bool kHold = E < 25;
+    // 0.86), and at E = 10-11, where it brings the kernel to 128 registers
+    // (4 CTAs per SM; 30M x 100 bp E = 10 0.463 -> 0.457 ms; slower at
+    // E = 7 and 12-15)
+    constexpr bool kHold = E < 10 || (E > 11 && E < 25);
     for (int k = 0; k < nb; ++k) {
         uint32_t nql[4], nqh[4], nrl[4], nrh[4];
         if constexpr (kHold) {
