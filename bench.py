@@ -9,8 +9,10 @@ odd pairs are independent random sequences (the shape of the paper's
 
 One step = the whole hot path over the batch: pack the resident ASCII reads
 and references to 2 bits per base in the bit-sliced layout (SS_FMT_SLICED2,
-2 launches) and run one plain filter launch per threshold over it (6
-launches, 32 pairs per thread).  ``value`` counts pair decisions (pairs x
+2 launches) and filter it at every threshold, 32 pairs per thread: E = 0, 2
+and 4 in one shared pass over the pairs (their walks cost less than reading
+the pairs), E = 6, 8 and 10 one launch each (4 launches, as
+ss_filter_sweep makes them).  ``value`` counts pair decisions (pairs x
 thresholds) per second with the inputs resident in HBM; the inputs (6 GB
 ASCII + 1.5 GB packed) are far larger than L2, so no flush is needed.
 ``pair_major_form`` times the same step with the pair-major packed format
@@ -45,6 +47,19 @@ import numpy as np  # noqa: E402
 N_PAIRS = 30_000_000
 M = 100
 SWEEP = [0, 2, 4, 6, 8, 10]
+# the step's filter launches, as ss_filter_sweep makes them: the sweep's
+# thresholds up to 4 share one pass over the pairs (their walks cost less
+# than the pass), every other threshold has its own launch
+SHARED_MAX_E = 4
+
+
+def sweep_groups(sweep):
+    low = [e for e in sweep if e <= SHARED_MAX_E]
+    groups = [tuple(low)] if len(low) >= 2 else [(e,) for e in low]
+    return groups + [(e,) for e in sweep if e > SHARED_MAX_E]
+
+
+GROUPS = sweep_groups(SWEEP)
 SEED = 1910_09020 + 2
 WORKLOAD = ("short-read threshold sweep: 30M synthetic pairs x 100 bp "
             "(even pairs Poisson(3) edits, odd pairs random), "
@@ -204,9 +219,10 @@ KERNEL_SOURCES = {
                      "ss_rwc.cuh", "ss_rw_launch.cuh", "ss_rw_e0.cu",
                      "ss_rw_e1.cu", "ss_rw_e2.cu", "ss_rw_e3.cu"],
     "k_pack_fixed": ["ss_device.cuh", "ss_pack.cuh", "ss_pack.cu"],
-    "k_sliced": ["ss_device.cuh", "ss_sliced.cuh", "ss_sliced.cu"],
-    "k_pack_sliced_span": ["ss_device.cuh", "ss_pack.cuh", "ss_sliced.cuh",
-                           "ss_pack.cu"],
+    "k_sliced": ["ss_device.cuh", "ss_rw_config.h", "ss_sliced.cuh",
+                 "ss_sliced.cu"],
+    "k_pack_sliced_span": ["ss_device.cuh", "ss_rw_config.h", "ss_pack.cuh",
+                           "ss_sliced.cuh", "ss_pack.cu"],
 }
 
 
@@ -998,10 +1014,11 @@ def run_ours(args):
     obs = torch.empty((len(SWEEP), n), dtype=torch.int32, device=dev)
     # events on the stream the kernels are launched on (torch's current
     # stream, passed to the library), one set per timed step
-    nev = 2 + 2 * len(SWEEP)
+    nev = 2 + 2 * len(GROUPS)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)]
            for _ in range(args.steps)]
-    launch_ms = {"pack": [], **{E: [] for E in SWEEP}}
+    launch_ms = {"pack": [], **{grp: [] for grp in GROUPS}}
+    row = {E: t for t, E in enumerate(SWEEP)}
 
     def step(ev):
         if ev:
@@ -1010,11 +1027,20 @@ def run_ours(args):
         F.pack_sliced(dr, m=M, n=n, out=sr)
         if ev:
             ev[1].record()
-        for t, E in enumerate(SWEEP):
+        for t, grp in enumerate(GROUPS):
             if ev:
                 ev[2 + 2 * t].record()
-            F.filter(sq, sr, m=M, e=E, n=n, fmt=binding.SS_FMT_SLICED2,
-                     out_accept=acc[t], out_obstacles=obs[t])
+            if len(grp) > 1:
+                # the group's rows of acc/obs are consecutive
+                a0 = row[grp[0]]
+                F.filter_sweep(sq, sr, m=M, e=list(grp), n=n,
+                               out_accept=acc[a0:a0 + len(grp)],
+                               out_obstacles=obs[a0:a0 + len(grp)])
+            else:
+                F.filter(sq, sr, m=M, e=grp[0], n=n,
+                         fmt=binding.SS_FMT_SLICED2,
+                         out_accept=acc[row[grp[0]]],
+                         out_obstacles=obs[row[grp[0]]])
             if ev:
                 ev[3 + 2 * t].record()
 
@@ -1036,8 +1062,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     for ev in evs:
         launch_ms["pack"].append(ev[0].elapsed_time(ev[1]))
-        for t, E in enumerate(SWEEP):
-            launch_ms[E].append(ev[2 + 2 * t].elapsed_time(ev[3 + 2 * t]))
+        for t, grp in enumerate(GROUPS):
+            launch_ms[grp].append(ev[2 + 2 * t].elapsed_time(ev[3 + 2 * t]))
     barrier(world)
     clk = clocks.stop()
     elapsed_ms = start.elapsed_time(stop)
@@ -1130,28 +1156,40 @@ def run_ours(args):
     hbm = peaks["hbm_gbs"] * 1e9
     per_launch = []
     roof_total = meas_total = 0.0
-    for E in SWEEP:
-        ms = float(np.mean(launch_ms[E]))
-        t_hbm = n * FILTER_BYTES_PER_PAIR / hbm
-        d = {"E": E, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
-             "hbm_gbs": n * FILTER_BYTES_PER_PAIR / (ms * 1e-3) / 1e9,
+    for grp in GROUPS:
+        ms = float(np.mean(launch_ms[grp]))
+        # the pairs read once, each threshold's results written
+        gbytes = FILTER_BYTES_PER_PAIR + 5 * (len(grp) - 1)
+        t_hbm = n * gbytes / hbm
+        d = {"E": grp[0] if len(grp) == 1 else list(grp), "ms": ms,
+             "kernel": "k_sliced" if len(grp) == 1 else "k_sliced_set",
+             "pairs_per_s": n / (ms * 1e-3),
+             "hbm_gbs": n * gbytes / (ms * 1e-3) / 1e9,
+             "algorithmic_bytes_per_pair": gbytes,
              "t_hbm_ms": 1e3 * t_hbm}
         t_bound, bound = t_hbm, "hbm"
         if model:
-            t_alu = n * model[E]["alu_ops_per_pair"] / ipk["lop3"]
-            t_xu = n * model[E]["xu_ops_per_pair"] / ipk["bfind"]
+            alu = sum(model[E]["alu_ops_per_pair"] for E in grp)
+            xu = sum(model[E]["xu_ops_per_pair"] for E in grp)
+            t_alu = n * alu / ipk["lop3"]
+            t_xu = n * xu / ipk["bfind"]
             d.update({"t_alu_ms": 1e3 * t_alu, "t_xu_ms": 1e3 * t_xu,
-                      "model": model[E]["model"],
-                      "alu_ops_per_pair": model[E]["alu_ops_per_pair"],
-                      "alu_ops_row_words_per_pair":
-                          model[E]["alu_ops_row_words_per_pair"],
-                      "alu_ops_columns_per_pair":
-                          model[E]["alu_ops_columns_per_pair"],
-                      "alu_ops_sliced_per_pair":
-                          model[E].get("alu_ops_sliced_per_pair"),
-                      "columns_per_pair": model[E]["columns_per_pair"],
-                      "tops": n * model[E]["alu_ops_per_pair"] / (ms * 1e-3)
-                      / 1e12})
+                      "model": [model[E]["model"] for E in grp],
+                      "alu_ops_per_pair": alu,
+                      "alu_ops_row_words_per_pair": sum(
+                          model[E]["alu_ops_row_words_per_pair"]
+                          for E in grp),
+                      "alu_ops_columns_per_pair": sum(
+                          model[E]["alu_ops_columns_per_pair"] for E in grp),
+                      "alu_ops_sliced_per_pair": sum(
+                          model[E].get("alu_ops_sliced_per_pair", 0)
+                          for E in grp),
+                      "columns_per_pair": [model[E]["columns_per_pair"]
+                                           for E in grp],
+                      "tops": n * alu / (ms * 1e-3) / 1e12})
+            if len(grp) == 1:
+                d["model"] = d["model"][0]
+                d["columns_per_pair"] = d["columns_per_pair"][0]
             if max(t_alu, t_xu) > t_bound:
                 t_bound, bound = max(t_alu, t_xu), ("alu" if t_alu >= t_xu
                                                     else "xu")
@@ -1160,12 +1198,13 @@ def run_ours(args):
         roof_total += 1e3 * t_bound
         meas_total += ms
         per_launch.append(d)
-    filter_ms = sum(float(np.mean(launch_ms[E])) for E in SWEEP)
+    filter_ms = sum(float(np.mean(launch_ms[grp])) for grp in GROUPS)
     pack_ms = float(np.mean(launch_ms["pack"]))
     alu_share = sum(d["ms"] for d in per_launch if d["bound"] != "hbm")
     dom_bound = "alu" if alu_share > filter_ms / 2 else "hbm"
     if dom_bound == "hbm":
-        achieved = n * FILTER_BYTES_PER_PAIR * len(SWEEP) / (filter_ms * 1e-3) / 1e9
+        achieved = sum(n * d["algorithmic_bytes_per_pair"]
+                       for d in per_launch) / (filter_ms * 1e-3) / 1e9
         peak, unit = peaks["hbm_gbs"], "GB/s"
     else:
         ops = sum(n * model[E]["alu_ops_per_pair"] for E in SWEEP)
@@ -1173,12 +1212,16 @@ def run_ours(args):
         peak, unit = ipk["lop3"] / 1e12, "Tops/s"
     traffic = ncu_traffic("k_sliced")
     roofline = {
-        "kernel": "k_sliced (plain filter over the bit-sliced layout, one "
-                  "launch per E)",
+        "kernel": "k_sliced / k_sliced_set (plain filter over the "
+                  "bit-sliced layout: E = 0, 2, 4 in one shared pass, "
+                  "E = 6, 8, 10 one launch each)",
         "bound": dom_bound, "achieved": achieved, "peak": peak, "unit": unit,
         "frac": roof_total / meas_total,
-        "frac_note": "sum over the sweep of max(HBM, ALU, find-first) "
-                     "roofline time / measured time; the ALU term counts "
+        "frac_note": "sum over the step's filter launches of max(HBM, ALU, "
+                     "find-first) roofline time / measured time (a shared "
+                     "pass: the pairs read once, each threshold's results "
+                     "written, the ALU ops of all its thresholds); the ALU "
+                     "term counts "
                      "the cheapest of three formulations of the greedy for "
                      "each E (per_launch[].model): row words, columns one "
                      "pair per thread, bit-sliced columns (32 pairs per "
@@ -1232,7 +1275,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "config": config_dict(world, n),
         "clocks": clk, "e2e": e2e,
-        "gpu_launches": (2 + len(SWEEP)) * args.steps,
+        "gpu_launches": (2 + len(GROUPS)) * args.steps,
         "roofline": roofline, "cpu_baseline": cpu, "parity": parity,
         "breakdown": {"pack_ms": pack_ms, "filter_ms": filter_ms,
                       "pack_gbs": n * PACK_BYTES_PER_PAIR / (pack_ms * 1e-3)

@@ -163,6 +163,23 @@ int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
                     int32_t e, int64_t n, int flags, void *stream,
                     uint8_t *out_accept, int32_t *out_obstacles);
 
+/* A threshold sweep on the device: n fixed-stride pairs of uniform length m
+ * (device, format SS_FMT_ASCII, SS_FMT_PACKED2 or SS_FMT_SLICED2 -- the last
+ * 16-byte aligned) filtered at each of the n_e thresholds of the host array
+ * e_list.  Outputs are DEVICE arrays laid out [n_e][n]: out_accept[t * n +
+ * p], out_obstacles[t * n + p].  Over the sliced layout (ASCII input with
+ * every threshold up to SS_SLICED_MAX_E is packed to it, chunk by chunk in
+ * the context's workspace), the distinct thresholds from 0 to 4 share one
+ * pass over the pairs (their walks cost less than reading the pairs) and
+ * every other threshold gets its own launch; PACKED2 input is filtered one
+ * threshold at a time.  Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_OOM,
+ * SS_ERR_UNSUPPORTED (sliced input with a threshold above SS_SLICED_MAX_E)
+ * or SS_ERR_CUDA; device-side errors through ss_sync. */
+int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
+                    int format, int32_t m, const int32_t *e_list, int n_e,
+                    int64_t n, void *stream, uint8_t *out_accept,
+                    int32_t *out_obstacles);
+
 /* Fixed-stride pairs of uniform length m held in HOST memory, filtered at
  * each of the n_e thresholds of the host array e_list (a threshold sweep as
  * in Section 3.2 needs the pairs copied once).  The library streams chunks

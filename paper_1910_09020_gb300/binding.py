@@ -43,7 +43,7 @@ SLICED_MAX_E = 31
 EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
-    "ss_sliced_words", "ss_pack_sliced",
+    "ss_sliced_words", "ss_pack_sliced", "ss_filter_sweep",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
@@ -117,6 +117,8 @@ def load(build_if_needed: bool = True):
     lib.ss_sliced_words.argtypes = [I64, I64]
     lib.ss_sliced_words.restype = I64
     lib.ss_pack_sliced.argtypes = [P, P, I32, I64, P, P]
+    lib.ss_filter_sweep.argtypes = [P, P, P, ctypes.c_int, I32, P,
+                                    ctypes.c_int, I64, P, P, P]
     lib.ss_filter_batch.argtypes = [P, P, P, ctypes.c_int, P, P, I32, P, I32,
                                     I64, ctypes.c_int, P, P, P]
     lib.ss_filter_host.argtypes = [P, P, P, ctypes.c_int, I32, P,
@@ -195,6 +197,13 @@ def ss_sliced_words(m: int, n: int) -> int:
 def ss_pack_sliced(ctx, ascii, m, n, sliced, stream) -> int:
     return load().ss_pack_sliced(ctx, ascii or None, m, n, sliced or None,
                                  stream or None)
+
+
+def ss_filter_sweep(ctx, reads, refs, fmt, m, e_list, n_e, n, stream,
+                    out_accept, out_obstacles) -> int:
+    return load().ss_filter_sweep(ctx, reads or None, refs or None, fmt, m,
+                                  e_list or None, n_e, n, stream or None,
+                                  out_accept or None, out_obstacles or None)
 
 
 def ss_pack(ctx, ascii, offsets, lengths, m, n, packed, packed_offsets,
@@ -406,6 +415,35 @@ class Filter:
                              _dptr(out_accept, d, "out_accept", n),
                              _dptr(out_obstacles, d, "out_obstacles", 4 * n))
         _check(rc, "ss_filter_batch")
+        if sync:
+            self.sync(stream)
+        return out_accept, out_obstacles
+
+    def filter_sweep(self, reads, refs, *, m: int, e, n: int,
+                     fmt: int = SS_FMT_SLICED2, out_accept=None,
+                     out_obstacles=None, stream=None, sync: bool = False):
+        """Device pairs filtered at every threshold of the list e; outputs
+        (accept uint8, obstacles int32) of shape (len(e), n), device."""
+        import torch
+        es = [int(x) for x in e]
+        e_arr = (ctypes.c_int32 * len(es))(*es)
+        k = len(es)
+        dev = reads.device
+        if out_accept is None:
+            out_accept = torch.empty((k, n), dtype=torch.uint8, device=dev)
+        if out_obstacles is None:
+            out_obstacles = torch.empty((k, n), dtype=torch.int32,
+                                        device=dev)
+        d = self.device
+        seq = _seq_bytes(fmt, n, m)
+        rc = ss_filter_sweep(self.ctx, _dptr(reads, d, "reads", seq),
+                             _dptr(refs, d, "refs", seq), fmt, m,
+                             ctypes.addressof(e_arr), k, n,
+                             _stream_handle(stream),
+                             _dptr(out_accept, d, "out_accept", k * n),
+                             _dptr(out_obstacles, d, "out_obstacles",
+                                   4 * k * n))
+        _check(rc, "ss_filter_sweep")
         if sync:
             self.sync(stream)
         return out_accept, out_obstacles

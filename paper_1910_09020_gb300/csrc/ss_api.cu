@@ -492,6 +492,142 @@ static int filter_sliced(ss_ctx *ctx, const uint32_t *q, const uint32_t *r,
     return SS_OK;
 }
 
+extern "C++" {
+// A threshold sweep over SS_FMT_SLICED2 input (every e_list[t] in
+// 0..kSlicedMaxE, checked by the caller): the distinct thresholds up to
+// kSlicedSetMaxE share one pass over the pairs when there are two or more
+// of them (their walks cost less than the pass), every other threshold gets
+// its own launch.  acc(t), obs(t): where threshold t's results go.
+template <class Acc, class Obs>
+static int sweep_sliced(ss_ctx *ctx, const uint32_t *q, const uint32_t *r,
+                        int32_t m, const int32_t *e_list, int n_e, int64_t n,
+                        Acc acc, Obs obs, cudaStream_t st)
+{
+    constexpr int S = ssk::kSlicedSetMaxE + 1;
+    int first[S];
+    for (int e = 0; e < S; ++e)
+        first[e] = -1;
+    int shared = 0;
+    for (int t = 0; t < n_e; ++t) {
+        const int e = e_list[t];
+        if (e < S && first[e] < 0) {
+            first[e] = t;
+            ++shared;
+        }
+    }
+    if (shared >= 2) {
+        unsigned mask = 0;
+        uint8_t *pa[S];
+        int32_t *po[S];
+        int i = 0;
+        for (int e = 0; e < S; ++e)
+            if (first[e] >= 0) {
+                mask |= 1u << e;
+                pa[i] = acc(first[e]);
+                po[i] = obs(first[e]);
+                ++i;
+            }
+        SS_CUDA(ssk::launch_sliced_set(q, r, n, m, mask, pa, po, st));
+        ctx->counters.launches += 1;
+    }
+    for (int t = 0; t < n_e; ++t) {
+        const int e = e_list[t];
+        if (shared >= 2 && e < S && first[e] == t)
+            continue;  // in the shared pass
+        SS_TRY(filter_sliced(ctx, q, r, m, e, n, acc(t), obs(t), st));
+    }
+    return SS_OK;
+}
+}  // extern "C++"
+
+int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
+                    int format, int32_t m, const int32_t *e_list, int n_e,
+                    int64_t n, void *stream, uint8_t *out_accept,
+                    int32_t *out_obstacles)
+{
+    if (!ctx || n < 0 || m < 0 || n_e < 0 || (n_e > 0 && !e_list))
+        return SS_ERR_INVALID_ARG;
+    if (format != SS_FMT_ASCII && format != SS_FMT_PACKED2 &&
+        format != SS_FMT_SLICED2)
+        return SS_ERR_INVALID_ARG;
+    bool all_sliced = true;
+    for (int t = 0; t < n_e; ++t) {
+        if (e_list[t] < 0)
+            return SS_ERR_INVALID_ARG;
+        all_sliced &= e_list[t] <= ssk::kSlicedMaxE;
+    }
+    if (n == 0 || n_e == 0)
+        return SS_OK;
+    if (!reads || !refs || !out_accept || !out_obstacles)
+        return SS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok)
+        return SS_ERR_CUDA;
+    cudaStream_t st = pick_stream(stream);
+    if (m == 0) {
+        // nothing to route: every pair accepted with 0 obstacles
+        SS_CUDA(cudaMemsetAsync(out_accept, 1, (size_t)n * n_e, st));
+        SS_CUDA(cudaMemsetAsync(out_obstacles, 0, (size_t)n * n_e * 4, st));
+        ctx->counters.pairs += n * n_e;
+        return SS_OK;
+    }
+    auto acc_at = [&](int64_t p0) {
+        return [=](int t) { return out_accept + (size_t)t * n + p0; };
+    };
+    auto obs_at = [&](int64_t p0) {
+        return [=](int t) { return out_obstacles + (size_t)t * n + p0; };
+    };
+    if (format == SS_FMT_SLICED2) {
+        if ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15)
+            return SS_ERR_INVALID_ARG;
+        if (!all_sliced)
+            return SS_ERR_UNSUPPORTED;
+        ctx->counters.pairs += n * n_e;
+        return sweep_sliced(ctx, (const uint32_t *)reads,
+                            (const uint32_t *)refs, m, e_list, n_e, n,
+                            acc_at(0), obs_at(0), st);
+    }
+    if (format == SS_FMT_ASCII && all_sliced) {
+        // packed once per chunk (whole groups) to the sliced layout in the
+        // workspace, every threshold over it
+        const size_t seq = (size_t)((m + 3) / 4) + 1;
+        if (ctx->budget <= 2048)
+            return SS_ERR_OOM;
+        int64_t chunk = (int64_t)((ctx->budget - 2048) / (2 * seq));
+        if (chunk < n)
+            chunk &= ~(int64_t)31;
+        if (chunk < 1)
+            return SS_ERR_OOM;
+        chunk = std::min(chunk, n);
+        const size_t seq_bytes =
+            align_up((size_t)ss_sliced_words(m, chunk) * 4, 256);
+        SS_TRY(ensure_workspace(ctx, 2 * seq_bytes));
+        uint32_t *pq = (uint32_t *)ctx->ws;
+        uint32_t *pr = (uint32_t *)((char *)ctx->ws + seq_bytes);
+        for (int64_t p0 = 0; p0 < n; p0 += chunk) {
+            const int64_t cn = std::min(chunk, n - p0);
+            SS_CUDA(ssk::launch_pack_sliced(
+                (const uint8_t *)reads + p0 * (int64_t)m, cn, m, pq,
+                ctx->d_status, st));
+            SS_CUDA(ssk::launch_pack_sliced(
+                (const uint8_t *)refs + p0 * (int64_t)m, cn, m, pr,
+                ctx->d_status, st));
+            ctx->counters.launches += 2;
+            SS_TRY(sweep_sliced(ctx, pq, pr, m, e_list, n_e, cn, acc_at(p0),
+                                obs_at(p0), st));
+        }
+        ctx->counters.pairs += n * n_e;
+        return SS_OK;
+    }
+    // one fixed-stride filter per threshold
+    for (int t = 0; t < n_e; ++t)
+        SS_TRY(ss_filter_batch(ctx, reads, refs, format, nullptr, nullptr, m,
+                               nullptr, e_list[t], n, SS_MODE_AUTO, stream,
+                               out_accept + (size_t)t * n,
+                               out_obstacles + (size_t)t * n));
+    return SS_OK;
+}
+
 int ss_filter_batch(ss_ctx *ctx, const void *reads, const void *refs,
                     int format, const int64_t *offsets,
                     const int32_t *lengths, int32_t m, const int32_t *E,
@@ -695,12 +831,16 @@ int ss_filter_host(ss_ctx *ctx, const void *reads, const void *refs,
             fq = pq;
             fr = pr;
         }
+        if (sliced)
+            SS_TRY(sweep_sliced(
+                ctx, pq, pr, m, e_list, n_e, cn,
+                [=](int t) { return dacc + (size_t)t * acc_stride; },
+                [=](int t) { return dobs + (size_t)t * acc_stride; }, st));
         for (int t = 0; t < n_e; ++t) {
             uint8_t *ta = dacc + (size_t)t * acc_stride;
             int32_t *to = dobs + (size_t)t * acc_stride;
             if (sliced) {
-                SS_TRY(filter_sliced(ctx, pq, pr, m, e_list[t], cn, ta, to,
-                                     st));
+                // filtered above
             } else if (m == 0) {
                 SS_CUDA(cudaMemsetAsync(ta, 1, (size_t)cn, st));
                 SS_CUDA(cudaMemsetAsync(to, 0, (size_t)cn * 4, st));

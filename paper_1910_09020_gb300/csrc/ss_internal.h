@@ -31,6 +31,13 @@ cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
 cudaError_t launch_sliced(const uint32_t *reads, const uint32_t *refs,
                           int64_t n, int32_t m, int32_t E, uint8_t *acc,
                           int32_t *obs, cudaStream_t st);
+// Several thresholds 0..4 in one pass (bit e of mask: threshold e; two or
+// more bits): acc[i], obs[i] receive the i-th threshold of the mask in
+// ascending order.
+cudaError_t launch_sliced_set(const uint32_t *reads, const uint32_t *refs,
+                              int64_t n, int32_t m, unsigned mask,
+                              uint8_t *const *acc, int32_t *const *obs,
+                              cudaStream_t st);
 
 // K3a plain launch for 0 <= E <= kRwMaxE, m <= kRwMaxM.  status: device
 // word for latched errors.

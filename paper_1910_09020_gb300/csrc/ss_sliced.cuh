@@ -31,8 +31,11 @@
 // of a group does not depend on how similar its pairs are.
 #pragma once
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 
 #include "ss_device.cuh"
+#include "ss_rw_config.h"
 
 namespace ssk {
 
@@ -225,18 +228,21 @@ struct SlicedEdges {
 // EDGE, vw holds the block's validity words: a diagonal that reads a query
 // base outside 0..m-1 meets an obstacle (Eq. 1 case 4).  one holds 1 (a
 // run-time value: S_d * one + z is a multiply-add on the FMA pipe).
-template <int E, bool EDGE, int U>
+// The window may be wider than E needs (NW blocks either side, NW >= NBH):
+// word w is then query base j0 - 4 NW + w.
+template <int E, bool EDGE, int U, int NW = SlicedShape<E>::NBH>
 SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
                          SlicedCount<E> &cnt,
-                         const uint32_t (&ql)[SlicedShape<E>::WW],
-                         const uint32_t (&qh)[SlicedShape<E>::WW],
+                         const uint32_t (&ql)[4 * (2 * NW + 1)],
+                         const uint32_t (&qh)[4 * (2 * NW + 1)],
                          const uint32_t (&rl)[4], const uint32_t (&rh)[4],
                          const uint32_t *vw, uint32_t one)
 {
     using Sh = SlicedShape<E>;
+    static_assert(NW >= Sh::NBH, "window narrower than E needs");
 #pragma unroll
     for (int d = 0; d < Sh::ND; ++d) {
-        const int w = Sh::OFF + U + d;
+        const int w = 4 * NW - E + U + d;
         // (S_d | z) & ~(Q lo ^ R lo) & ~(Q hi ^ R hi)
         uint32_t s = S[d] * one + z;
         s = lop3<0x90>(s, ql[w], rl[U]);
@@ -398,3 +404,262 @@ SS_HD uint32_t transpose_level(uint32_t v, uint32_t x, int lane, int d)
 }
 
 }  // namespace ssk
+
+namespace ssk {
+
+// ---- several thresholds in one pass over the data ------------------------
+// Thresholds whose walks cost less than streaming the pairs (E <= 4 at
+// 100 bp) share one pass: one query window (sized for the largest E), one
+// set of reference words and one edge table, and per threshold its own
+// rows, restart word and count.  Each threshold's walk is exactly the
+// single-threshold walk above; only the loads are shared.
+
+
+// One threshold's state.
+template <int E>
+struct SlicedTrack {
+    uint32_t S[2 * E + 1];
+    uint32_t z;
+    SlicedCount<E> cnt;
+    SS_HD void init(uint32_t pad)
+    {
+#pragma unroll
+        for (int d = 0; d < 2 * E + 1; ++d)
+            S[d] = 0xffffffffu;
+        z = 0u;
+        cnt.init(pad);
+    }
+};
+
+template <int... Es>
+struct SlicedTracks;
+
+template <>
+struct SlicedTracks<> {
+    SS_HD void init(uint32_t) {}
+    SS_HD uint32_t done() const { return 0xffffffffu; }
+};
+
+template <int E, int... R>
+struct SlicedTracks<E, R...> {
+    SlicedTrack<E> head;
+    SlicedTracks<R...> tail;
+    SS_HD void init(uint32_t pad)
+    {
+        head.init(pad);
+        tail.init(pad);
+    }
+    // pairs past E for every threshold of the set
+    SS_HD uint32_t done() const { return head.cnt.done() & tail.done(); }
+};
+
+// Column U of a block for every threshold of the set (window of NW blocks
+// either side).
+template <int NW, bool EDGE, int U>
+SS_HD void set_column(SlicedTracks<> &, const uint32_t (&)[4 * (2 * NW + 1)],
+                      const uint32_t (&)[4 * (2 * NW + 1)],
+                      const uint32_t (&)[4], const uint32_t (&)[4],
+                      const uint32_t *, uint32_t)
+{
+}
+
+template <int NW, bool EDGE, int U, int E, int... R>
+SS_HD void set_column(SlicedTracks<E, R...> &t,
+                      const uint32_t (&ql)[4 * (2 * NW + 1)],
+                      const uint32_t (&qh)[4 * (2 * NW + 1)],
+                      const uint32_t (&rl)[4], const uint32_t (&rh)[4],
+                      const uint32_t *vw, uint32_t one)
+{
+    sliced_column<E, EDGE, U, NW>(t.head.S, t.head.z, t.head.cnt, ql, qh, rl,
+                                  rh, vw, one);
+    set_column<NW, EDGE, U>(t.tail, ql, qh, rl, rh, vw, one);
+}
+
+template <int NW, bool EDGE, int... Es>
+SS_HD void set_block(SlicedTracks<Es...> &t,
+                     const uint32_t (&ql)[4 * (2 * NW + 1)],
+                     const uint32_t (&qh)[4 * (2 * NW + 1)],
+                     const uint32_t (&rl)[4], const uint32_t (&rh)[4],
+                     const uint32_t *vw, int live, uint32_t one)
+{
+    set_column<NW, EDGE, 0>(t, ql, qh, rl, rh, vw, one);
+    if (live > 1)
+        set_column<NW, EDGE, 1>(t, ql, qh, rl, rh, vw, one);
+    if (live > 2)
+        set_column<NW, EDGE, 2>(t, ql, qh, rl, rh, vw, one);
+    if (live > 3)
+        set_column<NW, EDGE, 3>(t, ql, qh, rl, rh, vw, one);
+}
+
+// The walk of sliced_walk for every threshold of the ascending set Es
+// (largest EMAX) over one group; vtab: the validity table of
+// SlicedEdges<EMAX>(m).
+template <int EMAX, class Src, int... Es>
+SS_HD void sliced_walk_set(const Src &src, int m, uint32_t pad,
+                           SlicedTracks<Es...> &t, const uint32_t *vtab,
+                           uint32_t one)
+{
+    constexpr int NW = SlicedShape<EMAX>::NBH;
+    constexpr int WW = SlicedShape<EMAX>::WW;
+    const SlicedEdges<EMAX> ed(m);
+    const int nb = ed.nb;
+    uint32_t ql[WW], qh[WW];
+#pragma unroll
+    for (int b = 0; b < 2 * NW + 1; ++b) {
+        uint32_t lo[4], hi[4];
+        src.query(b - NW, nb, lo, hi);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            ql[4 * b + x] = lo[x];
+            qh[4 * b + x] = hi[x];
+        }
+    }
+    t.init(pad);
+    uint32_t rl[4], rh[4];
+    if (nb > 0)
+        src.ref(0, rl, rh);
+    for (int k = 0; k < nb; ++k) {
+        uint32_t nql[4], nqh[4], nrl[4], nrh[4];
+        src.query(k + NW + 1, nb, nql, nqh);
+        if (k + 1 < nb)
+            src.ref(k + 1, nrl, nrh);
+        const int live = imin(4, m - 4 * k);
+        if (k < ed.kl || k >= ed.kr)
+            set_block<NW, true>(t, ql, qh, rl, rh,
+                                vtab + ed.row_of(k) * WW, live, one);
+        else
+            set_block<NW, false>(t, ql, qh, rl, rh, nullptr, live, one);
+        if (t.done() == 0xffffffffu)
+            break;  // every pair past every threshold
+#pragma unroll
+        for (int w = 0; w + 4 < WW; ++w) {
+            ql[w] = ql[w + 4];
+            qh[w] = qh[w + 4];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            ql[WW - 4 + x] = nql[x];
+            qh[WW - 4 + x] = nqh[x];
+            rl[x] = nrl[x];
+            rh[x] = nrh[x];
+        }
+    }
+}
+
+// The thresholds of a bit mask (bit e: threshold e), ascending.
+template <unsigned MASK, int B, int... Es>
+struct MaskThresholds {
+    using type = typename std::conditional<
+        ((MASK >> B) & 1u) != 0u,
+        typename MaskThresholds<MASK, B + 1, Es..., B>::type,
+        typename MaskThresholds<MASK, B + 1, Es...>::type>::type;
+};
+template <unsigned MASK, int... Es>
+struct MaskThresholds<MASK, kSlicedSetMaxE + 1, Es...> {
+    using type = std::integer_sequence<int, Es...>;
+};
+
+}  // namespace ssk
+
+#ifdef __CUDACC__
+namespace ssk {
+
+// ---- device side: one group's words in global memory, results -----------
+
+constexpr int kSlicedThreads = 128;
+
+// Reads or refs in the layout: uint4 index (blk * G + g) * 2 + b.
+struct SlicedSrc {
+    const uint4 *q, *r;
+    int64_t G, g;
+    __device__ __forceinline__ void load(const uint4 *base, int blk,
+                                         uint32_t (&lo)[4],
+                                         uint32_t (&hi)[4]) const
+    {
+        const uint4 *p = base + ((int64_t)blk * G + g) * 2;
+        const uint4 a = __ldg(p), b = __ldg(p + 1);
+        lo[0] = a.x, lo[1] = a.y, lo[2] = a.z, lo[3] = a.w;
+        hi[0] = b.x, hi[1] = b.y, hi[2] = b.z, hi[3] = b.w;
+    }
+    __device__ __forceinline__ void query(int blk, int nb, uint32_t (&lo)[4],
+                                          uint32_t (&hi)[4]) const
+    {
+        if (blk < 0 || blk >= nb) {
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                lo[x] = hi[x] = 0u;
+            return;
+        }
+        load(q, blk, lo, hi);
+    }
+    __device__ __forceinline__ void ref(int blk, uint32_t (&lo)[4],
+                                        uint32_t (&hi)[4]) const
+    {
+        load(r, blk, lo, hi);
+    }
+    // both planes of a block are 32 contiguous bytes: one L1 line each
+    __device__ __forceinline__ void prefetch(int qblk, int rblk, int nb) const
+    {
+        if (qblk >= 0 && qblk < nb)
+            asm volatile("prefetch.global.L1 [%0];"
+                         :
+                         : "l"(q + ((int64_t)qblk * G + g) * 2));
+        if (rblk < nb)
+            asm volatile("prefetch.global.L1 [%0];"
+                         :
+                         : "l"(r + ((int64_t)rblk * G + g) * 2));
+    }
+};
+
+// Bytes 0..3 of the result: 1 for the pairs 4q..4q+3 of `ok` that are set.
+__device__ __forceinline__ uint32_t flag_bytes(uint32_t ok, int q)
+{
+    return (((ok >> (4 * q)) & 0xfu) * 0x00204081u) & 0x01010101u;
+}
+
+// The validity table of the edge blocks, the same for every thread of the
+// CTA (all threads call this, then synchronise).
+template <int E>
+__device__ __forceinline__ void sliced_fill_edges(uint32_t *vtab, int m)
+{
+    using Ed = SlicedEdges<E>;
+    constexpr int WW = SlicedShape<E>::WW;
+    const Ed ed(m);
+    for (int i = threadIdx.x; i < ed.rows() * WW; i += kSlicedThreads)
+        vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, m);
+}
+
+// Results of the group's np pairs starting at pair p0: accept (count <= E,
+// Section 2.4 step 5) and min(count, E+1); vec: acc and obs 16-byte
+// aligned, so a whole group is stored with 16-byte stores.
+template <int E>
+__device__ __forceinline__ void sliced_store(const SlicedCount<E> &cnt,
+                                             uint8_t *acc, int32_t *obs,
+                                             int64_t p0, int np, bool vec)
+{
+    uint32_t cb[SlicedShape<E>::NB];
+    cnt.bits(cb);
+    const uint32_t ok = ~cnt.done();
+    if (np == 32 && vec) {
+        uint4 *o = reinterpret_cast<uint4 *>(obs + p0);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+            o[v] = make_uint4((uint32_t)sliced_count<E>(cb, 4 * v),
+                              (uint32_t)sliced_count<E>(cb, 4 * v + 1),
+                              (uint32_t)sliced_count<E>(cb, 4 * v + 2),
+                              (uint32_t)sliced_count<E>(cb, 4 * v + 3));
+        uint4 *f = reinterpret_cast<uint4 *>(acc + p0);
+        f[0] = make_uint4(flag_bytes(ok, 0), flag_bytes(ok, 1),
+                          flag_bytes(ok, 2), flag_bytes(ok, 3));
+        f[1] = make_uint4(flag_bytes(ok, 4), flag_bytes(ok, 5),
+                          flag_bytes(ok, 6), flag_bytes(ok, 7));
+    } else {
+        for (int i = 0; i < np; ++i) {
+            obs[p0 + i] = sliced_count<E>(cb, i);
+            acc[p0 + i] = (uint8_t)((ok >> i) & 1u);
+        }
+    }
+}
+
+}  // namespace ssk
+#endif

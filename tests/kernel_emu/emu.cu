@@ -224,9 +224,64 @@ int sliced_dispatch(int E, const uint32_t *q, const uint32_t *r, int64_t n,
     return out;
 }
 
+template <int I>
+void store_set_host(const SlicedTracks<> &, int64_t, int, uint8_t **,
+                    int32_t **)
+{
+}
+
+template <int I, int E, int... R>
+void store_set_host(const SlicedTracks<E, R...> &t, int64_t p0, int np,
+                    uint8_t **acc, int32_t **obs)
+{
+    uint32_t cb[SlicedShape<E>::NB];
+    t.head.cnt.bits(cb);
+    for (int i = 0; i < np; ++i) {
+        obs[I][p0 + i] = sliced_count<E>(cb, i);
+        acc[I][p0 + i] = (uint8_t)(((~t.head.cnt.done()) >> i) & 1u);
+    }
+    store_set_host<I + 1>(t.tail, p0, np, acc, obs);
+}
+
+template <int EMAX, int... Es>
+void sliced_set_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
+                       uint8_t **acc, int32_t **obs)
+{
+    const int64_t G = (n + 31) / 32;
+    using Ed = SlicedEdges<EMAX>;
+    constexpr int WW = SlicedShape<EMAX>::WW;
+    const Ed ed(m);
+    std::vector<uint32_t> vtab(Ed::kRows * WW);
+    for (int i = 0; i < ed.rows() * WW; ++i)
+        vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, m);
+    for (int64_t g = 0; g < G; ++g) {
+        const int np = (int)std::min<int64_t>(32, n - 32 * g);
+        const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
+        SlicedTracks<Es...> t;
+        sliced_walk_set<EMAX>(HostSliced{q, r, G, g}, m, pad, t, vtab.data(),
+                              1u);
+        store_set_host<0>(t, 32 * g, np, acc, obs);
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+// Several thresholds in one pass over the sliced layout (the sweep's shared
+// pass) for the sets {0,2,4}, {0,1,2,3,4}, {1,3}, {3,4} (which = 0..3):
+// acc[i], obs[i] get the set's i-th threshold.
+int emu_sliced_set(const uint32_t *q, const uint32_t *r, int64_t n, int m,
+                   int which, uint8_t **acc, int32_t **obs)
+{
+    switch (which) {
+    case 0: sliced_set_groups<4, 0, 2, 4>(q, r, n, m, acc, obs); return 0;
+    case 1: sliced_set_groups<4, 0, 1, 2, 3, 4>(q, r, n, m, acc, obs); return 0;
+    case 2: sliced_set_groups<3, 1, 3>(q, r, n, m, acc, obs); return 0;
+    case 3: sliced_set_groups<4, 3, 4>(q, r, n, m, acc, obs); return 0;
+    default: return -100;
+    }
+}
 
 // The bit-sliced walk over every group of a sliced layout (n pairs of
 // length m): the plain sliced launch's results.  Returns -100 if E is not

@@ -179,3 +179,46 @@ def test_filter_batch_ascii_uses_sliced_chunks():
             oacc, oobs = oracle_fixed(reads, refs, E)
             assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
                         f"ascii E={E}")
+
+
+@pytest.mark.parametrize("es", [[0, 2, 4, 6, 8, 10], [4, 0, 3, 1, 2, 31],
+                                [2, 2, 0, 15], [3], [0, 4]])
+def test_filter_sweep_sliced(F, es):
+    """ss_filter_sweep over the sliced layout: the thresholds 0..4 of the
+    list share one pass (duplicates after the first get their own launch),
+    the others one launch each; every threshold against the oracle, n not a
+    multiple of 16 (results stored one by one) and one that is."""
+    for n in (10007, 4096):
+        m = 100
+        reads, refs = synth.pairs_fixed(340 + n, 0, n, m,
+                                        synth.rate_recipe(0.08))
+        q = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+        r = F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n)
+        acc, obs = F.filter_sweep(q, r, m=m, e=es, n=n, sync=True)
+        acc, obs = acc.cpu().numpy(), obs.cpu().numpy()
+        for t, E in enumerate(es):
+            oacc, oobs = oracle_fixed(reads, refs, E)
+            assert_same(acc[t], obs[t], oacc, oobs, f"sweep {es} E={E} n={n}")
+
+
+def test_filter_sweep_ascii_and_packed():
+    """ss_filter_sweep from resident ASCII (packed to the sliced layout chunk
+    by chunk in a small workspace) and from the pair-major packed format."""
+    n, m = 9001, 150
+    es = [0, 2, 4, 7, 20]
+    reads, refs = synth.pairs_fixed(350, 0, n, m, synth.rate_recipe(0.12))
+    dq, dr = to_dev(reads.reshape(-1)), to_dev(refs.reshape(-1))
+    want = [oracle_fixed(reads, refs, E) for E in es]
+    with binding.Filter(0, workspace_bytes=256 << 10) as F2:
+        acc, obs = F2.filter_sweep(dq, dr, m=m, e=es, n=n,
+                                   fmt=binding.SS_FMT_ASCII, sync=True)
+        for t, E in enumerate(es):
+            assert_same(acc[t].cpu().numpy(), obs[t].cpu().numpy(), *want[t],
+                        f"ascii sweep E={E}")
+        pq = F2.pack(dq, m=m, n=n)
+        pr = F2.pack(dr, m=m, n=n)
+        acc, obs = F2.filter_sweep(pq, pr, m=m, e=es, n=n,
+                                   fmt=binding.SS_FMT_PACKED2, sync=True)
+        for t, E in enumerate(es):
+            assert_same(acc[t].cpu().numpy(), obs[t].cpu().numpy(), *want[t],
+                        f"packed sweep E={E}")

@@ -379,3 +379,27 @@ def test_sliced_walk_matches_oracle(emu, m):
         oacc, oobs = oracle.filter_batch(reads, refs, m, E)
         bad = np.flatnonzero((acc != oacc) | (obs != oobs))
         assert bad.size == 0, (m, n, E, bad[:5], obs[bad[:5]], oobs[bad[:5]])
+
+
+SETS = {0: (0, 2, 4), 1: (0, 1, 2, 3, 4), 2: (1, 3), 3: (3, 4)}
+
+
+@pytest.mark.parametrize("m", [1, 3, 5, 9, 16, 33, 100, 150])
+def test_sliced_threshold_sets_match_oracle(emu, m):
+    """Several thresholds walked in one pass over the sliced layout (one
+    window for the largest, each its own rows and count): every threshold's
+    results equal the oracle's, groups ragged."""
+    rng = np.random.default_rng(2000 + m)
+    n = int(rng.choice([7, 32, 70]))
+    reads, refs = synth.pairs_fixed(7100 + m, 0, n, m, synth.rate_recipe(0.1))
+    q, r = oracle.pack_sliced(reads), oracle.pack_sliced(refs)
+    for which, Es in SETS.items():
+        accs = [np.zeros(n, np.uint8) for _ in Es]
+        obss = [np.zeros(n, np.int32) for _ in Es]
+        pa = (ctypes.c_void_p * len(Es))(*[a.ctypes.data for a in accs])
+        po = (ctypes.c_void_p * len(Es))(*[o.ctypes.data for o in obss])
+        assert emu.emu_sliced_set(P(q), P(r), n, m, which, pa, po) == 0
+        for i, E in enumerate(Es):
+            oacc, oobs = oracle.filter_batch(reads, refs, m, E)
+            assert (accs[i] == oacc).all() and (obss[i] == oobs).all(), \
+                (m, Es, E)
