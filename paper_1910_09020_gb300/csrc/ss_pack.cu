@@ -319,12 +319,22 @@ __global__ void __launch_bounds__(32 * kPackSlicedWarps, 8)
         ((uintptr_t)ascii & 15) == 0 && (cb + nc) * 16 <= limit;
     uint32_t err = 0;
     if (fast) {
+        // four loads of a thread in flight before any is packed (0.69 ->
+        // 0.66 ms per 30M x 100 bp side with the full-group branch below)
         const uint4 *src = reinterpret_cast<const uint4 *>(ascii) + cb;
-#pragma unroll 4
-        for (int c = threadIdx.x; c < nc; c += 32 * kPackSlicedWarps) {
-            const uint4 v = __ldg(src + c);
-            const uint32_t x[4] = {v.x, v.y, v.z, v.w};
-            code[c] = pack_chunk_pairs(x, err);
+        constexpr int T = 32 * kPackSlicedWarps;
+        for (int c0 = threadIdx.x; c0 < nc; c0 += 4 * T) {
+            uint4 v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (c0 + i * T < nc)
+                    v[i] = __ldg(src + c0 + i * T);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (c0 + i * T < nc) {
+                    const uint32_t x[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+                    code[c0 + i * T] = pack_chunk_pairs(x, err);
+                }
         }
     } else {
         for (int c = threadIdx.x; c < nc; c += 32 * kPackSlicedWarps) {
@@ -375,10 +385,18 @@ __global__ void __launch_bounds__(32 * kPackSlicedWarps, 8)
                         (lane & 1) * 4 + ((lane >> 1) & 3);
         const int64_t step = 32 * G;  // four blocks
         uint32_t cur = src[0];
-        for (int c = 0; c + 1 < w16; ++c) {
-            const uint32_t nxt = src[c + 1];
-            dst[c * step] = tr(funnel_r(cur, nxt, sh) & live);
-            cur = nxt;
+        if ((g + 1) * 32 <= n) {  // a full group: every lane a pair
+            for (int c = 0; c + 1 < w16; ++c) {
+                const uint32_t nxt = src[c + 1];
+                dst[c * step] = tr(funnel_r(cur, nxt, sh));
+                cur = nxt;
+            }
+        } else {
+            for (int c = 0; c + 1 < w16; ++c) {
+                const uint32_t nxt = src[c + 1];
+                dst[c * step] = tr(funnel_r(cur, nxt, sh) & live);
+                cur = nxt;
+            }
         }
         // the last 16 bases: codes past the pair's end cleared, words of
         // blocks past the last one not stored
