@@ -720,24 +720,33 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
             "per_E": rows, "results_identical": same}
 
 
-def run_submaze(F, pq, pr, n, acc, obs, t=8, y=3) -> dict:
+def run_submaze(F, sq, sr, pq, pr, n, acc, obs, t=8, y=3) -> dict:
     """Snake-on-Chip's sub-maze mode (t=8 columns, y=3 segments each, the
-    hardware design point of Section 2.5) on the headline pairs: per-E launch
+    hardware design point of Section 2.5) on the headline pairs, over the
+    bit-sliced layout (and, beside it, the pair-major one): per-E launch
     time and the decisions it adds over the exact filter just timed."""
     import torch
-    out = []
-    sacc = torch.empty(n, dtype=torch.uint8, device=pq.device)
-    sobs = torch.empty(n, dtype=torch.int32, device=pq.device)
-    for k, E in enumerate(SWEEP):
-        F.filter_submaze(pq, pr, m=M, e=E, t=t, y=y, n=n)  # warm
+
+    from paper_1910_09020_gb300 import binding
+
+    def timed(f):
+        f()  # warm
         a, b = _ev(), _ev()
         a.record()
         reps = 5
         for _ in range(reps):
-            sacc, sobs = F.filter_submaze(pq, pr, m=M, e=E, t=t, y=y, n=n)
+            r = f()
         b.record()
         torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / reps
+        return a.elapsed_time(b) / reps, r
+
+    out = []
+    for k, E in enumerate(SWEEP):
+        ms, (sacc, sobs) = timed(lambda: F.filter_submaze(
+            sq, sr, m=M, e=E, t=t, y=y, n=n, fmt=binding.SS_FMT_SLICED2))
+        pm_ms, (pacc, pobs) = timed(lambda: F.filter_submaze(
+            pq, pr, m=M, e=E, t=t, y=y, n=n))
+        same = bool(torch.equal(sacc, pacc) and torch.equal(sobs, pobs))
         extra = int((sacc.to(torch.int32) - acc[k].to(torch.int32)).clamp(min=0)
                     .sum().item())
         lost = int((acc[k].to(torch.int32) - sacc.to(torch.int32)).clamp(min=0)
@@ -747,11 +756,13 @@ def run_submaze(F, pq, pr, n, acc, obs, t=8, y=3) -> dict:
         out.append({"E": E, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
                     "hbm_gbs": gbs,
                     "hbm_frac": gbs / measured_peaks()["hbm_gbs"],
+                    "pair_major_ms": pm_ms, "forms_identical": same,
                     "accepts": int(sacc.sum(dtype=torch.int64).item()),
                     "exact_accepts": int(acc[k].sum(dtype=torch.int64).item()),
                     "added_accepts": extra, "lost_accepts": lost,
                     "count_above_exact": above})
-    return {"t": t, "y": y, "pairs": n, "per_E": out}
+    return {"t": t, "y": y, "pairs": n, "form": "bit-sliced (k_sliced_sub)",
+            "per_E": out}
 
 
 def run_unequal(F, n=2_000_000) -> dict:
@@ -1120,7 +1131,6 @@ def run_ours(args):
 
     # the same step in the pair-major packed format (one pair per thread),
     # beside the headline; its results must equal the sliced form's
-    del sq, sr
     W16 = binding.ss_packed_words(M)
     pq = torch.empty(n * W16, dtype=torch.int32, device=dev)
     pr = torch.empty(n * W16, dtype=torch.int32, device=dev)
@@ -1253,11 +1263,12 @@ def run_ours(args):
 
     extras = {}
     if not args.headline_only and world == 1:
-        extras["submaze_t8_y3"] = run_submaze(F, pq, pr, n, acc, obs)
+        extras["submaze_t8_y3"] = run_submaze(F, sq, sr, pq, pr, n, acc,
+                                              obs)
         extras["unequal_lengths"] = run_unequal(F)
         k4 = SWEEP.index(4)
         extras["compaction"] = run_compaction(F, pq, pr, acc[k4], n, 4)
-        del dq, dr, pq, pr
+        del dq, dr, pq, pr, sq, sr
         torch.cuda.empty_cache()
         extras["persistent_uneven_batch"] = run_batched(
             F, ipk, peaks["hbm_gbs"], not args.no_cpu,

@@ -307,8 +307,9 @@ int ss_filter_unequal(ss_ctx *ctx, const void *reads, const int64_t *read_off,
  * counts are summed and capped at e+1.  accept = (sum <= e).  The paper
  * notes that this can only underestimate the exact count (more false
  * accepts, never a false reject); t >= m with y > e gives the exact filter.
- * Fixed-stride SS_FMT_PACKED2 pairs of length m; min(e, m-1) <= 31 (else
- * SS_ERR_UNSUPPORTED); t, y >= 1.  For m <= 256 the pairs are staged by
+ * Fixed-stride SS_FMT_PACKED2 pairs of length m with min(e, m-1) <= 31, or
+ * SS_FMT_SLICED2 pairs (16-byte aligned) with e <= SS_SLICED_MAX_E, walked
+ * 32 pairs per thread (else SS_ERR_UNSUPPORTED); t, y >= 1.  For m <= 256 the pairs are staged by
  * bulk copies whose bounded waits, should one give up, latch SS_ERR_TIMEOUT
  * for the next ss_sync.  Asynchronous on `stream`.  Returns SS_OK,
  * SS_ERR_INVALID_ARG, SS_ERR_UNSUPPORTED or SS_ERR_CUDA. */

@@ -523,18 +523,18 @@ class Filter:
         return out
 
     def filter_submaze(self, reads, refs, *, m: int, e: int, t: int, y: int,
-                       n=None, stream=None):
+                       n=None, fmt: int = SS_FMT_PACKED2, stream=None):
         """Sub-maze approximate mode (Section 2.5) on fixed-stride packed
-        pairs; returns (accept, obstacles)."""
+        (pair-major or bit-sliced) pairs; returns (accept, obstacles)."""
         import torch
         n = reads.shape[0] if n is None else n
         acc = torch.empty(max(n, 1), dtype=torch.uint8, device=reads.device)
         obs = torch.empty(max(n, 1), dtype=torch.int32, device=reads.device)
         d = self.device
-        seq = _seq_bytes(SS_FMT_PACKED2, n, m)
+        seq = _seq_bytes(fmt, n, m)
         rc = load().ss_filter_submaze(self.ctx, _dptr(reads, d, "reads", seq),
                                       _dptr(refs, d, "refs", seq),
-                                      SS_FMT_PACKED2, m, e, t, y, n,
+                                      fmt, m, e, t, y, n,
                                       _stream_handle(stream) or None,
                                       _ptr(acc), _ptr(obs))
         _check(rc, "ss_filter_submaze")

@@ -1005,9 +1005,10 @@ int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
 {
     if (!ctx || n < 0 || m < 0 || e < 0 || t < 1 || y < 1)
         return SS_ERR_INVALID_ARG;
-    if (format != SS_FMT_PACKED2)
+    if (format != SS_FMT_PACKED2 && format != SS_FMT_SLICED2)
         return SS_ERR_INVALID_ARG;
-    if (ssk::eff_threshold(m, e) > 31)
+    if (format == SS_FMT_SLICED2 ? e > ssk::kSlicedMaxE
+                                 : ssk::eff_threshold(m, e) > 31)
         return SS_ERR_UNSUPPORTED;
     if (n == 0)
         return SS_OK;
@@ -1018,6 +1019,16 @@ int ss_filter_submaze(ss_ctx *ctx, const void *reads, const void *refs,
     if (m == 0) {
         SS_CUDA(cudaMemsetAsync(out_accept, 1, (size_t)n, st));
         SS_CUDA(cudaMemsetAsync(out_obstacles, 0, (size_t)n * 4, st));
+        return SS_OK;
+    }
+    if (format == SS_FMT_SLICED2) {
+        if ((((uintptr_t)reads) | ((uintptr_t)refs)) & 15)
+            return SS_ERR_INVALID_ARG;
+        SS_CUDA(ssk::launch_sliced_submaze((const uint32_t *)reads,
+                                           (const uint32_t *)refs, n, m, e,
+                                           t, y, out_accept, out_obstacles,
+                                           st));
+        ctx->counters.launches += 1;
         return SS_OK;
     }
     SS_CUDA(ssk::launch_submaze((const uint32_t *)reads,

@@ -31,6 +31,12 @@ cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
 cudaError_t launch_sliced(const uint32_t *reads, const uint32_t *refs,
                           int64_t n, int32_t m, int32_t E, uint8_t *acc,
                           int32_t *obs, cudaStream_t st);
+// The sub-maze mode (sub-mazes of t columns, at most y segments each) over
+// the bit-sliced layout, 0 <= E <= kSlicedMaxE.
+cudaError_t launch_sliced_submaze(const uint32_t *reads, const uint32_t *refs,
+                                  int64_t n, int32_t m, int32_t E, int32_t t,
+                                  int32_t y, uint8_t *acc, int32_t *obs,
+                                  cudaStream_t st);
 // Several thresholds 0..4 in one pass (bit e of mask: threshold e; two or
 // more bits): acc[i], obs[i] receive the i-th threshold of the mask in
 // ascending order.

@@ -228,18 +228,92 @@ struct SlicedEdges {
 // EDGE, vw holds the block's validity words: a diagonal that reads a query
 // base outside 0..m-1 meets an obstacle (Eq. 1 case 4).  one holds 1 (a
 // run-time value: S_d * one + z is a multiply-add on the FMA pipe).
+// What a column adds to the greedy, by mode.  The plain walk: nothing.
+struct SlicedPlain {
+    template <int N>
+    SS_HD void column_start(int, uint32_t (&)[N], uint32_t &)
+    {
+    }
+    SS_HD uint32_t counted(uint32_t nz) const { return nz; }
+    SS_HD void after(uint32_t) {}
+};
+
+// The sub-maze mode (Section 2.5): the maze cut into sub-mazes of t columns,
+// each routed from its own first column (every row restarts there), with at
+// most y escape segments counted per sub-maze (y taken as min(y, E+1): the
+// count stops at E+1 anyway).  Per pair a binary count of the sub-maze's
+// segments (NB words) and the pairs that reached y (frozen: their deaths
+// are no longer counted in this sub-maze).
+template <int E>
+struct SlicedSubMaze {
+    static constexpr int NB = SlicedShape<E>::NB;
+    uint32_t sb[NB];
+    uint32_t ym[NB];  // bit b of y, all ones or zero
+    uint32_t frozen;
+    int t, next;
+    SS_HD SlicedSubMaze(int t_, int y)
+    {
+        t = t_;
+        next = 0;
+        const int ye = y < E + 1 ? y : E + 1;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            sb[b] = 0u;
+            ym[b] = ((ye >> b) & 1) ? 0xffffffffu : 0u;
+        }
+        frozen = 0u;
+    }
+    // column j: a sub-maze's first column restarts every row of every pair
+    // (S | z all ones; S cleared so that S | z stays S + z)
+    template <int N>
+    SS_HD void column_start(int j, uint32_t (&S)[N], uint32_t &z)
+    {
+        if (j == next) {
+#pragma unroll
+            for (int d = 0; d < N; ++d)
+                S[d] = 0u;
+            z = 0xffffffffu;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                sb[b] = 0u;
+            frozen = 0u;
+            next += t;
+        }
+    }
+    // frozen pairs count as alive (no obstacle counted)
+    SS_HD uint32_t counted(uint32_t nz) const { return nz | frozen; }
+    SS_HD void after(uint32_t nz)
+    {
+        uint32_t k = lop3<0x03>(nz, frozen, 0u);  // a counted death
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const uint32_t x = sb[b];
+            sb[b] = x ^ k;
+            k &= x;
+        }
+        uint32_t eq = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            eq = lop3<0x90>(eq, sb[b], ym[b]);  // eq & ~(sb ^ ym)
+        frozen = eq;
+    }
+};
+
 // The window may be wider than E needs (NW blocks either side, NW >= NBH):
 // word w is then query base j0 - 4 NW + w.
-template <int E, bool EDGE, int U, int NW = SlicedShape<E>::NBH>
+template <int E, bool EDGE, int U, int NW = SlicedShape<E>::NBH,
+          class Mode = SlicedPlain>
 SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
                          SlicedCount<E> &cnt,
                          const uint32_t (&ql)[4 * (2 * NW + 1)],
                          const uint32_t (&qh)[4 * (2 * NW + 1)],
                          const uint32_t (&rl)[4], const uint32_t (&rh)[4],
-                         const uint32_t *vw, uint32_t one)
+                         const uint32_t *vw, uint32_t one, Mode &mode,
+                         int j0)
 {
     using Sh = SlicedShape<E>;
     static_assert(NW >= Sh::NBH, "window narrower than E needs");
+    mode.column_start(j0 + U, S, z);
 #pragma unroll
     for (int d = 0; d < Sh::ND; ++d) {
         const int w = 4 * NW - E + U + d;
@@ -254,31 +328,41 @@ SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
     // the pairs with every row dead: count this column's obstacle,
     // restart at the next column
     const uint32_t nz = or_tree<Sh::ND>(S);
-    cnt.step(nz);
+    cnt.step(mode.counted(nz));
+    mode.after(nz);
     z = ~nz;
 }
 
 // The block's columns j0 + u for u < live (1..4; below 4 only in the last
 // block).
-template <int E, bool EDGE>
+template <int E, bool EDGE, class Mode>
 SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
                         SlicedCount<E> &cnt,
                         const uint32_t (&ql)[SlicedShape<E>::WW],
                         const uint32_t (&qh)[SlicedShape<E>::WW],
                         const uint32_t (&rl)[4], const uint32_t (&rh)[4],
-                        const uint32_t *vw, int live, uint32_t one)
+                        const uint32_t *vw, int live, uint32_t one,
+                        Mode &mode, int j0)
 {
+    constexpr int NW = SlicedShape<E>::NBH;
     if (live >= 4) {
-        sliced_column<E, EDGE, 0>(S, z, cnt, ql, qh, rl, rh, vw, one);
-        sliced_column<E, EDGE, 1>(S, z, cnt, ql, qh, rl, rh, vw, one);
-        sliced_column<E, EDGE, 2>(S, z, cnt, ql, qh, rl, rh, vw, one);
-        sliced_column<E, EDGE, 3>(S, z, cnt, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 0, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                      mode, j0);
+        sliced_column<E, EDGE, 1, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                      mode, j0);
+        sliced_column<E, EDGE, 2, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                      mode, j0);
+        sliced_column<E, EDGE, 3, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                      mode, j0);
     } else {
-        sliced_column<E, EDGE, 0>(S, z, cnt, ql, qh, rl, rh, vw, one);
+        sliced_column<E, EDGE, 0, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                      mode, j0);
         if (live > 1)
-            sliced_column<E, EDGE, 1>(S, z, cnt, ql, qh, rl, rh, vw, one);
+            sliced_column<E, EDGE, 1, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                          mode, j0);
         if (live > 2)
-            sliced_column<E, EDGE, 2>(S, z, cnt, ql, qh, rl, rh, vw, one);
+            sliced_column<E, EDGE, 2, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
+                                          mode, j0);
     }
 }
 
@@ -290,10 +374,10 @@ SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
 // src.prefetch(qblk, rblk, nb) asks for those of query block qblk and
 // reference block rblk ahead of their loads (a hint, no result); vtab:
 // the validity table of SlicedEdges<E>(m), WW words per row.
-template <int E, class Src>
+template <int E, class Src, class Mode = SlicedPlain>
 SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
                        SlicedCount<E> &cnt, const uint32_t *vtab,
-                       uint32_t one)
+                       uint32_t one, Mode mode = Mode())
 {
     using Sh = SlicedShape<E>;
     const SlicedEdges<E> ed(m);
@@ -339,10 +423,11 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
         const int live = imin(4, m - 4 * k);
         if (k < ed.kl || k >= ed.kr)
             sliced_block<E, true>(S, z, cnt, ql, qh, rl, rh,
-                                  vtab + ed.row_of(k) * Sh::WW, live, one);
+                                  vtab + ed.row_of(k) * Sh::WW, live, one,
+                                  mode, 4 * k);
         else
             sliced_block<E, false>(S, z, cnt, ql, qh, rl, rh, nullptr, live,
-                                   one);
+                                   one, mode, 4 * k);
         if (cnt.done() == 0xffffffffu)
             break;  // every pair of the group is past E
 #pragma unroll
@@ -470,8 +555,9 @@ SS_HD void set_column(SlicedTracks<E, R...> &t,
                       const uint32_t (&rl)[4], const uint32_t (&rh)[4],
                       const uint32_t *vw, uint32_t one)
 {
+    SlicedPlain plain;
     sliced_column<E, EDGE, U, NW>(t.head.S, t.head.z, t.head.cnt, ql, qh, rl,
-                                  rh, vw, one);
+                                  rh, vw, one, plain, 0);
     set_column<NW, EDGE, U>(t.tail, ql, qh, rl, rh, vw, one);
 }
 

@@ -67,6 +67,9 @@ def load():
     lib.emu_sliced.argtypes = [P, P, ctypes.c_int64, ctypes.c_int,
                                ctypes.c_int, P, P]
     lib.emu_transpose32.argtypes = [P, P]
+    lib.emu_sliced_submaze.argtypes = [P, P, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, P, P]
     lib.emu_sliced_set.argtypes = [P, P, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_int, P, P]
     _lib = lib

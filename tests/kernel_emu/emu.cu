@@ -214,6 +214,44 @@ void sliced_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
     }
 }
 
+template <int E>
+void sliced_sub_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
+                       int t, int y, uint8_t *acc, int32_t *obs)
+{
+    const int64_t G = (n + 31) / 32;
+    using Ed = SlicedEdges<E>;
+    constexpr int WW = SlicedShape<E>::WW;
+    const Ed ed(m);
+    std::vector<uint32_t> vtab(Ed::kRows * WW);
+    for (int i = 0; i < ed.rows() * WW; ++i)
+        vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, m);
+    for (int64_t g = 0; g < G; ++g) {
+        const int np = (int)std::min<int64_t>(32, n - 32 * g);
+        const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
+        SlicedCount<E> cnt;
+        sliced_walk<E>(HostSliced{q, r, G, g}, m, pad, cnt, vtab.data(), 1u,
+                       SlicedSubMaze<E>(t, y));
+        uint32_t cb[SlicedShape<E>::NB];
+        cnt.bits(cb);
+        for (int i = 0; i < np; ++i) {
+            obs[32 * g + i] = sliced_count<E>(cb, i);
+            acc[32 * g + i] = (uint8_t)(((~cnt.done()) >> i) & 1u);
+        }
+    }
+}
+
+template <int... Es>
+int sliced_sub_dispatch(int E, const uint32_t *q, const uint32_t *r,
+                        int64_t n, int m, int t, int y, uint8_t *acc,
+                        int32_t *obs, std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    ((E == Es ? (sliced_sub_groups<Es>(q, r, n, m, t, y, acc, obs), out = 0)
+              : 0),
+     ...);
+    return out;
+}
+
 template <int... Es>
 int sliced_dispatch(int E, const uint32_t *q, const uint32_t *r, int64_t n,
                     int m, uint8_t *acc, int32_t *obs,
@@ -291,6 +329,15 @@ int emu_sliced(const uint32_t *q, const uint32_t *r, int64_t n, int m, int E,
 {
     return sliced_dispatch(E, q, r, n, m, acc, obs,
                            std::make_integer_sequence<int, 32>{});
+}
+
+// The sub-maze mode over the sliced layout (sub-mazes of t columns, at most
+// y segments each), every group.  Returns -100 if E is not built.
+int emu_sliced_submaze(const uint32_t *q, const uint32_t *r, int64_t n, int m,
+                       int E, int t, int y, uint8_t *acc, int32_t *obs)
+{
+    return sliced_sub_dispatch(E, q, r, n, m, t, y, acc, obs,
+                               std::make_integer_sequence<int, 16>{});
 }
 
 // The warp transpose of the sliced packer, the 32 lanes simulated in turn:

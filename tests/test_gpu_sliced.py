@@ -222,3 +222,31 @@ def test_filter_sweep_ascii_and_packed():
         for t, E in enumerate(es):
             assert_same(acc[t].cpu().numpy(), obs[t].cpu().numpy(), *want[t],
                         f"packed sweep E={E}")
+
+
+@pytest.mark.parametrize("m", [5, 8, 33, 100, 150])
+def test_sliced_submaze_matches_oracle(F, m):
+    """The sub-maze mode over the sliced layout against the oracle's
+    sso_filter_submaze, several (t, y), and equal to the pair-major form."""
+    n = 3001
+    reads, refs = synth.pairs_fixed(360 + m, 0, n, m, synth.rate_recipe(0.12))
+    q = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+    r = F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n)
+    pq = F.pack(to_dev(reads.reshape(-1)), m=m, n=n)
+    pr = F.pack(to_dev(refs.reshape(-1)), m=m, n=n)
+    for E, t, y in ((0, 8, 3), (4, 8, 3), (10, 8, 3), (6, 5, 1), (15, 16, 2),
+                    (31, 7, 9), (3, 1000, 50)):
+        acc, obs = F.filter_submaze(q, r, m=m, e=E, t=t, y=y, n=n,
+                                    fmt=SLICED)
+        F.sync()
+        acc, obs = acc.cpu().numpy(), obs.cpu().numpy()
+        for p in range(0, n, 7):
+            want = oracle.filter_submaze(reads[p].tobytes(), refs[p].tobytes(),
+                                         E, t, y)
+            assert (bool(acc[p]), int(obs[p])) == \
+                (want.accept, want.obstacles), (m, E, t, y, p)
+        if min(E, m - 1) <= 31:
+            pacc, pobs = F.filter_submaze(pq, pr, m=m, e=E, t=t, y=y, n=n)
+            F.sync()
+            assert (pacc.cpu().numpy() == acc).all()
+            assert (pobs.cpu().numpy() == obs).all()

@@ -403,3 +403,26 @@ def test_sliced_threshold_sets_match_oracle(emu, m):
             oacc, oobs = oracle.filter_batch(reads, refs, m, E)
             assert (accs[i] == oacc).all() and (obss[i] == oobs).all(), \
                 (m, Es, E)
+
+
+@pytest.mark.parametrize("m", [1, 5, 8, 9, 17, 64, 100, 150])
+def test_sliced_submaze_matches_oracle(emu, m):
+    """The sub-maze mode on the sliced walk (every row restarting at each
+    sub-maze's first column, at most y counted segments per sub-maze): the
+    oracle's sso_filter_submaze at widths within, at and around the
+    4-column blocks, y from 1 to beyond E+1, E up to 15."""
+    rng = np.random.default_rng(3000 + m)
+    n = int(rng.choice([9, 33, 64]))
+    reads, refs = synth.pairs_fixed(7200 + m, 0, n, m, synth.rate_recipe(0.15))
+    q, r = oracle.pack_sliced(reads), oracle.pack_sliced(refs)
+    for E in (0, 1, 3, 6, 10, 15):
+        for t, y in ((1, 1), (3, 2), (4, 1), (8, 3), (13, 2), (1000, 99)):
+            acc = np.zeros(n, np.uint8)
+            obs = np.zeros(n, np.int32)
+            assert emu.emu_sliced_submaze(P(q), P(r), n, m, E, t, y, P(acc),
+                                          P(obs)) == 0
+            for p in range(n):
+                want = oracle.filter_submaze(reads[p].tobytes(),
+                                             refs[p].tobytes(), E, t, y)
+                assert (bool(acc[p]), int(obs[p])) == \
+                    (want.accept, want.obstacles), (m, E, t, y, p)
