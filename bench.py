@@ -616,36 +616,47 @@ def run_batched(F, ipk, hbm_gbs, want_cpu: bool,
 
 
 def _fixed_model(reads, refs, m, E):
-    """Op model (the cheaper formulation, see K_COL) of fixed-length pairs:
+    """Op model (the cheapest formulation, see K_COL; the pairs share one
+    length, so the bit-sliced one is a candidate) of fixed-length pairs:
     per-pair ALU and find-first ops from the oracle's counters."""
     import oracle
+    n = len(reads)
     _, _, (_, w, it, col) = oracle.filter_batch(reads, refs, m, E,
                                                 with_stats=True)
-    alu, xu, _ = model_ops(E, w, it, col)
-    return alu / len(reads), xu / len(reads)
+    alu, xu, _ = model_ops(E, w, it, col, sliced_ops(E, m, n))
+    return alu / n, xu / n
 
 
 def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
     """10M pairs of 250 bp and 10M of 150 bp, edit rate U[0, 0.12], E = 0 %
-    .. 10 % of length: two plain launches against one persistent graph,
-    each with its roofline fraction (HBM bytes of the form; ALU ops of the
-    op model from the oracle's counters on `sample` pairs of each length)."""
+    .. 10 % of length: two plain launches (pair-major packed input, as the
+    persistent graph reads) against one persistent graph, and the two
+    plain launches over the bit-sliced layout, each with its roofline
+    fraction (HBM bytes of the form; ALU ops of the cheapest op model, the
+    bit-sliced one included, from the oracle's counters on `sample` pairs
+    of each length)."""
     import torch
 
     from paper_1910_09020_gb300 import synth
     n3 = 10_000_000
     seed = 1910_09020 + 3
     rec = synth.rate_recipe(0.12)
+    from paper_1910_09020_gb300 import binding
     samples = {}
     bufs = []
+    sbufs = []  # the same pairs in the bit-sliced layout
     for m, first in ((250, 0), (150, n3)):
         r, f = synth.pairs_fixed(seed, first, n3, m, rec)
         samples[m] = (r[:sample].copy(), f[:sample].copy())
-        q = F.pack(torch.from_numpy(r.reshape(-1)).cuda(), m=m, n=n3)
-        g = F.pack(torch.from_numpy(f.reshape(-1)).cuda(), m=m, n=n3)
+        dr_, df_ = (torch.from_numpy(r.reshape(-1)).cuda(),
+                    torch.from_numpy(f.reshape(-1)).cuda())
+        q = F.pack(dr_, m=m, n=n3)
+        g = F.pack(df_, m=m, n=n3)
+        sbufs.append((F.pack_sliced(dr_, m=m, n=n3),
+                      F.pack_sliced(df_, m=m, n=n3)))
         F.sync()
         bufs.append((q, g))
-        del r, f
+        del r, f, dr_, df_
     w250, w150 = 16, 10
     allq = torch.cat([bufs[0][0], bufs[1][0]])
     allr = torch.cat([bufs[0][1], bufs[1][1]])
@@ -657,6 +668,7 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
     a = torch.empty(2 * n3, dtype=torch.uint8, device="cuda")
     o = torch.empty(2 * n3, dtype=torch.int32, device="cuda")
     a2, o2 = torch.empty_like(a), torch.empty_like(o)
+    a3, o3 = torch.empty_like(a), torch.empty_like(o)
     rows = []
     same = True
     for pct in range(0, 11):
@@ -671,9 +683,19 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
                      out_accept=a[n3:], out_obstacles=o[n3:])
         persistent = lambda: F.filter(allq, allr, offsets=offs, lengths=lens,
                                       E=Es, out_accept=a2, out_obstacles=o2)
+
+        def plain_sliced():
+            F.filter(sbufs[0][0], sbufs[0][1], m=250, e=e250, n=n3,
+                     fmt=binding.SS_FMT_SLICED2, out_accept=a3[:n3],
+                     out_obstacles=o3[:n3])
+            F.filter(sbufs[1][0], sbufs[1][1], m=150, e=e150, n=n3,
+                     fmt=binding.SS_FMT_SLICED2, out_accept=a3[n3:],
+                     out_obstacles=o3[n3:])
         tp = _time_ms(plain, 5, F.sync)
         tb = _time_ms(persistent, 5, F.sync)
-        same &= bool(torch.equal(a, a2) and torch.equal(o, o2))
+        ts = _time_ms(plain_sliced, 5, F.sync)
+        same &= bool(torch.equal(a, a2) and torch.equal(o, o2) and
+                     torch.equal(a, a3) and torch.equal(o, o3))
         # accuracy of these decisions against the banded edit distance
         conf = [0, 0, 0, 0]
         for (q, g), (m, e), sl in (((bufs[0]), (250, e250), slice(0, n3)),
@@ -687,6 +709,8 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
                "plain_pairs_per_s": 2 * n3 / (tp * 1e-3),
                "persistent_pairs_per_s": 2 * n3 / (tb * 1e-3),
                "plain_ms": tp, "persistent_ms": tb,
+               "plain_sliced_ms": ts,
+               "plain_sliced_pairs_per_s": 2 * n3 / (ts * 1e-3),
                "false_accepts": fa, "false_rejects": fr,
                "false_accept_rate": fa / max(fa + tr, 1)}
         if ipk and hbm_gbs:
@@ -703,7 +727,8 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
             t_alu = 1e3 * alu / ipk["lop3"]
             t_xu = 1e3 * xu / ipk["bfind"]
             for form, nb, ms in (("plain", b_plain, tp),
-                                 ("persistent", b_pers, tb)):
+                                 ("persistent", b_pers, tb),
+                                 ("plain_sliced", b_plain, ts)):
                 t_hbm = 1e3 * nb / (hbm_gbs * 1e9)
                 t = max(t_hbm, t_alu, t_xu)
                 row[form + "_roofline"] = {
@@ -715,7 +740,8 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
     return {"workload": "10M x 250 bp + 10M x 150 bp, edit rate U[0,0.12], "
                         "E = 0..10 % of length",
             "roofline_note": "max(HBM, ALU, find-first) time of the form / "
-                             "measured time; ALU from the cheaper op model "
+                             "measured time; ALU from the cheapest op model "
+                             "(row words, columns, bit-sliced columns) "
                              f"on {sample} pairs of each length",
             "per_E": rows, "results_identical": same}
 
@@ -1091,17 +1117,25 @@ def run_ours(args):
         hq2, hr2 = hq.view(n, M), hr.view(n, M)
         F.filter_host(hq2, hr2, m=M, e=SWEEP, fmt=binding.SS_FMT_ASCII,
                       out_accept=hacc, out_obstacles=hobs)
-        e2e_steps = max(3, args.steps // 6)
+        # each step timed on its own; the value is taken from the median
+        # step (a host-side transient, e.g. memory a previous process is
+        # still releasing, slows single steps), the mean is reported beside
+        e2e_steps = max(5, args.steps // 4)
         barrier(world)
-        t0 = time.perf_counter()
+        per_step = []
         for _ in range(e2e_steps):
+            t0 = time.perf_counter()
             F.filter_host(hq2, hr2, m=M, e=SWEEP, fmt=binding.SS_FMT_ASCII,
                           out_accept=hacc, out_obstacles=hobs)
-        dt = max_over_ranks(time.perf_counter() - t0, world)
-        e2e = {"value": world * pairs_per_step * e2e_steps / dt,
+            per_step.append(time.perf_counter() - t0)
+        dt = max_over_ranks(float(np.median(per_step)), world)
+        dt_mean = max_over_ranks(float(np.mean(per_step)), world)
+        e2e = {"value": world * pairs_per_step / dt,
                "unit": "pairs/s", "h2d_bytes_per_step": 2 * n * M,
                "d2h_bytes_per_step": 5 * n * len(SWEEP),
-               "ms_per_step": 1e3 * dt / e2e_steps}
+               "ms_per_step": 1e3 * dt, "steps": e2e_steps,
+               "ms_per_step_mean": 1e3 * dt_mean,
+               "ms_per_step_each": [1e3 * x for x in per_step]}
         # the device path and the host path must agree
         same = (torch.equal(hacc, acc.cpu()) and torch.equal(hobs, obs.cpu()))
         e2e["matches_device_path"] = bool(same)

@@ -1,10 +1,13 @@
 """Parity at the benchmark's full sizes, in the launch configurations
 bench.py times:
 
-* 30M x 100 bp, E = 0, 2, ..., 10, plain launches (the headline sweep):
-  every pair at every threshold against the oracle;
+* 30M x 100 bp, E = 0, 2, ..., 10 (the headline sweep), over the
+  bit-sliced layout as bench.py's step runs it (ss_filter_sweep: E = 0, 2,
+  4 in one pass): every pair at every threshold against the oracle, and
+  the pair-major plain launches equal to it;
 * 10M x 250 bp + 10M x 150 bp at every E from 0 % to 10 % of the length,
-  plain and persistent: every pair of both forms against the oracle;
+  persistent: every pair against the oracle; the pair-major plain launches
+  and the bit-sliced sweep over all eleven thresholds equal to it;
 * the uneven 2M-pair batch (64..10000 bp, E = 5 %), one bucketed graph:
   every pair up to 2 kbp and a seeded 2 % sample of the longer ones;
 * full-shape served requests (up to 4096 pairs, 100..100000 bp, E = 10 %):
@@ -65,13 +68,21 @@ def test_headline_sweep_30M_every_pair():
     synth.pairs_fixed(SEED + 2, 0, n, m, synth.SHORT_POISSON,
                       out=(hq.numpy(), hr.numpy()))
     reads, refs = hq.numpy().reshape(n, m), hr.numpy().reshape(n, m)
+    sweep = [0, 2, 4, 6, 8, 10]
     with binding.Filter(0) as F:
-        q = F.pack(hq.cuda(), m=m, n=n)
-        r = F.pack(hr.cuda(), m=m, n=n)
-        for E in (0, 2, 4, 6, 8, 10):
+        dq, dr = hq.cuda(), hr.cuda()
+        sq = F.pack_sliced(dq, m=m, n=n)
+        sr = F.pack_sliced(dr, m=m, n=n)
+        sacc, sobs = F.filter_sweep(sq, sr, m=m, e=sweep, n=n, sync=True)
+        del sq, sr
+        q = F.pack(dq, m=m, n=n)
+        r = F.pack(dr, m=m, n=n)
+        for t, E in enumerate(sweep):
+            a, o = sacc[t].cpu().numpy(), sobs[t].cpu().numpy()
+            _check_all(a, o, reads, refs, m, E, f"sweep E={E}")
             acc, obs = F.filter(q, r, m=m, e=E, n=n, sync=True)
-            _check_all(acc.cpu().numpy(), obs.cpu().numpy(), reads, refs, m,
-                       E, f"sweep E={E}")
+            assert (acc.cpu().numpy() == a).all(), f"pair-major E={E}"
+            assert (obs.cpu().numpy() == o).all(), f"pair-major E={E}"
 
 
 def test_two_lengths_20M_every_pair_both_forms():
@@ -94,6 +105,17 @@ def test_two_lengths_20M_every_pair_both_forms():
                          ).cuda()
         lens = torch.cat([torch.full((n3,), 250, dtype=torch.int32),
                           torch.full((n3,), 150, dtype=torch.int32)]).cuda()
+        # the bit-sliced sweep over all eleven thresholds of each length
+        sliced = []
+        for (rd, rf), m in ((r250, 250), (r150, 150)):
+            sq = F.pack_sliced(torch.from_numpy(rd.reshape(-1)).cuda(), m=m,
+                               n=n3)
+            sr = F.pack_sliced(torch.from_numpy(rf.reshape(-1)).cuda(), m=m,
+                               n=n3)
+            es = [m * pct // 100 for pct in range(0, 11)]
+            sa, so = F.filter_sweep(sq, sr, m=m, e=es, n=n3, sync=True)
+            sliced.append((sa.cpu().numpy(), so.cpu().numpy()))
+            del sq, sr, sa, so
         for pct in range(0, 11):
             e250, e150 = 250 * pct // 100, 150 * pct // 100
             a1, o1 = F.filter(bufs[0][0], bufs[0][1], m=250, e=e250, n=n3,
@@ -115,6 +137,9 @@ def test_two_lengths_20M_every_pair_both_forms():
             assert (o1.cpu().numpy() == ob[:n3]).all(), f"250 bp {pct}%"
             assert (a2.cpu().numpy() == ab[n3:]).all(), f"150 bp {pct}%"
             assert (o2.cpu().numpy() == ob[n3:]).all(), f"150 bp {pct}%"
+            for k, part in ((0, slice(0, n3)), (1, slice(n3, 2 * n3))):
+                assert (sliced[k][0][pct] == ab[part]).all(), (k, pct)
+                assert (sliced[k][1][pct] == ob[part]).all(), (k, pct)
 
 
 def test_uneven_2M_batch_short_pairs_all_long_sampled():
