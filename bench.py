@@ -9,10 +9,11 @@ odd pairs are independent random sequences (the shape of the paper's
 
 One step = the whole hot path over the batch: pack the resident ASCII reads
 and references to 2 bits per base in the bit-sliced layout (SS_FMT_SLICED2,
-2 launches) and filter it at every threshold, 32 pairs per thread: E = 0, 2
-and 4 in one shared pass over the pairs (their walks cost less than reading
-the pairs), E = 6, 8 and 10 one launch each (4 launches, as
-ss_filter_sweep makes them).  ``value`` counts pair decisions (pairs x
+2 launches) and filter it at every threshold with one ss_filter_sweep
+call, 32 pairs per thread: E = 0, 2 and 4 in one shared pass over the pairs
+(their walks cost less than reading the pairs), E = 6, 8 and 10 one launch
+each (4 launches, side by side on the library's streams so that the GPU
+does not drain between them).  ``value`` counts pair decisions (pairs x
 thresholds) per second with the inputs resident in HBM; the inputs (6 GB
 ASCII + 1.5 GB packed) are far larger than L2, so no flush is needed.
 ``pair_major_form`` times the same step with the pair-major packed format
@@ -63,7 +64,8 @@ GROUPS = sweep_groups(SWEEP)
 SEED = 1910_09020 + 2
 WORKLOAD = ("short-read threshold sweep: 30M synthetic pairs x 100 bp "
             "(even pairs Poisson(3) edits, odd pairs random), "
-            "E in {0,2,4,6,8,10}, plain one-launch-per-threshold form")
+            "E in {0,2,4,6,8,10}, plain form (one sweep call: a shared pass "
+            "for E <= 4, one launch per larger E)")
 METRIC = "sequence pairs/sec (and Gbases/s) per GB300 vs roofline"
 # algorithmic bytes of one pair decision: both sequences at 2 bits per base
 # plus the accept byte and the int32 obstacle count
@@ -103,10 +105,11 @@ def parse():
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the batched and served forms")
     ap.add_argument("--workload", default="all",
-                    choices=["all", "batched", "long"],
+                    choices=["all", "batched", "long", "two_lengths"],
                     help="long: only the CTA-per-pair class (profiling); "
                          "batched: only the persistent launch of the uneven "
-                         "batch (for profiling)")
+                         "batch (for profiling); two_lengths: only the "
+                         "two-length comparison of forms")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window of each offered load")
     ap.add_argument("--batched-pairs", type=int, default=2_000_000,
@@ -630,11 +633,13 @@ def _fixed_model(reads, refs, m, E):
 def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
     """10M pairs of 250 bp and 10M of 150 bp, edit rate U[0, 0.12], E = 0 %
     .. 10 % of length: two plain launches (pair-major packed input, as the
-    persistent graph reads) against one persistent graph, and the two
-    plain launches over the bit-sliced layout, each with its roofline
-    fraction (HBM bytes of the form; ALU ops of the cheapest op model, the
-    bit-sliced one included, from the oracle's counters on `sample` pairs
-    of each length)."""
+    persistent graph reads) against one persistent graph; over the
+    bit-sliced layout, the two plain launches one after the other against
+    one segmented call (ss_filter_segments: a replayed CUDA graph whose two
+    launches run side by side); each with its roofline fraction (HBM bytes
+    of the form; ALU ops of the cheapest op model, the bit-sliced one
+    included, from the oracle's counters on `sample` pairs of each
+    length)."""
     import torch
 
     from paper_1910_09020_gb300 import synth
@@ -669,6 +674,7 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
     o = torch.empty(2 * n3, dtype=torch.int32, device="cuda")
     a2, o2 = torch.empty_like(a), torch.empty_like(o)
     a3, o3 = torch.empty_like(a), torch.empty_like(o)
+    a4, o4 = torch.empty_like(a), torch.empty_like(o)
     rows = []
     same = True
     for pct in range(0, 11):
@@ -691,11 +697,19 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
             F.filter(sbufs[1][0], sbufs[1][1], m=150, e=e150, n=n3,
                      fmt=binding.SS_FMT_SLICED2, out_accept=a3[n3:],
                      out_obstacles=o3[n3:])
+        def graph_sliced():
+            F.filter_segments(
+                [(sbufs[0][0], sbufs[0][1], 250, e250, n3,
+                  (a4[:n3], o4[:n3])),
+                 (sbufs[1][0], sbufs[1][1], 150, e150, n3,
+                  (a4[n3:], o4[n3:]))], fmt=binding.SS_FMT_SLICED2)
         tp = _time_ms(plain, 5, F.sync)
         tb = _time_ms(persistent, 5, F.sync)
         ts = _time_ms(plain_sliced, 5, F.sync)
+        tg = _time_ms(graph_sliced, 5, F.sync)
         same &= bool(torch.equal(a, a2) and torch.equal(o, o2) and
-                     torch.equal(a, a3) and torch.equal(o, o3))
+                     torch.equal(a, a3) and torch.equal(o, o3) and
+                     torch.equal(a, a4) and torch.equal(o, o4))
         # accuracy of these decisions against the banded edit distance
         conf = [0, 0, 0, 0]
         for (q, g), (m, e), sl in (((bufs[0]), (250, e250), slice(0, n3)),
@@ -711,6 +725,8 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
                "plain_ms": tp, "persistent_ms": tb,
                "plain_sliced_ms": ts,
                "plain_sliced_pairs_per_s": 2 * n3 / (ts * 1e-3),
+               "graph_sliced_ms": tg,
+               "graph_sliced_pairs_per_s": 2 * n3 / (tg * 1e-3),
                "false_accepts": fa, "false_rejects": fr,
                "false_accept_rate": fa / max(fa + tr, 1)}
         if ipk and hbm_gbs:
@@ -728,7 +744,8 @@ def run_two_lengths(F, ipk=None, hbm_gbs=None, sample=20000) -> dict:
             t_xu = 1e3 * xu / ipk["bfind"]
             for form, nb, ms in (("plain", b_plain, tp),
                                  ("persistent", b_pers, tb),
-                                 ("plain_sliced", b_plain, ts)):
+                                 ("plain_sliced", b_plain, ts),
+                                 ("graph_sliced", b_plain, tg)):
                 t_hbm = 1e3 * nb / (hbm_gbs * 1e9)
                 t = max(t_hbm, t_alu, t_xu)
                 row[form + "_roofline"] = {
@@ -1049,12 +1066,12 @@ def run_ours(args):
     sr = torch.empty(SL, dtype=torch.int32, device=dev)
     acc = torch.empty((len(SWEEP), n), dtype=torch.uint8, device=dev)
     obs = torch.empty((len(SWEEP), n), dtype=torch.int32, device=dev)
-    # events on the stream the kernels are launched on (torch's current
-    # stream, passed to the library), one set per timed step
-    nev = 2 + 2 * len(GROUPS)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)]
+    # events on the stream the library is called on (torch's current
+    # stream; the sweep's launches on the library's other streams are
+    # joined back into it before the call returns), one set per timed step
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
            for _ in range(args.steps)]
-    launch_ms = {"pack": [], **{grp: [] for grp in GROUPS}}
+    launch_ms = {"pack": [], "filter": []}
     row = {E: t for t, E in enumerate(SWEEP)}
 
     def step(ev):
@@ -1064,22 +1081,10 @@ def run_ours(args):
         F.pack_sliced(dr, m=M, n=n, out=sr)
         if ev:
             ev[1].record()
-        for t, grp in enumerate(GROUPS):
-            if ev:
-                ev[2 + 2 * t].record()
-            if len(grp) > 1:
-                # the group's rows of acc/obs are consecutive
-                a0 = row[grp[0]]
-                F.filter_sweep(sq, sr, m=M, e=list(grp), n=n,
-                               out_accept=acc[a0:a0 + len(grp)],
-                               out_obstacles=obs[a0:a0 + len(grp)])
-            else:
-                F.filter(sq, sr, m=M, e=grp[0], n=n,
-                         fmt=binding.SS_FMT_SLICED2,
-                         out_accept=acc[row[grp[0]]],
-                         out_obstacles=obs[row[grp[0]]])
-            if ev:
-                ev[3 + 2 * t].record()
+        F.filter_sweep(sq, sr, m=M, e=SWEEP, n=n, out_accept=acc,
+                       out_obstacles=obs)
+        if ev:
+            ev[2].record()
 
     for _ in range(args.warmup):
         step(None)
@@ -1099,8 +1104,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     for ev in evs:
         launch_ms["pack"].append(ev[0].elapsed_time(ev[1]))
-        for t, grp in enumerate(GROUPS):
-            launch_ms[grp].append(ev[2 + 2 * t].elapsed_time(ev[3 + 2 * t]))
+        launch_ms["filter"].append(ev[1].elapsed_time(ev[2]))
     barrier(world)
     clk = clocks.stop()
     elapsed_ms = start.elapsed_time(stop)
@@ -1198,13 +1202,30 @@ def run_ours(args):
             acc.cpu().numpy(), obs.cpu().numpy())
         model = op_model(stats, n, M)
     hbm = peaks["hbm_gbs"] * 1e9
+    # each launch of the sweep alone (outside the timed region, one after
+    # the other on one stream), for the per-launch rooflines
+    solo_ms = {}
+    for grp in GROUPS:
+        a0 = row[grp[0]]
+        if len(grp) > 1:
+            fn = (lambda grp=grp, a0=a0: F.filter_sweep(
+                sq, sr, m=M, e=list(grp), n=n,
+                out_accept=acc[a0:a0 + len(grp)],
+                out_obstacles=obs[a0:a0 + len(grp)]))
+        else:
+            fn = (lambda grp=grp, a0=a0: F.filter(
+                sq, sr, m=M, e=grp[0], n=n, fmt=binding.SS_FMT_SLICED2,
+                out_accept=acc[a0], out_obstacles=obs[a0]))
+        solo_ms[grp] = _time_ms(fn, 5, F.sync)
     per_launch = []
     roof_total = meas_total = 0.0
+    sum_t = {"hbm": 0.0, "alu": 0.0, "xu": 0.0}
     for grp in GROUPS:
-        ms = float(np.mean(launch_ms[grp]))
+        ms = solo_ms[grp]
         # the pairs read once, each threshold's results written
         gbytes = FILTER_BYTES_PER_PAIR + 5 * (len(grp) - 1)
         t_hbm = n * gbytes / hbm
+        sum_t["hbm"] += 1e3 * t_hbm
         d = {"E": grp[0] if len(grp) == 1 else list(grp), "ms": ms,
              "kernel": "k_sliced" if len(grp) == 1 else "k_sliced_set",
              "pairs_per_s": n / (ms * 1e-3),
@@ -1217,6 +1238,8 @@ def run_ours(args):
             xu = sum(model[E]["xu_ops_per_pair"] for E in grp)
             t_alu = n * alu / ipk["lop3"]
             t_xu = n * xu / ipk["bfind"]
+            sum_t["alu"] += 1e3 * t_alu
+            sum_t["xu"] += 1e3 * t_xu
             d.update({"t_alu_ms": 1e3 * t_alu, "t_xu_ms": 1e3 * t_xu,
                       "model": [model[E]["model"] for E in grp],
                       "alu_ops_per_pair": alu,
@@ -1242,27 +1265,42 @@ def run_ours(args):
         roof_total += 1e3 * t_bound
         meas_total += ms
         per_launch.append(d)
-    filter_ms = sum(float(np.mean(launch_ms[grp])) for grp in GROUPS)
+    # the step's filter section (the sweep call, launches side by side),
+    # timed in the timed region; its roofline time is the largest of the
+    # summed HBM, logic-pipe and find-first times of its launches (they
+    # share the GPU's bandwidth and pipes)
+    filter_ms = float(np.mean(launch_ms["filter"]))
     pack_ms = float(np.mean(launch_ms["pack"]))
-    alu_share = sum(d["ms"] for d in per_launch if d["bound"] != "hbm")
-    dom_bound = "alu" if alu_share > filter_ms / 2 else "hbm"
+    dom_bound = max(sum_t, key=sum_t.get)
     if dom_bound == "hbm":
         achieved = sum(n * d["algorithmic_bytes_per_pair"]
                        for d in per_launch) / (filter_ms * 1e-3) / 1e9
         peak, unit = peaks["hbm_gbs"], "GB/s"
-    else:
+    elif dom_bound == "alu":
         ops = sum(n * model[E]["alu_ops_per_pair"] for E in SWEEP)
         achieved = ops / (filter_ms * 1e-3) / 1e12
         peak, unit = ipk["lop3"] / 1e12, "Tops/s"
+    else:
+        ops = sum(n * model[E]["xu_ops_per_pair"] for E in SWEEP)
+        achieved = ops / (filter_ms * 1e-3) / 1e12
+        peak, unit = ipk["bfind"] / 1e12, "Tops/s"
     traffic = ncu_traffic("k_sliced")
     roofline = {
         "kernel": "k_sliced / k_sliced_set (plain filter over the "
                   "bit-sliced layout: E = 0, 2, 4 in one shared pass, "
-                  "E = 6, 8, 10 one launch each)",
+                  "E = 6, 8, 10 one launch each, side by side)",
         "bound": dom_bound, "achieved": achieved, "peak": peak, "unit": unit,
-        "frac": roof_total / meas_total,
-        "frac_note": "sum over the step's filter launches of max(HBM, ALU, "
-                     "find-first) roofline time / measured time (a shared "
+        "frac": max(sum_t.values()) / filter_ms,
+        "filter_section_ms": filter_ms,
+        "t_section_ms": sum_t,
+        "frac_launches_alone": roof_total / meas_total,
+        "frac_note": "the step's filter section (one ss_filter_sweep call, "
+                     "its 4 launches side by side, timed by events in the "
+                     "timed region): max over HBM, ALU and find-first of "
+                     "the launches' summed roofline times / the section's "
+                     "time.  frac_launches_alone: the sum over the launches "
+                     "of max(HBM, ALU, find-first) / the sum of their times "
+                     "each launched alone (per_launch; a shared "
                      "pass: the pairs read once, each threshold's results "
                      "written, the ALU ops of all its thresholds); the ALU "
                      "term counts "
@@ -1351,6 +1389,21 @@ def run_batched_only(args):
     return 0
 
 
+def run_two_lengths_only(args):
+    """The two-length comparison of forms alone (10M x 250 bp + 10M x 150
+    bp, E = 0..10 % of length)."""
+    import torch
+
+    from paper_1910_09020_gb300 import binding
+    from paper_1910_09020_gb300.peaks import measure as measure_int_peaks
+    torch.cuda.set_device(0)
+    F = binding.Filter(0, workspace_bytes=8 << 30)
+    out = run_two_lengths(F, measure_int_peaks(0), measured_peaks()["hbm_gbs"])
+    print(json.dumps(out), flush=True)
+    F.close()
+    return 0
+
+
 def run_long_only(args):
     """The CTA-per-pair class alone (profiling aid): 608 pairs of 20 kbp,
     edit rate 5 %, E = 10 % of the length (2000; 126 row words per pair,
@@ -1390,6 +1443,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched_only(args)
+    if args.workload == "two_lengths":
+        return run_two_lengths_only(args)
     if args.workload == "long":
         return run_long_only(args)
     return run_ours(args)

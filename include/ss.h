@@ -180,6 +180,35 @@ int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
                     int64_t n, void *stream, uint8_t *out_accept,
                     int32_t *out_obstacles);
 
+/* One batch of a segmented call: n fixed-stride pairs of uniform length m
+ * filtered at threshold e (Section 2.4), in the call's format. */
+typedef struct ss_segment {
+    const void *reads;       /* device; SS_FMT_SLICED2: 16-byte aligned      */
+    const void *refs;        /* device; same layout as reads                 */
+    int64_t n;               /* pairs (>= 0; 0: the segment is skipped)      */
+    int32_t m;               /* bases per sequence (>= 0)                    */
+    int32_t e;               /* threshold (>= 0)                             */
+    uint8_t *out_accept;     /* device uint8[n]: 1 if count <= e             */
+    int32_t *out_obstacles;  /* device int32[n]: min(count, e + 1)           */
+} ss_segment;
+
+/* Several uniform batches (segments, e.g. reads of 150 and of 250 bases,
+ * each with its own threshold) filtered by one call: a batch mixing lengths
+ * and thresholds, bucketed by the caller into uniform segments.  format is
+ * SS_FMT_SLICED2 (every e <= SS_SLICED_MAX_E) or SS_FMT_PACKED2 (fixed
+ * stride ceil(m/16) words per sequence; m <= SS_PLAIN_MAX_M and e <=
+ * SS_PLAIN_MAX_E).  Every segment's launch is independent of the others:
+ * they run side by side on the context's streams, the costliest first, so
+ * that the GPU does not drain between them.  Unless flags holds
+ * SS_FLAG_NO_GRAPH, the launches are captured once per distinct segment
+ * table (pointers and sizes) as a CUDA graph and replayed.  The segments'
+ * outputs must not overlap one another.  The whole table is checked before
+ * anything is launched.  Returns SS_OK, SS_ERR_INVALID_ARG, SS_ERR_UNSUPPORTED
+ * (a threshold or length the format's kernel does not take) or SS_ERR_CUDA;
+ * device-side errors through ss_sync. */
+int ss_filter_segments(ss_ctx *ctx, const ss_segment *segs, int n_seg,
+                       int format, int flags, void *stream);
+
 /* Fixed-stride pairs of uniform length m held in HOST memory, filtered at
  * each of the n_e thresholds of the host array e_list (a threshold sweep as
  * in Section 3.2 needs the pairs copied once).  The library streams chunks

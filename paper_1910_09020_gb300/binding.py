@@ -44,6 +44,7 @@ EXPORTED = (
     "ss_create", "ss_destroy", "ss_strerror", "ss_version",
     "ss_packed_words", "ss_pack", "ss_filter_batch", "ss_filter_host",
     "ss_sliced_words", "ss_pack_sliced", "ss_filter_sweep",
+    "ss_filter_segments",
     "ss_sync", "ss_get_counters", "ss_set_tuning", "ss_get_tuning",
     "ss_autotune", "ss_filter_batch_noalloc", "ss_edit_distance_banded",
     "ss_filter_confusion", "ss_compact_accepted", "ss_gather_pairs",
@@ -79,6 +80,14 @@ class ServerStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Segment(ctypes.Structure):
+    """ss_segment: one uniform batch of ss_filter_segments."""
+    _fields_ = [("reads", ctypes.c_void_p), ("refs", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("m", ctypes.c_int32),
+                ("e", ctypes.c_int32), ("out_accept", ctypes.c_void_p),
+                ("out_obstacles", ctypes.c_void_p)]
 
 
 class Counters(ctypes.Structure):
@@ -119,6 +128,9 @@ def load(build_if_needed: bool = True):
     lib.ss_pack_sliced.argtypes = [P, P, I32, I64, P, P]
     lib.ss_filter_sweep.argtypes = [P, P, P, ctypes.c_int, I32, P,
                                     ctypes.c_int, I64, P, P, P]
+    lib.ss_filter_segments.argtypes = [P, ctypes.POINTER(Segment),
+                                       ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, P]
     lib.ss_filter_batch.argtypes = [P, P, P, ctypes.c_int, P, P, I32, P, I32,
                                     I64, ctypes.c_int, P, P, P]
     lib.ss_filter_host.argtypes = [P, P, P, ctypes.c_int, I32, P,
@@ -204,6 +216,12 @@ def ss_filter_sweep(ctx, reads, refs, fmt, m, e_list, n_e, n, stream,
     return load().ss_filter_sweep(ctx, reads or None, refs or None, fmt, m,
                                   e_list or None, n_e, n, stream or None,
                                   out_accept or None, out_obstacles or None)
+
+
+def ss_filter_segments(ctx, segs, n_seg, fmt, flags, stream) -> int:
+    """segs: a ctypes array of Segment (or None with n_seg 0)."""
+    return load().ss_filter_segments(ctx, segs, n_seg, fmt, flags,
+                                     stream or None)
 
 
 def ss_pack(ctx, ascii, offsets, lengths, m, n, packed, packed_offsets,
@@ -447,6 +465,41 @@ class Filter:
         if sync:
             self.sync(stream)
         return out_accept, out_obstacles
+
+    def filter_segments(self, segments, *, fmt: int = SS_FMT_SLICED2,
+                        graph: bool = True, stream=None, sync: bool = False):
+        """Uniform batches filtered by one call (ss_filter_segments).
+        ``segments``: (reads, refs, m, e, n) tuples of device tensors in the
+        format ``fmt``; returns one (accept uint8[n], obstacles int32[n])
+        pair of new device tensors per segment, in the given order.  A
+        6-tuple (reads, refs, m, e, n, (out_accept, out_obstacles)) writes
+        to the given tensors instead."""
+        import torch
+        d = self.device
+        arr = (Segment * max(len(segments), 1))()
+        outs = []
+        for i, sg in enumerate(segments):
+            reads, refs, m, e, n = sg[:5]
+            m, e, n = int(m), int(e), int(n)
+            if len(sg) > 5:
+                acc, obs = sg[5]
+            else:
+                acc = torch.empty(n, dtype=torch.uint8, device=reads.device)
+                obs = torch.empty(n, dtype=torch.int32, device=reads.device)
+            seq = _seq_bytes(fmt, n, m)
+            arr[i] = Segment(_dptr(reads, d, "reads", seq) or None,
+                             _dptr(refs, d, "refs", seq) or None, n, m, e,
+                             _dptr(acc, d, "out_accept", n) or None,
+                             _dptr(obs, d, "out_obstacles", 4 * n) or None)
+            outs.append((acc, obs))
+        rc = ss_filter_segments(self.ctx, arr if segments else None,
+                                len(segments), fmt,
+                                0 if graph else SS_FLAG_NO_GRAPH,
+                                _stream_handle(stream))
+        _check(rc, "ss_filter_segments")
+        if sync:
+            self.sync(stream)
+        return outs
 
     def filter_host(self, reads, refs, *, m: int, e, n=None,
                     fmt: int = SS_FMT_ASCII, out_accept=None,

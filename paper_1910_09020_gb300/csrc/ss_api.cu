@@ -37,6 +37,18 @@ struct GraphEntry {
     uint64_t last_use;
 };
 
+// A captured segmented call: its format and segment table.
+struct SegGraph {
+    int format;
+    std::vector<ss_segment> segs;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+};
+
+// Independent launches of one call go round-robin to the caller's stream
+// and kLanes - 1 streams of the context.
+constexpr int kLanes = 4;
+
 }  // namespace
 
 struct ss_ctx {
@@ -46,6 +58,9 @@ struct ss_ctx {
     cudaStream_t side = nullptr;     // column-wise classes (forked)
     cudaStream_t hstream[2] = {nullptr, nullptr};  // ss_filter_host pipeline
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t lane[kLanes - 1] = {};   // independent launches (forked)
+    cudaEvent_t lane_fork = nullptr;
+    cudaEvent_t lane_done[kLanes - 1] = {};
     int *d_status = nullptr;         // [0] latched device errors, [1] the
                                      // value ss_sync last took from [0]
     size_t budget = 0;
@@ -53,6 +68,7 @@ struct ss_ctx {
     size_t ws_bytes = 0;
     ssk::TuneParams tune;
     std::vector<GraphEntry> graphs;
+    std::vector<SegGraph> seg_graphs;
     uint64_t tick = 0;
     ss_counters counters{};
 };
@@ -104,6 +120,9 @@ void drop_graphs(ss_ctx *ctx)
     for (GraphEntry &g : ctx->graphs)
         cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
+    for (SegGraph &g : ctx->seg_graphs)
+        cudaGraphExecDestroy(g.exec);
+    ctx->seg_graphs.clear();
 }
 
 // Grow the workspace to at least `bytes` (within the budget).
@@ -132,6 +151,69 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // NULL selects the CUDA default stream, as in other CUDA libraries (and as
 // torch's default stream handle is 0).
 cudaStream_t pick_stream(void *stream) { return (cudaStream_t)stream; }
+
+// Launches that do not depend on one another, spread over the caller's
+// stream and the context's lane streams: the CTAs of the next kernel fill
+// the SMs that the previous one's last wave leaves idle, instead of the GPU
+// draining between them.  Job i runs on lane i % kLanes (lane 0: the
+// caller's stream); the destructor joins every lane used back into the
+// caller's stream, so what follows on it sees all the jobs' results.
+class Lanes {
+  public:
+    Lanes(ss_ctx *ctx, cudaStream_t st) : ctx_(ctx), st_(st) {}
+    Lanes(const Lanes &) = delete;
+    Lanes &operator=(const Lanes &) = delete;
+    ~Lanes() { (void)join(); }
+
+    // The stream of job `job`; the jobs are asked for in launch order.
+    cudaError_t stream(int job, cudaStream_t &out)
+    {
+        const int l = job % kLanes;
+        out = st_;
+        cudaError_t e;
+        if (!forked_) {
+            // the fork point: on the caller's stream before the first job,
+            // so that no lane waits for a job of lane 0
+            if ((e = cudaEventRecord(ctx_->lane_fork, st_)) != cudaSuccess)
+                return e;
+            forked_ = true;
+        }
+        if (l == 0)
+            return cudaSuccess;
+        if (!(used_ & (1u << l))) {
+            if ((e = cudaStreamWaitEvent(ctx_->lane[l - 1], ctx_->lane_fork,
+                                         0)) != cudaSuccess)
+                return e;
+            used_ |= 1u << l;
+        }
+        out = ctx_->lane[l - 1];
+        return cudaSuccess;
+    }
+
+    cudaError_t join()
+    {
+        cudaError_t first = cudaSuccess;
+        for (int l = 1; l < kLanes; ++l) {
+            if (!(used_ & (1u << l)))
+                continue;
+            cudaError_t e = cudaEventRecord(ctx_->lane_done[l - 1],
+                                            ctx_->lane[l - 1]);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(st_, ctx_->lane_done[l - 1], 0);
+            if (e != cudaSuccess && first == cudaSuccess)
+                first = e;
+        }
+        used_ = 0;
+        forked_ = false;
+        return first;
+    }
+
+  private:
+    ss_ctx *ctx_;
+    cudaStream_t st_;
+    unsigned used_ = 0;
+    bool forked_ = false;
+};
 
 static_assert(SS_SLICED_MAX_E == ssk::kSlicedMaxE, "sliced limit");
 static_assert(SS_PLAIN_MAX_E == ssk::kRwMaxE && SS_PLAIN_MAX_M == ssk::kRwMaxM,
@@ -338,7 +420,7 @@ cudaError_t launch_rw_uniform(int E, const uint32_t *reads,
 
 extern "C" {
 
-int ss_version(void) { return 300; }
+int ss_version(void) { return 400; }
 
 const char *ss_strerror(int code)
 {
@@ -396,12 +478,23 @@ int ss_create(ss_ctx **out, int device, size_t workspace_bytes)
             cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) !=
             cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->lane_fork, cudaEventDisableTiming) !=
+            cudaSuccess ||
         cudaMalloc(&ctx->d_status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
         (void)cudaGetLastError();
         ss_destroy(ctx);
         return SS_ERR_CUDA;
     }
+    for (int l = 0; l < kLanes - 1; ++l)
+        if (cudaStreamCreateWithFlags(&ctx->lane[l], cudaStreamNonBlocking) !=
+                cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->lane_done[l],
+                                     cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ss_destroy(ctx);
+            return SS_ERR_CUDA;
+        }
     ctx->sm_count = prop.multiProcessorCount;
     if (ssk::bucket_init() != cudaSuccess) {
         (void)cudaGetLastError();
@@ -427,6 +520,14 @@ int ss_destroy(ss_ctx *ctx)
         cudaEventDestroy(ctx->fork);
     if (ctx->join)
         cudaEventDestroy(ctx->join);
+    for (int l = 0; l < kLanes - 1; ++l) {
+        if (ctx->lane[l])
+            cudaStreamDestroy(ctx->lane[l]);
+        if (ctx->lane_done[l])
+            cudaEventDestroy(ctx->lane_done[l]);
+    }
+    if (ctx->lane_fork)
+        cudaEventDestroy(ctx->lane_fork);
     if (ctx->ws)
         cudaFree(ctx->ws);
     if (ctx->d_status)
@@ -497,7 +598,9 @@ extern "C++" {
 // 0..kSlicedMaxE, checked by the caller): the distinct thresholds up to
 // kSlicedSetMaxE share one pass over the pairs when there are two or more
 // of them (their walks cost less than the pass), every other threshold gets
-// its own launch.  acc(t), obs(t): where threshold t's results go.
+// its own launch.  The launches are independent (each writes its own
+// results): they go to the lanes, the costliest (largest threshold) first,
+// the shared pass last.  acc(t), obs(t): where threshold t's results go.
 template <class Acc, class Obs>
 static int sweep_sliced(ss_ctx *ctx, const uint32_t *q, const uint32_t *r,
                         int32_t m, const int32_t *e_list, int n_e, int64_t n,
@@ -515,6 +618,22 @@ static int sweep_sliced(ss_ctx *ctx, const uint32_t *q, const uint32_t *r,
             ++shared;
         }
     }
+    std::vector<int> own;  // thresholds with a launch of their own
+    for (int t = 0; t < n_e; ++t) {
+        const int e = e_list[t];
+        if (!(shared >= 2 && e < S && first[e] == t))
+            own.push_back(t);
+    }
+    std::stable_sort(own.begin(), own.end(), [&](int a, int b) {
+        return e_list[a] > e_list[b];
+    });
+    Lanes lanes(ctx, st);
+    int job = 0;
+    cudaStream_t ls;
+    for (int t : own) {
+        SS_CUDA(lanes.stream(job++, ls));
+        SS_TRY(filter_sliced(ctx, q, r, m, e_list[t], n, acc(t), obs(t), ls));
+    }
     if (shared >= 2) {
         unsigned mask = 0;
         uint8_t *pa[S];
@@ -527,15 +646,11 @@ static int sweep_sliced(ss_ctx *ctx, const uint32_t *q, const uint32_t *r,
                 po[i] = obs(first[e]);
                 ++i;
             }
-        SS_CUDA(ssk::launch_sliced_set(q, r, n, m, mask, pa, po, st));
+        SS_CUDA(lanes.stream(job++, ls));
+        SS_CUDA(ssk::launch_sliced_set(q, r, n, m, mask, pa, po, ls));
         ctx->counters.launches += 1;
     }
-    for (int t = 0; t < n_e; ++t) {
-        const int e = e_list[t];
-        if (shared >= 2 && e < S && first[e] == t)
-            continue;  // in the shared pass
-        SS_TRY(filter_sliced(ctx, q, r, m, e, n, acc(t), obs(t), st));
-    }
+    SS_CUDA(lanes.join());
     return SS_OK;
 }
 }  // extern "C++"
@@ -606,12 +721,20 @@ int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
         uint32_t *pr = (uint32_t *)((char *)ctx->ws + seq_bytes);
         for (int64_t p0 = 0; p0 < n; p0 += chunk) {
             const int64_t cn = std::min(chunk, n - p0);
-            SS_CUDA(ssk::launch_pack_sliced(
-                (const uint8_t *)reads + p0 * (int64_t)m, cn, m, pq,
-                ctx->d_status, st));
-            SS_CUDA(ssk::launch_pack_sliced(
-                (const uint8_t *)refs + p0 * (int64_t)m, cn, m, pr,
-                ctx->d_status, st));
+            {
+                // the two sides' packs side by side
+                Lanes pk(ctx, st);
+                cudaStream_t ls;
+                SS_CUDA(pk.stream(0, ls));
+                SS_CUDA(ssk::launch_pack_sliced(
+                    (const uint8_t *)reads + p0 * (int64_t)m, cn, m, pq,
+                    ctx->d_status, ls));
+                SS_CUDA(pk.stream(1, ls));
+                SS_CUDA(ssk::launch_pack_sliced(
+                    (const uint8_t *)refs + p0 * (int64_t)m, cn, m, pr,
+                    ctx->d_status, ls));
+                SS_CUDA(pk.join());
+            }
             ctx->counters.launches += 2;
             SS_TRY(sweep_sliced(ctx, pq, pr, m, e_list, n_e, cn, acc_at(p0),
                                 obs_at(p0), st));
@@ -625,6 +748,140 @@ int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
                                nullptr, e_list[t], n, SS_MODE_AUTO, stream,
                                out_accept + (size_t)t * n,
                                out_obstacles + (size_t)t * n));
+    return SS_OK;
+}
+
+extern "C++" {
+// One segment's launch (the segment checked by the caller).
+static int segment_launch(ss_ctx *ctx, int format, const ss_segment &s,
+                          cudaStream_t st)
+{
+    if (s.m == 0) {
+        // nothing to route: every pair accepted with 0 obstacles
+        SS_CUDA(cudaMemsetAsync(s.out_accept, 1, (size_t)s.n, st));
+        SS_CUDA(cudaMemsetAsync(s.out_obstacles, 0, (size_t)s.n * 4, st));
+        return SS_OK;
+    }
+    if (format == SS_FMT_SLICED2)
+        return filter_sliced(ctx, (const uint32_t *)s.reads,
+                             (const uint32_t *)s.refs, s.m, s.e, s.n,
+                             s.out_accept, s.out_obstacles, st);
+    SS_CUDA(ssk::launch_rw_uniform(s.e, (const uint32_t *)s.reads,
+                                   (const uint32_t *)s.refs, s.n, s.m,
+                                   s.out_accept, s.out_obstacles,
+                                   ctx->d_status, st));
+    ctx->counters.launches += 1;
+    return SS_OK;
+}
+
+static int segments_launch(ss_ctx *ctx, int format,
+                           const std::vector<ss_segment> &segs,
+                           cudaStream_t st)
+{
+    Lanes lanes(ctx, st);
+    cudaStream_t ls;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        SS_CUDA(lanes.stream((int)i, ls));
+        SS_TRY(segment_launch(ctx, format, segs[i], ls));
+    }
+    SS_CUDA(lanes.join());
+    return SS_OK;
+}
+
+// A segment's time, roughly: the larger of its bytes at the HBM rate and
+// its walk's logic operations (m (6e + 3) / 32 per pair) at the logic-pipe
+// rate, in units where the two rates are 6.8 and 20 per unit time.
+static double segment_cost(const ss_segment &s)
+{
+    const double bytes = 2.0 * ((s.m + 3) / 4) + 5.0;
+    const double ops = (double)s.m * (6.0 * s.e + 3.0) / 32.0;
+    return (double)s.n * std::max(bytes / 6.8, ops / 20.0);
+}
+}  // extern "C++"
+
+int ss_filter_segments(ss_ctx *ctx, const ss_segment *segs, int n_seg,
+                       int format, int flags, void *stream)
+{
+    if (!ctx || n_seg < 0 || (n_seg > 0 && !segs))
+        return SS_ERR_INVALID_ARG;
+    if (format != SS_FMT_SLICED2 && format != SS_FMT_PACKED2)
+        return SS_ERR_INVALID_ARG;
+    if (flags & ~SS_FLAG_NO_GRAPH)
+        return SS_ERR_INVALID_ARG;
+    std::vector<ss_segment> work;
+    int64_t pairs = 0;
+    bool unsupported = false;
+    for (int i = 0; i < n_seg; ++i) {
+        const ss_segment &s = segs[i];
+        if (s.n < 0 || s.m < 0 || s.e < 0)
+            return SS_ERR_INVALID_ARG;
+        if (s.n == 0)
+            continue;
+        if (!s.reads || !s.refs || !s.out_accept || !s.out_obstacles)
+            return SS_ERR_INVALID_ARG;
+        if (format == SS_FMT_SLICED2) {
+            if ((((uintptr_t)s.reads) | ((uintptr_t)s.refs)) & 15)
+                return SS_ERR_INVALID_ARG;
+            unsupported |= s.e > ssk::kSlicedMaxE;
+        } else {
+            unsupported |= s.m > 0 && !plain_ok(s.m, s.e);
+        }
+        work.push_back(s);
+        pairs += s.n;
+    }
+    if (unsupported)
+        return SS_ERR_UNSUPPORTED;
+    if (work.empty())
+        return SS_OK;
+    std::stable_sort(work.begin(), work.end(),
+                     [](const ss_segment &a, const ss_segment &b) {
+                         return segment_cost(a) > segment_cost(b);
+                     });
+    DeviceGuard g(ctx->device);
+    if (!g.ok)
+        return SS_ERR_CUDA;
+    cudaStream_t st = pick_stream(stream);
+    ctx->counters.pairs += pairs;
+    if (flags & SS_FLAG_NO_GRAPH)
+        return segments_launch(ctx, format, work, st);
+    const size_t key_bytes = work.size() * sizeof(ss_segment);
+    for (SegGraph &sg : ctx->seg_graphs)
+        if (sg.format == format && sg.segs.size() == work.size() &&
+            std::memcmp(sg.segs.data(), work.data(), key_bytes) == 0) {
+            sg.last_use = ++ctx->tick;
+            SS_CUDA(cudaGraphLaunch(sg.exec, st));
+            ctx->counters.graph_replays += 1;
+            return SS_OK;
+        }
+    // capture on the context's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured), replay on the caller's
+    cudaGraph_t graph = nullptr;
+    SS_CUDA(cudaStreamBeginCapture(ctx->stream,
+                                   cudaStreamCaptureModeThreadLocal));
+    const int rc = segments_launch(ctx, format, work, ctx->stream);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc != SS_OK || ce != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc != SS_OK ? rc : cuda_fail(ce);
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess)
+        return cuda_fail(ie);
+    if (ctx->seg_graphs.size() >= kMaxGraphs) {
+        auto lru = std::min_element(
+            ctx->seg_graphs.begin(), ctx->seg_graphs.end(),
+            [](const SegGraph &a, const SegGraph &b) {
+                return a.last_use < b.last_use;
+            });
+        cudaGraphExecDestroy(lru->exec);
+        ctx->seg_graphs.erase(lru);
+    }
+    ctx->seg_graphs.push_back(SegGraph{format, work, exec, ++ctx->tick});
+    SS_CUDA(cudaGraphLaunch(exec, st));
+    ctx->counters.graph_replays += 1;
     return SS_OK;
 }
 
@@ -877,6 +1134,8 @@ int ss_sync(ss_ctx *ctx, void *stream)
     SS_CUDA(cudaStreamSynchronize(st));
     SS_CUDA(cudaStreamSynchronize(ctx->stream));
     SS_CUDA(cudaStreamSynchronize(ctx->side));
+    for (cudaStream_t l : ctx->lane)
+        SS_CUDA(cudaStreamSynchronize(l));
     // take the status word (read and clear in one atomic exchange) on the
     // context's own non-blocking stream: a flag latched by a launch on any
     // other stream is either taken here or kept for the next ss_sync

@@ -57,6 +57,8 @@ def test_null_context_rejected():
     assert binding.ss_filter_batch(0, 1, 1, 0, 0, 0, 10, 0, 1, 5, 0, 0, 1,
                                    1) == binding.SS_ERR_INVALID_ARG
     assert binding.ss_sync(0) == binding.SS_ERR_INVALID_ARG
+    assert binding.ss_filter_segments(0, None, 0, binding.SS_FMT_SLICED2, 0,
+                                      0) == binding.SS_ERR_INVALID_ARG
     assert lib.ss_destroy(None) == binding.SS_OK
 
 
