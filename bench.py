@@ -224,6 +224,8 @@ KERNEL_SOURCES = {
     "k_pack_fixed": ["ss_device.cuh", "ss_pack.cuh", "ss_pack.cu"],
     "k_sliced": ["ss_device.cuh", "ss_rw_config.h", "ss_sliced.cuh",
                  "ss_sliced.cu"],
+    "k_sliced_set": ["ss_device.cuh", "ss_rw_config.h", "ss_sliced.cuh",
+                     "ss_sliced_set.cu"],
     "k_pack_sliced_span": ["ss_device.cuh", "ss_rw_config.h", "ss_pack.cuh",
                            "ss_sliced.cuh", "ss_pack.cu"],
 }
@@ -1284,7 +1286,11 @@ def run_ours(args):
         ops = sum(n * model[E]["xu_ops_per_pair"] for E in SWEEP)
         achieved = ops / (filter_ms * 1e-3) / 1e12
         peak, unit = ipk["bfind"] / 1e12, "Tops/s"
-    traffic = ncu_traffic("k_sliced")
+    # DRAM bytes of the section: each launch's ncu figure per pair
+    per_kernel = [ncu_traffic("k_sliced" if len(grp) == 1 else
+                              "k_sliced_set") for grp in GROUPS]
+    traffic = (None if any(t is None for t in per_kernel)
+               else n * sum(per_kernel))
     roofline = {
         "kernel": "k_sliced / k_sliced_set (plain filter over the "
                   "bit-sliced layout: E = 0, 2, 4 in one shared pass, "
@@ -1308,8 +1314,10 @@ def run_ours(args):
                      "each E (per_launch[].model): row words, columns one "
                      "pair per thread, bit-sliced columns (32 pairs per "
                      "word, every column walked)",
-        "traffic": None if traffic is None else traffic * n,
+        "traffic": traffic,
         "algorithmic_bytes_per_launch": n * FILTER_BYTES_PER_PAIR,
+        "algorithmic_bytes_section": sum(n * d["algorithmic_bytes_per_pair"]
+                                         for d in per_launch),
         "peak_source": f"HBM {peaks['hbm_source']} ({peaks['hbm_gbs']} GB/s); "
                        "integer pipes measured live by microbenchmark",
         "int_peaks_tops": {k: v / 1e12 for k, v in ipk.items()},

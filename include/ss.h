@@ -199,7 +199,8 @@ typedef struct ss_segment {
  * stride ceil(m/16) words per sequence; m <= SS_PLAIN_MAX_M and e <=
  * SS_PLAIN_MAX_E).  Every segment's launch is independent of the others:
  * they run side by side on the context's streams, the costliest first, so
- * that the GPU does not drain between them.  Unless flags holds
+ * that the GPU does not drain between them; over SS_FMT_SLICED2, segments
+ * of one threshold share a launch (up to 8 per launch).  Unless flags holds
  * SS_FLAG_NO_GRAPH, the launches are captured once per distinct segment
  * table (pointers and sizes) as a CUDA graph and replayed.  The segments'
  * outputs must not overlap one another.  The whole table is checked before

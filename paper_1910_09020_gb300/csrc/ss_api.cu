@@ -752,9 +752,9 @@ int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
 }
 
 extern "C++" {
-// One segment's launch (the segment checked by the caller).
-static int segment_launch(ss_ctx *ctx, int format, const ss_segment &s,
-                          cudaStream_t st)
+// One segment's launch in the pair-major packed format (the segment checked
+// by the caller).
+static int segment_launch(ss_ctx *ctx, const ss_segment &s, cudaStream_t st)
 {
     if (s.m == 0) {
         // nothing to route: every pair accepted with 0 obstacles
@@ -762,10 +762,6 @@ static int segment_launch(ss_ctx *ctx, int format, const ss_segment &s,
         SS_CUDA(cudaMemsetAsync(s.out_obstacles, 0, (size_t)s.n * 4, st));
         return SS_OK;
     }
-    if (format == SS_FMT_SLICED2)
-        return filter_sliced(ctx, (const uint32_t *)s.reads,
-                             (const uint32_t *)s.refs, s.m, s.e, s.n,
-                             s.out_accept, s.out_obstacles, st);
     SS_CUDA(ssk::launch_rw_uniform(s.e, (const uint32_t *)s.reads,
                                    (const uint32_t *)s.refs, s.n, s.m,
                                    s.out_accept, s.out_obstacles,
@@ -774,15 +770,43 @@ static int segment_launch(ss_ctx *ctx, int format, const ss_segment &s,
     return SS_OK;
 }
 
+// The segments' launches, side by side on the lanes in the given order;
+// over the sliced layout, segments of one threshold share a launch (up to
+// kSlicedMaxSegments each), placed where the first of them stands.
 static int segments_launch(ss_ctx *ctx, int format,
                            const std::vector<ss_segment> &segs,
                            cudaStream_t st)
 {
     Lanes lanes(ctx, st);
     cudaStream_t ls;
+    int job = 0;
+    if (format != SS_FMT_SLICED2) {
+        for (const ss_segment &sg : segs) {
+            SS_CUDA(lanes.stream(job++, ls));
+            SS_TRY(segment_launch(ctx, sg, ls));
+        }
+        SS_CUDA(lanes.join());
+        return SS_OK;
+    }
+    std::vector<bool> done(segs.size(), false);
     for (size_t i = 0; i < segs.size(); ++i) {
-        SS_CUDA(lanes.stream((int)i, ls));
-        SS_TRY(segment_launch(ctx, format, segs[i], ls));
+        if (done[i])
+            continue;
+        ssk::SlicedSegment grp[ssk::kSlicedMaxSegments];
+        int k = 0;
+        for (size_t j = i; j < segs.size() && k < ssk::kSlicedMaxSegments;
+             ++j) {
+            if (done[j] || segs[j].e != segs[i].e)
+                continue;
+            const ss_segment &sg = segs[j];
+            grp[k++] = ssk::SlicedSegment{
+                (const uint32_t *)sg.reads, (const uint32_t *)sg.refs, sg.n,
+                sg.m, sg.out_accept, sg.out_obstacles};
+            done[j] = true;
+        }
+        SS_CUDA(lanes.stream(job++, ls));
+        SS_CUDA(ssk::launch_sliced_segments(grp, k, segs[i].e, ls));
+        ctx->counters.launches += 1;
     }
     SS_CUDA(lanes.join());
     return SS_OK;

@@ -31,6 +31,19 @@ cudaError_t launch_pack_sliced(const uint8_t *ascii, int64_t n, int32_t m,
 cudaError_t launch_sliced(const uint32_t *reads, const uint32_t *refs,
                           int64_t n, int32_t m, int32_t E, uint8_t *acc,
                           int32_t *obs, cudaStream_t st);
+// The plain launch over up to kSlicedMaxSegments batches of one threshold E
+// (each its own n >= 1 and m >= 0, sliced layout): one grid, the CTAs of
+// segment s after those of segment s - 1.
+struct SlicedSegment {
+    const uint32_t *reads, *refs;
+    int64_t n;
+    int32_t m;
+    uint8_t *acc;
+    int32_t *obs;
+};
+constexpr int kSlicedMaxSegments = 8;
+cudaError_t launch_sliced_segments(const SlicedSegment *segs, int nseg,
+                                   int32_t E, cudaStream_t st);
 // The sub-maze mode (sub-mazes of t columns, at most y segments each) over
 // the bit-sliced layout, 0 <= E <= kSlicedMaxE.
 cudaError_t launch_sliced_submaze(const uint32_t *reads, const uint32_t *refs,

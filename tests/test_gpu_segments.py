@@ -81,6 +81,31 @@ def test_segments_match_oracle(F, fmt):
     check(outs, want, "replay")
 
 
+def test_segments_of_one_threshold_share_launches(F):
+    """Eleven segments at E = 4 (lengths 1..400, some n not a multiple of
+    32) and two at E = 9: the E = 4 ones go in two launches (8 + 3), every
+    pair against the oracle."""
+    torch = torch_cuda()
+    shapes = [(1, 4, 70), (3, 4, 33), (16, 4, 64), (17, 4, 1), (64, 4, 500),
+              (99, 4, 1031), (100, 9, 2048), (150, 4, 777), (200, 4, 96),
+              (250, 9, 129), (255, 4, 4099), (256, 4, 31), (400, 4, 640)]
+    segs, want = [], []
+    for i, (m, e, n) in enumerate(shapes):
+        reads, refs = synth.pairs_fixed(760 + i, 0, n, m,
+                                        synth.rate_recipe(0.1))
+        q = F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n)
+        r = F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n)
+        segs.append((q, r, m, e, n))
+        want.append(oracle_fixed(reads, refs, e))
+    F.sync()
+    before = F.counters().launches
+    outs = F.filter_segments(segs, graph=False, sync=True)
+    assert F.counters().launches == before + 3
+    for k, ((acc, obs), (oacc, oobs)) in enumerate(zip(outs, want)):
+        assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                    f"segment {k} {shapes[k]}")
+
+
 def test_segments_argument_errors(F):
     """The whole table is checked before anything runs: an unsupported or
     invalid segment anywhere leaves every output untouched."""
