@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(kRwThreads) k_unequal_tile(
     const int t = threadIdx.x;
     if (t < 32)
         s_cnt[t] = 0;
+    // the counts zero before any thread of the tile adds to them
+    __syncthreads();
     int bad = 0;
     const int64_t ntiles = (a.n + kRwThreads - 1) / kRwThreads;
     for (int j = 0; j < kUqGroup; ++j) {
