@@ -813,10 +813,13 @@ def run_submaze(F, sq, sr, pq, pr, n, acc, obs, t=8, y=3) -> dict:
 def run_unequal(F, n=2_000_000) -> dict:
     """Reads of 100 bp against reference windows of 92..116 bp (the read
     inside random flanks, or the window cut short): the filter for pairs of
-    different lengths, one launch per E."""
+    different lengths, one launch per E over the pair-major layout; and the
+    same pairs bucketed by window length into 25 uniform segments over the
+    bit-sliced layout, one segmented call per E (results checked equal).
+    Beside them, the plain sliced launch on 2M pairs of equal length."""
     import torch
 
-    from paper_1910_09020_gb300 import synth
+    from paper_1910_09020_gb300 import binding, synth
     data = synth.pairs_unequal(SEED + 7, 0, n, M, synth.SHORT_POISSON, -8, 16)
     reads, ro, rl, refs, fo, fl = data
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -836,13 +839,38 @@ def run_unequal(F, n=2_000_000) -> dict:
     r, fo_d = packed(refs, fo, fl)
     ql = torch.from_numpy(rl.astype(np.int32)).to(dev)
     rlen = torch.from_numpy(fl.astype(np.int32)).to(dev)
+    # the bit-sliced segments: pairs grouped by window length (host-side
+    # bucketing of the generator's output, outside the timed region)
+    order = np.argsort(fl, kind="stable")
+    rd = reads.reshape(n, M)
+    segs = []
+    for L in np.unique(fl):
+        idx = order[fl[order] == L]
+        rows = refs[(fo[idx][:, None] + np.arange(L)[None, :]).reshape(-1)]
+        sq = F.pack_sliced(torch.from_numpy(
+            np.ascontiguousarray(rd[idx]).reshape(-1)).to(dev), m=M,
+            n=len(idx))
+        sr = F.pack_sliced(torch.from_numpy(rows).to(dev), m=int(L),
+                           n=len(idx))
+        a_ = torch.empty(len(idx), dtype=torch.uint8, device=dev)
+        o_ = torch.empty(len(idx), dtype=torch.int32, device=dev)
+        segs.append([sq, sr, (M, int(L)), 0, len(idx), (a_, o_),
+                     torch.from_numpy(idx).to(dev)])
+    # equal-length pairs of the same recipe for the plain sliced launch
+    er, ef = synth.pairs_fixed(SEED + 8, 0, n, M, synth.SHORT_POISSON)
+    eq_q = F.pack_sliced(torch.from_numpy(er.reshape(-1)).to(dev), m=M, n=n)
+    eq_r = F.pack_sliced(torch.from_numpy(ef.reshape(-1)).to(dev), m=M, n=n)
+    del er, ef
     F.sync()
     # algorithmic bytes per launch: both packed sequences, their word
     # offsets and lengths (8 + 4 B each), and the two results
     words = int(((rl.astype(np.int64) + 15) // 16).sum()
                 + ((fl.astype(np.int64) + 15) // 16).sum())
     nbytes = 4 * words + n * (2 * 12 + 5)
+    sliced_bytes = int(n * ((M + 3) // 4) + ((fl.astype(np.int64) + 3)
+                                             // 4).sum() + 5 * n)
     out = []
+    same = True
     for E in (2, 6, 10):
         F.filter_unequal(q, qo, ql, r, fo_d, rlen, e=E)
         a, b = _ev(), _ev()
@@ -854,14 +882,44 @@ def run_unequal(F, n=2_000_000) -> dict:
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
         gbs = nbytes / (ms * 1e-3) / 1e9
+        # the segment table built once and handed to the C call directly
+        # (what a caller of the library does; the Python wrapper would add
+        # its per-segment checks to every call)
+        arr = (binding.Segment * len(segs))()
+        for i, sg in enumerate(segs):
+            arr[i] = binding.Segment(sg[0].data_ptr(), sg[1].data_ptr(),
+                                     sg[4], M, E, sg[5][0].data_ptr(),
+                                     sg[5][1].data_ptr(), sg[2][1])
+        stream = torch.cuda.current_stream().cuda_stream
+
+        def seg_call():
+            rc = binding.ss_filter_segments(F.ctx, arr, len(segs),
+                                            binding.SS_FMT_SLICED2, 0, stream)
+            assert rc == binding.SS_OK, rc
+        ms_s = _time_ms(seg_call, reps, F.sync)
+        for sg in segs:  # back to the batch's order
+            same &= bool(torch.equal(sg[5][0], acc[sg[6]]) and
+                         torch.equal(sg[5][1], obs[sg[6]]))
+        ms_p = _time_ms(lambda: F.filter(eq_q, eq_r, m=M, e=E, n=n,
+                                         fmt=binding.SS_FMT_SLICED2),
+                        reps, F.sync)
         out.append({"E": E, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
                     "hbm_gbs": gbs,
                     "hbm_frac": gbs / measured_peaks()["hbm_gbs"],
-                    "accept_rate": float(acc.float().mean().item())})
+                    "accept_rate": float(acc.float().mean().item()),
+                    "sliced_segments_ms": ms_s,
+                    "sliced_segments_hbm_frac":
+                        sliced_bytes / (ms_s * 1e-3) / 1e9
+                        / measured_peaks()["hbm_gbs"],
+                    "plain_sliced_equal_ms": ms_p,
+                    "sliced_segments_over_plain_sliced": ms_s / ms_p})
     F.sync()
     return {"workload": f"{n // 1000000}M reads of {M} bp vs reference "
                         f"windows of {M - 8}..{M + 16} bp (flanked or cut)",
-            "pairs": n, "per_E": out}
+            "pairs": n, "per_E": out,
+            "sliced_segments": f"{len(segs)} segments by window length, "
+                               "one ss_filter_segments call per E",
+            "results_identical": same}
 
 
 def run_compaction(F, pq, pr, acc, n, E) -> dict:

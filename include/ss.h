@@ -180,27 +180,33 @@ int ss_filter_sweep(ss_ctx *ctx, const void *reads, const void *refs,
                     int64_t n, void *stream, uint8_t *out_accept,
                     int32_t *out_obstacles);
 
-/* One batch of a segmented call: n fixed-stride pairs of uniform length m
- * filtered at threshold e (Section 2.4), in the call's format. */
+/* One batch of a segmented call: n fixed-stride pairs, reads of m bases
+ * against references of m_ref bases (0: m, equal lengths), filtered at
+ * threshold e (Section 2.4), in the call's format.  When m_ref differs
+ * from m, the maze has one column per reference base and the cells where a
+ * diagonal reads no base of the read are free, not obstacles (Section
+ * 2.4's correction of the leading and trailing obstacles). */
 typedef struct ss_segment {
     const void *reads;       /* device; SS_FMT_SLICED2: 16-byte aligned      */
-    const void *refs;        /* device; same layout as reads                 */
+    const void *refs;        /* device; same layout as reads, m_ref bases    */
     int64_t n;               /* pairs (>= 0; 0: the segment is skipped)      */
-    int32_t m;               /* bases per sequence (>= 0)                    */
+    int32_t m;               /* bases per read (>= 0)                        */
     int32_t e;               /* threshold (>= 0)                             */
     uint8_t *out_accept;     /* device uint8[n]: 1 if count <= e             */
     int32_t *out_obstacles;  /* device int32[n]: min(count, e + 1)           */
+    int32_t m_ref;           /* bases per reference (>= 0; 0: m)             */
 } ss_segment;
 
 /* Several uniform batches (segments, e.g. reads of 150 and of 250 bases,
  * each with its own threshold) filtered by one call: a batch mixing lengths
  * and thresholds, bucketed by the caller into uniform segments.  format is
- * SS_FMT_SLICED2 (every e <= SS_SLICED_MAX_E) or SS_FMT_PACKED2 (fixed
- * stride ceil(m/16) words per sequence; m <= SS_PLAIN_MAX_M and e <=
- * SS_PLAIN_MAX_E).  Every segment's launch is independent of the others:
+ * SS_FMT_SLICED2 (every e <= SS_SLICED_MAX_E; reads and references each in
+ * the layout of their own length) or SS_FMT_PACKED2 (fixed stride
+ * ceil(m/16) words per sequence; equal lengths, m <= SS_PLAIN_MAX_M and e
+ * <= SS_PLAIN_MAX_E).  Every segment's launch is independent of the others:
  * they run side by side on the context's streams, the costliest first, so
  * that the GPU does not drain between them; over SS_FMT_SLICED2, segments
- * of one threshold share a launch (up to 8 per launch).  Unless flags holds
+ * of one threshold share a launch (up to 32 per launch).  Unless flags holds
  * SS_FLAG_NO_GRAPH, the launches are captured once per distinct segment
  * table (pointers and sizes) as a CUDA graph and replayed.  The segments'
  * outputs must not overlap one another.  The whole table is checked before

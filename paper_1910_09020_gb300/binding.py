@@ -87,7 +87,7 @@ class Segment(ctypes.Structure):
     _fields_ = [("reads", ctypes.c_void_p), ("refs", ctypes.c_void_p),
                 ("n", ctypes.c_int64), ("m", ctypes.c_int32),
                 ("e", ctypes.c_int32), ("out_accept", ctypes.c_void_p),
-                ("out_obstacles", ctypes.c_void_p)]
+                ("out_obstacles", ctypes.c_void_p), ("m_ref", ctypes.c_int32)]
 
 
 class Counters(ctypes.Structure):
@@ -470,27 +470,29 @@ class Filter:
                         graph: bool = True, stream=None, sync: bool = False):
         """Uniform batches filtered by one call (ss_filter_segments).
         ``segments``: (reads, refs, m, e, n) tuples of device tensors in the
-        format ``fmt``; returns one (accept uint8[n], obstacles int32[n])
-        pair of new device tensors per segment, in the given order.  A
-        6-tuple (reads, refs, m, e, n, (out_accept, out_obstacles)) writes
-        to the given tensors instead."""
+        format ``fmt``, m the length of reads and references or a pair
+        (read length, reference length); returns one (accept uint8[n],
+        obstacles int32[n]) pair of new device tensors per segment, in the
+        given order.  A 6-tuple (reads, refs, m, e, n, (out_accept,
+        out_obstacles)) writes to the given tensors instead."""
         import torch
         d = self.device
         arr = (Segment * max(len(segments), 1))()
         outs = []
         for i, sg in enumerate(segments):
             reads, refs, m, e, n = sg[:5]
-            m, e, n = int(m), int(e), int(n)
+            m, m_ref = (m, m) if isinstance(m, int) else m
+            m, m_ref, e, n = int(m), int(m_ref), int(e), int(n)
             if len(sg) > 5:
                 acc, obs = sg[5]
             else:
                 acc = torch.empty(n, dtype=torch.uint8, device=reads.device)
                 obs = torch.empty(n, dtype=torch.int32, device=reads.device)
-            seq = _seq_bytes(fmt, n, m)
-            arr[i] = Segment(_dptr(reads, d, "reads", seq) or None,
-                             _dptr(refs, d, "refs", seq) or None, n, m, e,
-                             _dptr(acc, d, "out_accept", n) or None,
-                             _dptr(obs, d, "out_obstacles", 4 * n) or None)
+            arr[i] = Segment(
+                _dptr(reads, d, "reads", _seq_bytes(fmt, n, m)) or None,
+                _dptr(refs, d, "refs", _seq_bytes(fmt, n, m_ref)) or None,
+                n, m, e, _dptr(acc, d, "out_accept", n) or None,
+                _dptr(obs, d, "out_obstacles", 4 * n) or None, m_ref)
             outs.append((acc, obs))
         rc = ss_filter_segments(self.ctx, arr if segments else None,
                                 len(segments), fmt,

@@ -772,7 +772,9 @@ static int segment_launch(ss_ctx *ctx, const ss_segment &s, cudaStream_t st)
 
 // The segments' launches, side by side on the lanes in the given order;
 // over the sliced layout, segments of one threshold share a launch (up to
-// kSlicedMaxSegments each), placed where the first of them stands.
+// kSlicedMaxSegments each, equal and different lengths apart), placed
+// where the first of them stands.  m_ref is set (the caller's 0 replaced
+// by m).
 static int segments_launch(ss_ctx *ctx, int format,
                            const std::vector<ss_segment> &segs,
                            cudaStream_t st)
@@ -794,18 +796,22 @@ static int segments_launch(ss_ctx *ctx, int format,
             continue;
         ssk::SlicedSegment grp[ssk::kSlicedMaxSegments];
         int k = 0;
+        const bool free_ends = segs[i].m_ref != segs[i].m;
         for (size_t j = i; j < segs.size() && k < ssk::kSlicedMaxSegments;
              ++j) {
-            if (done[j] || segs[j].e != segs[i].e)
+            if (done[j] || segs[j].e != segs[i].e ||
+                (segs[j].m_ref != segs[j].m) != free_ends)
                 continue;
             const ss_segment &sg = segs[j];
             grp[k++] = ssk::SlicedSegment{
                 (const uint32_t *)sg.reads, (const uint32_t *)sg.refs, sg.n,
-                sg.m, sg.out_accept, sg.out_obstacles};
+                sg.m, sg.out_accept, sg.out_obstacles, sg.m_ref};
             done[j] = true;
         }
         SS_CUDA(lanes.stream(job++, ls));
-        SS_CUDA(ssk::launch_sliced_segments(grp, k, segs[i].e, ls));
+        SS_CUDA(free_ends
+                    ? ssk::launch_sliced_free_segments(grp, k, segs[i].e, ls)
+                    : ssk::launch_sliced_segments(grp, k, segs[i].e, ls));
         ctx->counters.launches += 1;
     }
     SS_CUDA(lanes.join());
@@ -817,8 +823,8 @@ static int segments_launch(ss_ctx *ctx, int format,
 // rate, in units where the two rates are 6.8 and 20 per unit time.
 static double segment_cost(const ss_segment &s)
 {
-    const double bytes = 2.0 * ((s.m + 3) / 4) + 5.0;
-    const double ops = (double)s.m * (6.0 * s.e + 3.0) / 32.0;
+    const double bytes = (s.m + 3) / 4 + (s.m_ref + 3) / 4 + 5.0;
+    const double ops = (double)s.m_ref * (6.0 * s.e + 3.0) / 32.0;
     return (double)s.n * std::max(bytes / 6.8, ops / 20.0);
 }
 }  // extern "C++"
@@ -837,20 +843,31 @@ int ss_filter_segments(ss_ctx *ctx, const ss_segment *segs, int n_seg,
     bool unsupported = false;
     for (int i = 0; i < n_seg; ++i) {
         const ss_segment &s = segs[i];
-        if (s.n < 0 || s.m < 0 || s.e < 0)
+        if (s.n < 0 || s.m < 0 || s.e < 0 || s.m_ref < 0)
             return SS_ERR_INVALID_ARG;
         if (s.n == 0)
             continue;
         if (!s.reads || !s.refs || !s.out_accept || !s.out_obstacles)
             return SS_ERR_INVALID_ARG;
+        // the fields alone (the key of the graph cache compares bytes)
+        ss_segment w;
+        std::memset(&w, 0, sizeof w);
+        w.reads = s.reads;
+        w.refs = s.refs;
+        w.n = s.n;
+        w.m = s.m;
+        w.e = s.e;
+        w.out_accept = s.out_accept;
+        w.out_obstacles = s.out_obstacles;
+        w.m_ref = s.m_ref ? s.m_ref : s.m;
         if (format == SS_FMT_SLICED2) {
             if ((((uintptr_t)s.reads) | ((uintptr_t)s.refs)) & 15)
                 return SS_ERR_INVALID_ARG;
             unsupported |= s.e > ssk::kSlicedMaxE;
         } else {
-            unsupported |= s.m > 0 && !plain_ok(s.m, s.e);
+            unsupported |= w.m_ref != w.m || (s.m > 0 && !plain_ok(s.m, s.e));
         }
-        work.push_back(s);
+        work.push_back(w);
         pairs += s.n;
     }
     if (unsupported)

@@ -37,13 +37,20 @@ cudaError_t launch_sliced(const uint32_t *reads, const uint32_t *refs,
 struct SlicedSegment {
     const uint32_t *reads, *refs;
     int64_t n;
-    int32_t m;
+    int32_t m;       // read length (and reference length, equal lengths)
     uint8_t *acc;
     int32_t *obs;
+    int32_t m_ref;   // reference length (launch_sliced_free_segments)
 };
-constexpr int kSlicedMaxSegments = 8;
+constexpr int kSlicedMaxSegments = 32;  // 2 KB of launch parameters
 cudaError_t launch_sliced_segments(const SlicedSegment *segs, int nseg,
                                    int32_t E, cudaStream_t st);
+// The same over batches whose reads and references differ in length
+// (m != m_ref, both >= 0; reads in the sliced layout of m bases, refs of
+// m_ref): Section 2.4's correction, a cell whose query base lies outside
+// the read is free.
+cudaError_t launch_sliced_free_segments(const SlicedSegment *segs, int nseg,
+                                        int32_t E, cudaStream_t st);
 // The sub-maze mode (sub-mazes of t columns, at most y segments each) over
 // the bit-sliced layout, 0 <= E <= kSlicedMaxE.
 cudaError_t launch_sliced_submaze(const uint32_t *reads, const uint32_t *refs,

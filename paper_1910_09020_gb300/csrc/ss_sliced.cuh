@@ -190,44 +190,67 @@ struct SlicedCount<E, true> {
     }
 };
 
-// The edge blocks of a walk of m columns: a block k is an edge block when
-// one of its columns has a diagonal that reads a query base outside 0..m-1
-// (Eq. 1 case 4): k < kl (j0 < E) or k >= kr (j0 + 3 + E >= m).  Their
-// validity words -- all ones or zero per window word, the same for every
-// pair -- are rows of a table: row k for k < kl, row kl + k - max(kr, kl)
-// for k >= kr.  At most 2 NBH + 2 rows.
+// The edge blocks of a walk over mR reference columns against a query of
+// mQ bases (mQ = mR = m for pairs of equal length): a block k is an edge
+// block when one of its columns has a diagonal that reads a query base
+// outside 0..mQ-1 (Eq. 1 case 4): k < kl (j0 < E) or k >= kr (j0 + 3 + E >=
+// mQ).  Their validity words -- all ones or zero per window word, the same
+// for every pair -- are rows of a table: row k for k < kl, row kl +
+// min(k, kz) - kr for k >= kr, where from block kz on the whole window lies
+// past the query (every such block has the same row; only a reference
+// longer than the query reaches it).  At most 2 NBH + 1 rows with equal
+// lengths, 3 NBH + 2 otherwise.
 template <int E>
 struct SlicedEdges {
     static constexpr int kRows = 2 * SlicedShape<E>::NBH + 2;
-    int nb, kl, kr;
-    SS_HD SlicedEdges(int m)
+    static constexpr int kRowsFree = 3 * SlicedShape<E>::NBH + 3;
+    int nb, kl, kr, kz;
+    SS_HD explicit SlicedEdges(int m) : SlicedEdges(m, m) {}
+    SS_HD SlicedEdges(int mQ, int mR)
     {
-        nb = (m + 3) >> 2;
+        nb = (mR + 3) >> 2;
         kl = imin(nb, SlicedShape<E>::NBH);
-        // first k with 4k + 3 + E >= m
-        const int r = m - 3 - E;
-        kr = imax(kl, r <= 0 ? 0 : (r + 3) >> 2);
+        // first k with 4k + 3 + E >= mQ (at most nb: a query longer than
+        // the reference may leave no right edge)
+        const int r = mQ - 3 - E;
+        kr = imin(nb, imax(kl, r <= 0 ? 0 : (r + 3) >> 2));
+        // first k whose window (query bases 4k - 4 NBH ..) starts past the
+        // query: at least nb with equal lengths
+        kz = ((mQ + 3) >> 2) + SlicedShape<E>::NBH;
     }
-    SS_HD int rows() const { return kl + (nb - kr); }
-    SS_HD int row_of(int k) const { return k < kl ? k : kl + (k - kr); }
+    SS_HD int rows() const { return kl + (imin(nb, kz + 1) - kr); }
+    SS_HD int row_of(int k) const
+    {
+        return k < kl ? k : kl + (imin(k, kz) - kr);
+    }
     SS_HD int block_of(int row) const
     {
         return row < kl ? row : kr + (row - kl);
     }
-    // validity word w of the window of block k
-    SS_HD static uint32_t valid(int k, int w, int m)
+    // validity word w of the window of block k (mQ: the query's bases)
+    SS_HD static uint32_t valid(int k, int w, int mQ)
     {
-        return (uint32_t)(4 * k - 4 * SlicedShape<E>::NBH + w) < (uint32_t)m
+        return (uint32_t)(4 * k - 4 * SlicedShape<E>::NBH + w) < (uint32_t)mQ
                    ? 0xffffffffu
                    : 0u;
+    }
+    // word w of block k's table row: with equal lengths the validity word
+    // (a cell outside the query is an obstacle), with different lengths
+    // its complement (such a cell is free: Section 2.4's correction)
+    SS_HD static uint32_t entry(int k, int w, int mQ, bool free_ends)
+    {
+        const uint32_t v = valid(k, w, mQ);
+        return free_ends ? ~v : v;
     }
 };
 
 // Column j0 + u of a block.  ql/qh: the window's query words (word w =
 // query base j0 - 4 NBH + w); rl/rh: the reference bases j0..j0+3.  With
-// EDGE, vw holds the block's validity words: a diagonal that reads a query
-// base outside 0..m-1 meets an obstacle (Eq. 1 case 4).  one holds 1 (a
-// run-time value: S_d * one + z is a multiply-add on the FMA pipe).
+// EDGE, vw holds the block's table row: a diagonal that reads a query base
+// outside 0..mQ-1 meets an obstacle (Eq. 1 case 4; vw the validity words)
+// or, with FREE (the lengths differ), a free cell (vw their complement:
+// S_d = (S_d | z) & (equal | outside)).  one holds 1 (a run-time value:
+// S_d * one + z is a multiply-add on the FMA pipe).
 // What a column adds to the greedy, by mode.  The plain walk: nothing.
 struct SlicedPlain {
     template <int N>
@@ -302,7 +325,7 @@ struct SlicedSubMaze {
 // The window may be wider than E needs (NW blocks either side, NW >= NBH):
 // word w is then query base j0 - 4 NW + w.
 template <int E, bool EDGE, int U, int NW = SlicedShape<E>::NBH,
-          class Mode = SlicedPlain>
+          class Mode = SlicedPlain, bool FREE = false>
 SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
                          SlicedCount<E> &cnt,
                          const uint32_t (&ql)[4 * (2 * NW + 1)],
@@ -318,11 +341,11 @@ SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
     for (int d = 0; d < Sh::ND; ++d) {
         const int w = 4 * NW - E + U + d;
         // (S_d | z) & ~(Q lo ^ R lo) & ~(Q hi ^ R hi)
-        uint32_t s = S[d] * one + z;
-        s = lop3<0x90>(s, ql[w], rl[U]);
+        const uint32_t t = S[d] * one + z;
+        uint32_t s = lop3<0x90>(t, ql[w], rl[U]);
         s = lop3<0x90>(s, qh[w], rh[U]);
         if (EDGE)
-            s &= vw[w];
+            s = FREE ? lop3<0xF8>(s, t, vw[w]) : (s & vw[w]);  // s | (t & vw)
         S[d] = s;
     }
     // the pairs with every row dead: count this column's obstacle,
@@ -335,7 +358,7 @@ SS_HD void sliced_column(uint32_t (&S)[2 * E + 1], uint32_t &z,
 
 // The block's columns j0 + u for u < live (1..4; below 4 only in the last
 // block).
-template <int E, bool EDGE, class Mode>
+template <int E, bool EDGE, class Mode, bool FREE = false>
 SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
                         SlicedCount<E> &cnt,
                         const uint32_t (&ql)[SlicedShape<E>::WW],
@@ -345,48 +368,50 @@ SS_HD void sliced_block(uint32_t (&S)[2 * E + 1], uint32_t &z,
                         Mode &mode, int j0)
 {
     constexpr int NW = SlicedShape<E>::NBH;
+    auto col = [&](auto u) {
+        sliced_column<E, EDGE, decltype(u)::value, NW, Mode, FREE>(
+            S, z, cnt, ql, qh, rl, rh, vw, one, mode, j0);
+    };
+    using std::integral_constant;
     if (live >= 4) {
-        sliced_column<E, EDGE, 0, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                      mode, j0);
-        sliced_column<E, EDGE, 1, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                      mode, j0);
-        sliced_column<E, EDGE, 2, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                      mode, j0);
-        sliced_column<E, EDGE, 3, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                      mode, j0);
+        col(integral_constant<int, 0>{});
+        col(integral_constant<int, 1>{});
+        col(integral_constant<int, 2>{});
+        col(integral_constant<int, 3>{});
     } else {
-        sliced_column<E, EDGE, 0, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                      mode, j0);
+        col(integral_constant<int, 0>{});
         if (live > 1)
-            sliced_column<E, EDGE, 1, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                          mode, j0);
+            col(integral_constant<int, 1>{});
         if (live > 2)
-            sliced_column<E, EDGE, 2, NW>(S, z, cnt, ql, qh, rl, rh, vw, one,
-                                          mode, j0);
+            col(integral_constant<int, 2>{});
     }
 }
 
-// Walk the 32 pairs of one group over all m columns; on return cnt holds
-// each pair's min(count, E+1).  pad: pairs that do not exist (the last
-// group's), counted as past E so that the group can stop early.
-// src.query(blk, nb, lo, hi) / src.ref(blk, lo, hi) load the four words of
-// each plane of a block (zero for a query block outside 0..nb-1);
-// src.prefetch(qblk, rblk, nb) asks for those of query block qblk and
-// reference block rblk ahead of their loads (a hint, no result); vtab:
-// the validity table of SlicedEdges<E>(m), WW words per row.
-template <int E, class Src, class Mode = SlicedPlain>
-SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
-                       SlicedCount<E> &cnt, const uint32_t *vtab,
-                       uint32_t one, Mode mode = Mode())
+// Walk the 32 pairs of one group over all mR reference columns against
+// queries of mQ bases (FREE: mQ != mR, Section 2.4's correction; else mQ =
+// mR); on return cnt holds each pair's min(count, E+1).  pad: pairs that
+// do not exist (the last group's), counted as past E so that the group can
+// stop early.  src.query(blk, nb, lo, hi) / src.ref(blk, lo, hi) load the
+// four words of each plane of a block (zero for a query block outside
+// 0..nb-1); src.prefetch(qblk, rblk, nbq, nbr) asks for those of query
+// block qblk (if below nbq) and reference block rblk (if below nbr) ahead
+// of their loads (a hint, no result);
+// vtab: the table of SlicedEdges<E>(mQ, mR), WW words per row (entry()).
+template <int E, bool FREE, class Src, class Mode = SlicedPlain>
+SS_HD void sliced_walk2(const Src &src, int mQ, int mR, uint32_t pad,
+                        SlicedCount<E> &cnt, const uint32_t *vtab,
+                        uint32_t one, Mode mode = Mode())
 {
     using Sh = SlicedShape<E>;
-    const SlicedEdges<E> ed(m);
-    const int nb = ed.nb;
+    const SlicedEdges<E> ed(mQ, mR);
+    const int nb = ed.nb;                       // reference blocks
+    const int nbq = FREE ? (mQ + 3) >> 2 : nb;  // query blocks
+    const int m = mR;
     uint32_t ql[Sh::WW], qh[Sh::WW];
 #pragma unroll
     for (int b = 0; b < 2 * Sh::NBH + 1; ++b) {
         uint32_t lo[4], hi[4];
-        src.query(b - Sh::NBH, nb, lo, hi);
+        src.query(b - Sh::NBH, nbq, lo, hi);
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
             ql[4 * b + x] = lo[x];
@@ -414,20 +439,21 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
         uint32_t nql[4], nqh[4], nrl[4], nrh[4];
         if constexpr (kHold) {
             // the next block's words, loaded before this block is walked
-            src.query(k + Sh::NBH + 1, nb, nql, nqh);
+            src.query(k + Sh::NBH + 1, nbq, nql, nqh);
             if (k + 1 < nb)
                 src.ref(k + 1, nrl, nrh);
         } else {
-            src.prefetch(k + Sh::NBH + 1, k + 1, nb);
+            src.prefetch(k + Sh::NBH + 1, k + 1, nbq, nb);
         }
         const int live = imin(4, m - 4 * k);
         if (k < ed.kl || k >= ed.kr)
-            sliced_block<E, true>(S, z, cnt, ql, qh, rl, rh,
-                                  vtab + ed.row_of(k) * Sh::WW, live, one,
-                                  mode, 4 * k);
+            sliced_block<E, true, Mode, FREE>(S, z, cnt, ql, qh, rl, rh,
+                                              vtab + ed.row_of(k) * Sh::WW,
+                                              live, one, mode, 4 * k);
         else
-            sliced_block<E, false>(S, z, cnt, ql, qh, rl, rh, nullptr, live,
-                                   one, mode, 4 * k);
+            sliced_block<E, false, Mode, FREE>(S, z, cnt, ql, qh, rl, rh,
+                                               nullptr, live, one, mode,
+                                               4 * k);
         if (cnt.done() == 0xffffffffu)
             break;  // every pair of the group is past E
 #pragma unroll
@@ -436,7 +462,7 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
             qh[w] = qh[w + 4];
         }
         if constexpr (!kHold) {
-            src.query(k + Sh::NBH + 1, nb, nql, nqh);
+            src.query(k + Sh::NBH + 1, nbq, nql, nqh);
             if (k + 1 < nb)
                 src.ref(k + 1, nrl, nrh);
         }
@@ -448,6 +474,15 @@ SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
             rh[x] = nrh[x];
         }
     }
+}
+
+// The walk of pairs of equal length m.
+template <int E, class Src, class Mode = SlicedPlain>
+SS_HD void sliced_walk(const Src &src, int m, uint32_t pad,
+                       SlicedCount<E> &cnt, const uint32_t *vtab,
+                       uint32_t one, Mode mode = Mode())
+{
+    sliced_walk2<E, false>(src, m, m, pad, cnt, vtab, one, mode);
 }
 
 // min(count, E+1) of pair i of the group.
@@ -684,13 +719,14 @@ struct SlicedSrc {
         load(r, blk, lo, hi);
     }
     // both planes of a block are 32 contiguous bytes: one L1 line each
-    __device__ __forceinline__ void prefetch(int qblk, int rblk, int nb) const
+    __device__ __forceinline__ void prefetch(int qblk, int rblk, int nbq,
+                                             int nbr) const
     {
-        if (qblk >= 0 && qblk < nb)
+        if (qblk >= 0 && qblk < nbq)
             asm volatile("prefetch.global.L1 [%0];"
                          :
                          : "l"(q + ((int64_t)qblk * G + g) * 2));
-        if (rblk < nb)
+        if (rblk < nbr)
             asm volatile("prefetch.global.L1 [%0];"
                          :
                          : "l"(r + ((int64_t)rblk * G + g) * 2));
@@ -713,6 +749,19 @@ __device__ __forceinline__ void sliced_fill_edges(uint32_t *vtab, int m)
     const Ed ed(m);
     for (int i = threadIdx.x; i < ed.rows() * WW; i += kSlicedThreads)
         vtab[i] = Ed::valid(ed.block_of(i / WW), i % WW, m);
+}
+
+// The table of a walk over mR reference columns against queries of mQ
+// bases, with the free-end rule when they differ (SlicedEdges::entry).
+template <int E>
+__device__ __forceinline__ void sliced_fill_edges2(uint32_t *vtab, int mQ,
+                                                   int mR)
+{
+    using Ed = SlicedEdges<E>;
+    constexpr int WW = SlicedShape<E>::WW;
+    const Ed ed(mQ, mR);
+    for (int i = threadIdx.x; i < ed.rows() * WW; i += kSlicedThreads)
+        vtab[i] = Ed::entry(ed.block_of(i / WW), i % WW, mQ, mQ != mR);
 }
 
 // Results of the group's np pairs starting at pair p0: accept (count <= E,

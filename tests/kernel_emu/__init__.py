@@ -72,5 +72,7 @@ def load():
                                        ctypes.c_int, P, P]
     lib.emu_sliced_set.argtypes = [P, P, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_int, P, P]
+    lib.emu_sliced_free.argtypes = [P, P, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, P, P]
     _lib = lib
     return lib

@@ -186,7 +186,7 @@ struct HostSliced {
     {
         load(r, blk, lo, hi);
     }
-    void prefetch(int, int, int) const {}
+    void prefetch(int, int, int, int) const {}
 };
 
 template <int E>
@@ -212,6 +212,46 @@ void sliced_groups(const uint32_t *q, const uint32_t *r, int64_t n, int m,
             acc[32 * g + i] = (uint8_t)(((~cnt.done()) >> i) & 1u);
         }
     }
+}
+
+// Reads of mQ bases against references of mR (mQ != mR) over the sliced
+// layout, every group, with the free-end rule.
+template <int E>
+void sliced_free_groups(const uint32_t *q, const uint32_t *r, int64_t n,
+                        int mQ, int mR, uint8_t *acc, int32_t *obs)
+{
+    const int64_t G = (n + 31) / 32;
+    using Ed = SlicedEdges<E>;
+    constexpr int WW = SlicedShape<E>::WW;
+    const Ed ed(mQ, mR);
+    std::vector<uint32_t> vtab(Ed::kRowsFree * WW);
+    for (int i = 0; i < ed.rows() * WW; ++i)
+        vtab[i] = Ed::entry(ed.block_of(i / WW), i % WW, mQ, mQ != mR);
+    for (int64_t g = 0; g < G; ++g) {
+        const int np = (int)std::min<int64_t>(32, n - 32 * g);
+        const uint32_t pad = np >= 32 ? 0u : 0xffffffffu << np;
+        SlicedCount<E> cnt;
+        sliced_walk2<E, true>(HostSliced{q, r, G, g}, mQ, mR, pad, cnt,
+                              vtab.data(), 1u);
+        uint32_t cb[SlicedShape<E>::NB];
+        cnt.bits(cb);
+        for (int i = 0; i < np; ++i) {
+            obs[32 * g + i] = sliced_count<E>(cb, i);
+            acc[32 * g + i] = (uint8_t)(((~cnt.done()) >> i) & 1u);
+        }
+    }
+}
+
+template <int... Es>
+int sliced_free_dispatch(int E, const uint32_t *q, const uint32_t *r,
+                         int64_t n, int mQ, int mR, uint8_t *acc,
+                         int32_t *obs, std::integer_sequence<int, Es...>)
+{
+    int out = -100;
+    ((E == Es ? (sliced_free_groups<Es>(q, r, n, mQ, mR, acc, obs), out = 0)
+              : 0),
+     ...);
+    return out;
 }
 
 template <int E>
@@ -329,6 +369,18 @@ int emu_sliced(const uint32_t *q, const uint32_t *r, int64_t n, int m, int E,
 {
     return sliced_dispatch(E, q, r, n, m, acc, obs,
                            std::make_integer_sequence<int, 32>{});
+}
+
+// Reads of mQ bases against references of mR bases (mQ != mR) over the
+// sliced layout, with the free-end rule, every group.  Returns -100 if E is
+// not built, -1 for equal lengths.
+int emu_sliced_free(const uint32_t *q, const uint32_t *r, int64_t n, int mQ,
+                    int mR, int E, uint8_t *acc, int32_t *obs)
+{
+    if (mQ == mR)
+        return -1;
+    return sliced_free_dispatch(E, q, r, n, mQ, mR, acc, obs,
+                                std::make_integer_sequence<int, 32>{});
 }
 
 // The sub-maze mode over the sliced layout (sub-mazes of t columns, at most

@@ -83,8 +83,8 @@ def test_segments_match_oracle(F, fmt):
 
 def test_segments_of_one_threshold_share_launches(F):
     """Eleven segments at E = 4 (lengths 1..400, some n not a multiple of
-    32) and two at E = 9: the E = 4 ones go in two launches (8 + 3), every
-    pair against the oracle."""
+    32) and two at E = 9: one launch per threshold, every pair against the
+    oracle."""
     torch = torch_cuda()
     shapes = [(1, 4, 70), (3, 4, 33), (16, 4, 64), (17, 4, 1), (64, 4, 500),
               (99, 4, 1031), (100, 9, 2048), (150, 4, 777), (200, 4, 96),
@@ -100,10 +100,81 @@ def test_segments_of_one_threshold_share_launches(F):
     F.sync()
     before = F.counters().launches
     outs = F.filter_segments(segs, graph=False, sync=True)
-    assert F.counters().launches == before + 3
+    assert F.counters().launches == before + 2
     for k, ((acc, obs), (oacc, oobs)) in enumerate(zip(outs, want)):
         assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
                     f"segment {k} {shapes[k]}")
+
+
+# (read length, reference length, E, n): windows longer and shorter than
+# the read, E from 0 to 31, E at or above the shorter length, ragged groups
+FREE = [(100, 116, 10, 3001), (100, 92, 6, 2048), (100, 108, 4, 1000),
+        (150, 170, 15, 513), (250, 240, 25, 96), (33, 40, 31, 70),
+        (8, 5, 6, 64), (4, 9, 2, 33), (100, 101, 0, 257), (100, 116, 10, 77)]
+
+
+@pytest.mark.parametrize("fmt_graph", [False, True])
+def test_segments_of_different_lengths(F, fmt_graph):
+    """Reads against references of another length (reads inside flanked
+    windows, cut windows, unrelated pairs) over the sliced layout, mixed
+    with a segment of equal lengths: every pair equal to the oracle's
+    sso_filter2 (Section 2.4's correction); segments of one threshold share
+    a launch."""
+    import oracle
+    rng = np.random.default_rng(780)
+    segs, want = [], []
+    for i, (mq, mr, e, n) in enumerate(FREE):
+        reads, _ = synth.pairs_fixed(790 + i, 0, n, mq, synth.rate_recipe(0.1))
+        refs = synth.pairs_fixed(800 + i, 0, n, mr, synth.SHORT_POISSON)[1]
+        for p in range(0, n, 2):  # the read inside random flanks, or cut
+            o = int(rng.integers(0, max(mr - mq, 0) + 1))
+            k = min(mq, mr - o)
+            refs[p, o:o + k] = reads[p, :k]
+        q = F.pack_sliced(to_dev(reads.reshape(-1)), m=mq, n=n)
+        r = F.pack_sliced(to_dev(refs.reshape(-1)), m=mr, n=n)
+        segs.append((q, r, (mq, mr), e, n))
+        want.append(oracle.filter_unequal_batch(
+            reads.reshape(-1), np.arange(n, dtype=np.int64) * mq,
+            np.full(n, mq, np.int32), refs.reshape(-1),
+            np.arange(n, dtype=np.int64) * mr, np.full(n, mr, np.int32), e))
+    # and one of equal lengths at a threshold shared with a different-length
+    # segment: the two kinds never share a launch
+    reads, refs = synth.pairs_fixed(830, 0, 500, 100, synth.SHORT_POISSON)
+    segs.append((F.pack_sliced(to_dev(reads.reshape(-1)), m=100, n=500),
+                 F.pack_sliced(to_dev(refs.reshape(-1)), m=100, n=500), 100,
+                 10, 500))
+    want.append(oracle_fixed(reads, refs, 10))
+    F.sync()
+    outs = F.filter_segments(segs, graph=fmt_graph, sync=True)
+    for k, ((acc, obs), (oacc, oobs)) in enumerate(zip(outs, want)):
+        assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                    f"segment {k} {(FREE + [(100, 100, 10, 500)])[k]}")
+    # pair-major input takes equal lengths only
+    pk = torch_cuda().zeros(64 * 8, dtype=torch_cuda().int32, device="cuda")
+    with pytest.raises(binding.SSError) as ex:
+        F.filter_segments([(pk, pk, (100, 116), 3, 4)], fmt=PACKED)
+    assert ex.value.code == binding.SS_ERR_UNSUPPORTED
+
+
+def test_more_segments_than_a_launch_takes(F):
+    """37 segments at one threshold (lengths 1..37): two launches (32 + 5),
+    every pair against the oracle."""
+    segs, want = [], []
+    for m in range(1, 38):
+        n = 33 + m
+        reads, refs = synth.pairs_fixed(840 + m, 0, n, m,
+                                        synth.rate_recipe(0.2))
+        segs.append((F.pack_sliced(to_dev(reads.reshape(-1)), m=m, n=n),
+                     F.pack_sliced(to_dev(refs.reshape(-1)), m=m, n=n), m, 3,
+                     n))
+        want.append(oracle_fixed(reads, refs, 3))
+    F.sync()
+    before = F.counters().launches
+    outs = F.filter_segments(segs, graph=False, sync=True)
+    assert F.counters().launches == before + 2
+    for k, ((acc, obs), (oacc, oobs)) in enumerate(zip(outs, want)):
+        assert_same(acc.cpu().numpy(), obs.cpu().numpy(), oacc, oobs,
+                    f"segment {k} (m = {k + 1})")
 
 
 def test_segments_argument_errors(F):
@@ -132,7 +203,8 @@ def test_segments_argument_errors(F):
         binding.SS_ERR_UNSUPPORTED
     # a null output pointer, through the raw call
     arr = (binding.Segment * 1)()
-    arr[0] = binding.Segment(q.data_ptr(), q.data_ptr(), n, m, 3, None, None)
+    arr[0] = binding.Segment(q.data_ptr(), q.data_ptr(), n, m, 3, None, None,
+                             0)
     assert binding.ss_filter_segments(F.ctx, arr, 1, SLICED, 0, 0) == \
         binding.SS_ERR_INVALID_ARG
     assert binding.ss_filter_segments(F.ctx, arr, 1, SLICED, 1, 0) == \

@@ -381,6 +381,45 @@ def test_sliced_walk_matches_oracle(emu, m):
         assert bad.size == 0, (m, n, E, bad[:5], obs[bad[:5]], oobs[bad[:5]])
 
 
+# (read length, reference length): references longer and shorter, by less
+# and more than E, around the block edges, a one-base sequence
+FREE_SHAPES = [(100, 116), (100, 92), (100, 101), (100, 99), (33, 40),
+               (40, 33), (5, 9), (9, 5), (1, 4), (4, 1), (16, 17), (150, 100)]
+
+
+@pytest.mark.parametrize("mq,mr", FREE_SHAPES)
+def test_sliced_free_walk_matches_oracle(emu, mq, mr):
+    """The sliced walk over the reference's columns against a read of
+    another length, with Section 2.4's correction (cells past either end of
+    the read free), at every E it is built for, against the oracle's
+    sso_filter2 pair by pair: reads inside flanked windows, cut windows and
+    unrelated pairs, a ragged last group."""
+    rng = np.random.default_rng(3000 + 7 * mq + mr)
+    n = 70
+    reads, _ = synth.pairs_fixed(7200 + mq, 0, n, mq, synth.rate_recipe(0.1))
+    refs = synth.pairs_fixed(7300 + mr, 0, n, mr, synth.SHORT_POISSON)[1]
+    # half the references: the read itself inside random flanks (or cut)
+    for p in range(0, n, 2):
+        o = int(rng.integers(0, max(mr - mq, 0) + 1))
+        k = min(mq, mr - o)
+        refs[p, o:o + k] = reads[p, :k]
+    q = oracle.pack_sliced(reads)
+    r = oracle.pack_sliced(refs)
+    ro = np.arange(n + 1, dtype=np.int64) * mq
+    fo = np.arange(n + 1, dtype=np.int64) * mr
+    for E in range(32):
+        acc = np.zeros(n, np.uint8)
+        obs = np.zeros(n, np.int32)
+        assert emu.emu_sliced_free(P(q), P(r), n, mq, mr, E, P(acc),
+                                   P(obs)) == 0
+        oacc, oobs = oracle.filter_unequal_batch(
+            reads.reshape(-1), ro[:-1], np.full(n, mq, np.int32),
+            refs.reshape(-1), fo[:-1], np.full(n, mr, np.int32), E)
+        bad = np.flatnonzero((acc != oacc) | (obs != oobs))
+        assert bad.size == 0, (mq, mr, E, bad[:5], obs[bad[:5]],
+                               oobs[bad[:5]])
+
+
 SETS = {0: (0, 2, 4), 1: (0, 1, 2, 3, 4), 2: (1, 3), 3: (3, 4)}
 
 
