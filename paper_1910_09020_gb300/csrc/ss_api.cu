@@ -773,8 +773,8 @@ static int segment_launch(ss_ctx *ctx, const ss_segment &s, cudaStream_t st)
 // The segments' launches, side by side on the lanes in the given order;
 // over the sliced layout, segments of one threshold share a launch (up to
 // kSlicedMaxSegments each, equal and different lengths apart), placed
-// where the first of them stands.  m_ref is set (the caller's 0 replaced
-// by m).
+// where the first of them stands.  Every segment's m_ref is its reference
+// length (the caller's 0 already replaced by m).
 static int segments_launch(ss_ctx *ctx, int format,
                            const std::vector<ss_segment> &segs,
                            cudaStream_t st)
@@ -819,8 +819,9 @@ static int segments_launch(ss_ctx *ctx, int format,
 }
 
 // A segment's time, roughly: the larger of its bytes at the HBM rate and
-// its walk's logic operations (m (6e + 3) / 32 per pair) at the logic-pipe
-// rate, in units where the two rates are 6.8 and 20 per unit time.
+// its walk's logic operations (m_ref (6e + 3) / 32 per pair: one column
+// per reference base) at the logic-pipe rate, in units where the two rates
+// are 6.8 and 20 per unit time.
 static double segment_cost(const ss_segment &s)
 {
     const double bytes = (s.m + 3) / 4 + (s.m_ref + 3) / 4 + 5.0;
