@@ -5,8 +5,10 @@
 //
 // Three passes, no host synchronisation: per-CTA counts of accepted pairs,
 // an exclusive scan of the CTA counts (one CTA), and a scatter in which each
-// CTA writes its accepted indices at its offset, ranks inside the CTA coming
-// from warp ballots.
+// CTA writes its accepted indices at its offset.  A thread takes 16
+// consecutive flags (one 16-byte load where the flags are aligned) as a
+// 16-bit mask; ranks inside the CTA come from a scan of the threads' mask
+// counts.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -20,18 +22,40 @@ constexpr int kCompactThreads = 256;
 constexpr int kCompactItems = 16;  // pairs per thread
 constexpr int kCompactChunk = kCompactThreads * kCompactItems;
 
+// Flags p0 .. p0+15 (those below n) as a mask: bit k set when flag p0 + k
+// is nonzero.
+__device__ __forceinline__ uint32_t compact_mask16(const uint8_t *acc,
+                                                   int64_t n, int64_t p0)
+{
+    uint32_t mask = 0u;
+    if (p0 + 16 <= n && ((uintptr_t)(acc + p0) & 15) == 0) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(acc + p0));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // bit 7 of each byte: the byte is nonzero
+            const uint32_t nz =
+                (((w[q] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w[q]) & 0x80808080u;
+            // bits 7, 15, 23, 31 -> bits 4q .. 4q+3
+            const uint32_t b = (nz >> 7) & 0x01010101u;
+            mask |= ((b * 0x01020408u) >> 24 & 0xfu) << (4 * q);
+        }
+    } else {
+        for (int k = 0; k < 16; ++k)
+            if (p0 + k < n && acc[p0 + k])
+                mask |= 1u << k;
+    }
+    return mask;
+}
+
 __global__ void __launch_bounds__(kCompactThreads)
     k_compact_count(const uint8_t *__restrict__ acc, int64_t n,
                     int64_t *__restrict__ block_counts)
 {
     __shared__ int warp_sums[kCompactThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kCompactChunk;
-    int c = 0;
-#pragma unroll
-    for (int k = 0; k < kCompactItems; ++k) {
-        const int64_t p = base + k * kCompactThreads + threadIdx.x;
-        c += (p < n && acc[p]) ? 1 : 0;
-    }
+    const int64_t p0 = (int64_t)blockIdx.x * kCompactChunk +
+                       (int64_t)threadIdx.x * kCompactItems;
+    int c = __popc(compact_mask16(acc, n, p0));
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0)
         warp_sums[threadIdx.x >> 5] = c;
@@ -79,34 +103,33 @@ __global__ void __launch_bounds__(kCompactThreads)
                       const int64_t *__restrict__ block_offsets,
                       int64_t *__restrict__ out_index)
 {
-    __shared__ int warp_base[kCompactThreads / 32];
-    __shared__ int64_t running;
+    __shared__ int warp_sums[kCompactThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kCompactChunk;
-    if (threadIdx.x == 0)
-        running = block_offsets[blockIdx.x];
+    const int64_t p0 = (int64_t)blockIdx.x * kCompactChunk +
+                       (int64_t)threadIdx.x * kCompactItems;
+    uint32_t mask = compact_mask16(acc, n, p0);
+    const int c = __popc(mask);
+    // inclusive scan of the counts over the warp, then over the warps
+    int x = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off)
+            x += y;
+    }
+    if (lane == 31)
+        warp_sums[warp] = x;
     __syncthreads();
-    for (int k = 0; k < kCompactItems; ++k) {
-        const int64_t p = base + k * kCompactThreads + threadIdx.x;
-        const bool a = p < n && acc[p];
-        const unsigned ballot = __ballot_sync(0xffffffffu, a);
-        if (lane == 0)
-            warp_base[warp] = __popc(ballot);
-        __syncthreads();
-        // prefix over the warps of this round (in index order)
-        int before = 0, round = 0;
-        for (int w = 0; w < kCompactThreads / 32; ++w) {
-            const int c = warp_base[w];
-            before += w < warp ? c : 0;
-            round += c;
-        }
-        if (a)
-            out_index[running + before +
-                      __popc(ballot & ((1u << lane) - 1u))] = p;
-        __syncthreads();
-        if (threadIdx.x == 0)
-            running += round;
-        __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < kCompactThreads / 32; ++w)
+        before += w < warp ? warp_sums[w] : 0;
+    int64_t o = block_offsets[blockIdx.x] + before + (x - c);
+    // the thread's accepted indices, in order
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        out_index[o++] = p0 + k;
     }
 }
 
