@@ -23,10 +23,14 @@ __host__ __device__ constexpr int rw_emax(int c)
 {
     return c == 0 ? 1 : c == 1 ? 3 : c == 2 ? 7 : c == 3 ? 15 : 31;
 }
-constexpr int kCwwClasses = 3;
+// m bounds of the warp-per-pair classes: a class's shared-memory slice is
+// sized for its bound, so finer bounds put more CTAs on an SM (the kernel
+// is latency-bound; its shared memory sets the CTAs per SM from 6 KB on)
+constexpr int kCwwClasses = 7;
 __host__ __device__ constexpr int cww_mbound(int c)
 {
-    return c == 0 ? 2048 : c == 1 ? 8192 : 16384;
+    return c == 0 ? 2048 : c == 1 ? 3072 : c == 2 ? 4096 : c == 3 ? 6144
+         : c == 4 ? 8192 : c == 5 ? 12288 : 16384;
 }
 constexpr int kCwwMaxE = 511;
 constexpr int kCwcWidths = 5;  // CTA widths 64, 128, 256, 512, 1024

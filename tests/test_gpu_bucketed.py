@@ -106,6 +106,19 @@ def test_tuning_never_changes_results(F, rw_max_e, k):
     assert_same(acc, obs, oacc, oobs, f"tuning {rw_max_e},{k}")
 
 
+def test_warp_classes_every_bound(F):
+    """Warp-per-pair pairs (32 <= E' <= 511) in every m bound of that
+    family, each bound's edges included."""
+    L = np.array([2048, 2049, 3072, 3073, 4096, 4097, 6144, 6145, 8192,
+                  8193, 12288, 12289, 16384, 5000, 10000], np.int32)
+    Es = np.array([40, 102, 300, 153, 204, 500, 307, 33, 409, 511, 100,
+                   61, 200, 250, 500], np.int32)
+    host, dev = packed_batch(F, 34, L, synth.rate_recipe(0.03))
+    acc, obs = run(F, dev, Es)
+    oacc, oobs = oracle_var(host, L, Es)
+    assert_same(acc, obs, oacc, oobs, "warp classes")
+
+
 def test_long_reads(F):
     """Lengths beyond the warp kernel (m > 16384) and in every m bound of
     the CTA kernel."""
