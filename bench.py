@@ -997,7 +997,8 @@ def _pool_model(pool, ipk, sample=400, seed=1910_09020 + 55):
 def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
     """Requests of 1..4096 pairs (log-uniform), lengths log-uniform
     100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
-    Poisson process at 30 %, 60 % and 90 % of the measured capacity."""
+    Poisson process at 30 %, 60 %, 75 % and 90 % of the measured (burst)
+    capacity."""
     import torch
 
     from paper_1910_09020_gb300 import binding, synth
@@ -1059,7 +1060,7 @@ def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
                 "sample": f"op model from the oracle on {k} pairs drawn "
                           f"uniformly from the pool ({t_o:.1f} s)"}
         loads = []
-        for frac in (0.3, 0.6, 0.9):
+        for frac in (0.3, 0.6, 0.75, 0.9):
             rate = frac * cap_req
             nreq = max(20, int(rate * seconds))
             arr = synth.poisson_arrivals(1910_09020 + int(frac * 100), nreq,

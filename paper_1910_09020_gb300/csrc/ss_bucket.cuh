@@ -202,13 +202,20 @@ struct LongQueue {
 
 constexpr int kLongRing = 1 << 18;   // entries (a power of two)
 constexpr int kLongBatches = 64;     // descriptors
-// Worker shape: one CTA of 512 threads per SM (A/B on GB300 with the
-// served workload at 2 slots: 256 threads 222k pairs/s, 512 threads 260k;
-// 768 or 1024 threads, or two CTAs per SM, left too little of the SM for
-// the batches' own kernels, which then waited for the worker to leave)
-constexpr int kLongThreads = 512;    // worker CTA width
-constexpr int kLongCtasPerSm = 1;    // worker CTAs per SM
-constexpr int kLongWords = 24 * 1024;  // worker shared words per pair
+// Worker shape: one CTA of 512 threads per SM, split into two teams of
+// 256 that each route their own pair, with 72 KB of shared memory each (the
+// longest pair of the served workload, 100 kbp at E = 10^4, needs 70 KB).
+// A/B on GB300, served workload at 2 slots (burst capacity): one pair per
+// CTA of 256 threads 222k pairs/s, of 512 threads 260k; two teams with 48,
+// 64, 72 and 80 KB each 342k, 25k, 374k and 376k -- with 48 KB the longest
+// pairs stayed in their batches' passes, and with 64 KB those passes'
+// kernels no longer fitted beside the worker and waited for it to leave;
+// four teams of 128 threads with 24 KB each 222k.  768 or 1024 threads, or
+// two CTAs per SM, left too little of the SM for the batches' own kernels.
+constexpr int kLongThreads = 512;      // worker CTA width
+constexpr int kLongCtasPerSm = 1;      // worker CTAs per SM
+constexpr int kLongTeams = 2;          // pairs a worker CTA routes at once
+constexpr int kLongWords = 36 * 1024;  // worker shared words per CTA
 
 // Whether the queue takes a pair of class cls (m, E'): the CTA-per-pair
 // classes whose staged planes fit the worker's shared memory.

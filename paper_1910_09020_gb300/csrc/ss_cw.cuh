@@ -151,25 +151,35 @@ struct CwArgs {
 __host__ __device__ inline bool long_queued(int cls, int m, int Ee)
 {
     return cls >= kRwClasses + kCwwClasses &&
-           CwLayout::of(m, Ee).words() <= kLongWords;
+           CwLayout::of(m, Ee).words() <= kLongWords / kLongTeams;
 }
 
-// Route one pair with the whole CTA (nt threads, any number of row words):
-// the pair staged into smem, then the greedy of Section 2.4 with one CTA
-// maximum per step (red: two 32-entry buffers, buf toggles between
-// steps).  Returns min(count, E+1) (count itself is capped by the loop).
-template <int K>
-__device__ __forceinline__ int cw_cta_route(uint32_t *smem, int (*red)[32],
-                                            int &buf, const uint32_t *gq,
-                                            const uint32_t *gr, int m, int E)
+// Barrier of a team of nt threads (whole warps) with its own named
+// barrier bar (1..15); bar 0: the whole CTA.
+__device__ __forceinline__ void team_sync(int bar, int nt)
 {
-    const int t = threadIdx.x;
-    const int nt = blockDim.x;
+    if (bar == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" : : "r"(bar), "r"(nt) : "memory");
+}
+
+// Route one pair with a team of nt threads (t: the thread's index in the
+// team; any number of row words): the pair staged into smem, then the
+// greedy of Section 2.4 with one team maximum per step (red: two 32-entry
+// buffers, buf toggles between steps).  Returns min(count, E+1) (count
+// itself is capped by the loop).
+template <int K>
+__device__ __forceinline__ int cw_team_route(uint32_t *smem, int (*red)[32],
+                                             int &buf, const uint32_t *gq,
+                                             const uint32_t *gr, int m, int E,
+                                             int t, int nt, int bar)
+{
     const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
     const int Ee = eff_threshold(m, E);
     const CwLayout L = CwLayout::of(m, Ee);
     cw_stage(smem, L, gq, gr, m, t, nt);
-    __syncthreads();
+    team_sync(bar, nt);
     const int nwords = (2 * Ee + 1 + 31) >> 5;
     int c = 0, count = 0;
     for (;;) {
@@ -179,7 +189,7 @@ __device__ __forceinline__ int cw_cta_route(uint32_t *smem, int (*red)[32],
         cand = __reduce_max_sync(0xffffffffu, cand);
         if (lane == 0)
             red[buf][warp] = cand;
-        __syncthreads();
+        team_sync(bar, nt);
         int v = lane < nwarp ? red[buf][lane] : -1;
         const int pstar = __reduce_max_sync(0xffffffffu, v);
         buf ^= 1;
@@ -191,6 +201,16 @@ __device__ __forceinline__ int cw_cta_route(uint32_t *smem, int (*red)[32],
         c = pstar + 1;
     }
     return count;
+}
+
+// The same with the whole CTA as the team.
+template <int K>
+__device__ __forceinline__ int cw_cta_route(uint32_t *smem, int (*red)[32],
+                                            int &buf, const uint32_t *gq,
+                                            const uint32_t *gr, int m, int E)
+{
+    return cw_team_route<K>(smem, red, buf, gq, gr, m, E, threadIdx.x,
+                            blockDim.x, 0);
 }
 
 // Warp per pair; blockDim.x / 32 warps, each with its own slice.

@@ -232,39 +232,44 @@ __device__ int long_claim(const ssk::LongQueue &q, uint64_t idle_ns,
     return -1;
 }
 
-// The long-lived worker: each CTA takes queued pairs one at a time and
-// routes each with the whole CTA (Section 2.4, rows across the threads);
-// the CTA that routes a batch's last queued pair publishes the batch's
+// The long-lived worker: each CTA is two teams of 256 threads, and each
+// team takes queued pairs one at a time and routes each (Section 2.4, rows
+// across the team's threads) in its half of the shared memory;
+// the team that routes a batch's last queued pair publishes the batch's
 // generation to the host.  Pairs flagged as holding a non-base get
 // obstacles -1 (their batch's request fails alone, as in the pass).
 __global__ void __launch_bounds__(ssk::kLongThreads)
     k_long_worker(const ssk::LongQueue q, uint64_t idle_ns)
 {
+    constexpr int TT = ssk::kLongThreads / ssk::kLongTeams;
     extern __shared__ uint32_t smem[];
-    __shared__ int red[2][32];
-    __shared__ int64_t s_pair;
-    __shared__ int s_batch;
-    const int t = threadIdx.x;
+    __shared__ int red[ssk::kLongTeams][2][32];
+    __shared__ int64_t s_pair[ssk::kLongTeams];
+    __shared__ int s_batch[ssk::kLongTeams];
+    const int team = threadIdx.x / TT, t = threadIdx.x % TT;
+    const int bar = 1 + team;  // named barrier of the team
+    uint32_t *slice = smem + team * (ssk::kLongWords / ssk::kLongTeams);
     int buf = 0;
     for (;;) {
         if (t == 0) {
             int64_t p = 0;
-            s_batch = long_claim(q, idle_ns, p);
-            s_pair = p;
+            s_batch[team] = long_claim(q, idle_ns, p);
+            s_pair[team] = p;
         }
-        __syncthreads();
-        const int b = s_batch;
+        ssk::team_sync(bar, TT);
+        const int b = s_batch[team];
         if (b < 0)
             break;
-        const int64_t p = s_pair;
+        const int64_t p = s_pair[team];
         const ssk::PairSet ps = q.batches[b].ps;
         const uint8_t *bad = q.batches[b].bad;
         const int m = ps.len(p), E = ps.thr(p);
         int count = -1;
         if (!(bad && bad[p])) {
             const int64_t off = ps.off(p);
-            count = ssk::cw_cta_route<8>(smem, red, buf, ps.reads + off,
-                                         ps.refs + off, m, E);
+            count = ssk::cw_team_route<8>(slice, red[team], buf,
+                                          ps.reads + off, ps.refs + off, m, E,
+                                          t, TT, bar);
         }
         if (t == 0) {
             ps.acc[p] = (uint8_t)(count >= 0 && count <= E);
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(ssk::kLongThreads)
             }
             atomicSub(q.busy, 1);
         }
-        __syncthreads();  // the slice and s_batch are reused
+        ssk::team_sync(bar, TT);  // the slice and s_batch are reused
     }
 }
 
