@@ -999,6 +999,9 @@ def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
     100..100000 bp, edit rate U[0, 0.15], E = 10 % of length, arriving as a
     Poisson process at 30 %, 60 %, 75 % and 90 % of the measured (burst)
     capacity."""
+    import queue
+    import threading
+
     import torch
 
     from paper_1910_09020_gb300 import binding, synth
@@ -1068,18 +1071,28 @@ def run_serving(seconds: float, slots: int = 2, ipk=None) -> dict:
             pick = np.random.default_rng(int(frac * 1000)).integers(
                 0, len(pool), nreq)
             S.reset_stats()
-            tickets = []
+            # a client thread fetches each result as soon as it is done,
+            # while requests keep arriving: a batch holds its device memory
+            # (within the server's budget) until its results are fetched
+            todo = queue.Queue()
+
+            def fetcher():
+                while True:
+                    t = todo.get()
+                    if t is None:
+                        return
+                    S.wait(t)
+                    S.fetch(t)
+            th = threading.Thread(target=fetcher)
+            th.start()
             t0 = time.perf_counter()
             for k in range(nreq):
                 delay = arr[k] - (time.perf_counter() - t0)
                 if delay > 0:
                     time.sleep(delay)
-                tickets.append(S.submit(*pool[pick[k]]))
-            # fetch each result as soon as it is done: results hold device
-            # memory (within the server's budget) until they are fetched
-            for t in tickets:
-                S.wait(t)
-                S.fetch(t)
+                todo.put(S.submit(*pool[pick[k]]))
+            todo.put(None)
+            th.join()
             span = time.perf_counter() - t0
             st = S.stats()
             npairs = int(sum(len(pool[i][2]) for i in pick))
